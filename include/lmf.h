@@ -1,0 +1,237 @@
+/*
+ * lmf.h -- C ABI of the GB300 aggregate-batch engine.
+ *
+ * The engine evaluates one batch of group-by aggregates over the natural join
+ * of an acyclic schema without materialising the join (Sec. 1.1, problem
+ * statement; Sec. 3.1-3.2, aggregates decomposed into views along the edges of
+ * a join tree).  A batch is a list of queries Q(F; alpha) (Eq. query, Sec. 2):
+ * F is 0..3 categorical group-by attributes, alpha is a product of factors,
+ * each a power x^p (p = 1, 2) of a continuous attribute or a threshold
+ * indicator 1[x <= t] / 1[x > t] (the Kronecker deltas of Sec. 1.1).
+ *
+ * Evaluation is one bottom-up pass over the join tree: every child relation
+ * is reduced on its join key into a device-resident view, views sharing a
+ * parent key are merged (Sec. 3.4), and the root relation is scanned once
+ * while probing the views (Sec. 3.5).  All compute runs in CUDA kernels for
+ * sm_103a; there is no CPU fallback.
+ *
+ * Conventions for every entry point
+ *   - Return value: LMF_OK (0) or a negative lmf_status; nothing crosses the
+ *     ABI as an exception.  lmf_error_message() gives a one-line detail of the
+ *     last failure on a context.
+ *   - Pointers named dev_* or documented as device pointers are CUDA device
+ *     pointers on the context's device; everything else is host memory.
+ *   - One context per host thread; a context is not thread safe.  There is no
+ *     global mutable state.
+ */
+#ifndef LMF_H_
+#define LMF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lmf_ctx lmf_ctx;
+typedef int32_t lmf_status;
+
+/* status codes */
+#define LMF_OK               0
+#define LMF_ERR_ARG         -1   /* bad argument: null pointer, bad id, bad size */
+#define LMF_ERR_NOT_TREE    -2   /* declared edges do not form a join tree */
+#define LMF_ERR_DTYPE       -3   /* column dtype/role does not fit its use */
+#define LMF_ERR_KEY         -4   /* key or category value out of its range */
+#define LMF_ERR_OOM         -5   /* device allocation failed */
+#define LMF_ERR_CUDA        -6   /* a CUDA call failed */
+#define LMF_ERR_TIMEOUT     -7   /* a device-side wait ran out of its limit */
+#define LMF_ERR_OVERFLOW    -8   /* an exact integer count would overflow */
+#define LMF_ERR_STATE       -9   /* call out of order (e.g. run before plan) */
+#define LMF_ERR_UNSUPPORTED -10  /* valid query shape this engine does not evaluate */
+
+/* column dtypes */
+#define LMF_I32 0
+#define LMF_F32 1
+#define LMF_F64 2
+#define LMF_I64 3                /* result dtype of exact counts */
+
+/* column roles */
+#define LMF_KEY  0               /* int32 join key, values >= 0 */
+#define LMF_CONT 1               /* continuous attribute (f32 or f64) */
+#define LMF_CAT  2               /* int32 category in [0, cat_domain) */
+
+/* factor kinds */
+#define LMF_POW 0                /* attr^power, power in {1, 2} */
+#define LMF_LE  1                /* 1[attr <= threshold] */
+#define LMF_GT  2                /* 1[attr >  threshold] */
+
+/* plan options */
+#define LMF_PREC_PLAIN_FP32  0   /* root Gram on CUDA cores, FP32 products */
+#define LMF_PREC_SPLIT_BF16  1   /* root Gram on tcgen05 tensor cores, 3-way split bf16 */
+#define LMF_BATCH_SINGLE     0   /* lmf_run enqueues the kernels one by one */
+#define LMF_BATCH_GRAPH      1   /* lmf_run replays one captured CUDA graph */
+#define LMF_ROOT_DECLARED    0   /* the relation that is nobody's child */
+
+#define LMF_MAX_GROUP_BY 3
+#define LMF_MAX_FACTORS  16
+
+typedef struct {
+  const char* name;       /* attribute name; join keys share names across relations */
+  int32_t dtype;          /* LMF_I32 / LMF_F32 / LMF_F64 */
+  int32_t role;           /* LMF_KEY / LMF_CONT / LMF_CAT */
+  const void* data;       /* nrows elements; device pointer, or pinned host pointer
+                             when on_host = 1 (copied to the device by every lmf_run) */
+  int32_t cat_domain;     /* LMF_CAT: number of categories */
+  int32_t on_host;        /* 0: device memory (borrowed); 1: host memory */
+} lmf_column;
+
+typedef struct {
+  const char* attr;
+  int32_t kind;           /* LMF_POW / LMF_LE / LMF_GT */
+  int32_t power;          /* LMF_POW: 1 or 2 */
+  double threshold;       /* LMF_LE / LMF_GT */
+} lmf_factor;
+
+typedef struct {
+  int32_t n_group_by;                     /* 0..LMF_MAX_GROUP_BY */
+  const char* group_by[LMF_MAX_GROUP_BY]; /* categorical attributes */
+  int32_t n_factors;                      /* 0 (COUNT) .. LMF_MAX_FACTORS */
+  const lmf_factor* factors;
+} lmf_agg_spec;
+
+typedef struct {
+  int32_t precision;      /* LMF_PREC_* */
+  int32_t batching;       /* LMF_BATCH_* */
+  int32_t tile_rows;      /* root rows per tile; 0 = tuned default */
+  int32_t ctas_per_sm;    /* resident CTAs per SM for the root scan; 0 = default */
+  int32_t root_mode;      /* LMF_ROOT_DECLARED */
+  int32_t reserved[3];
+} lmf_plan_opts;
+
+/* Statistics of a plan, for reporting (lmf_plan_info). */
+typedef struct {
+  int32_t n_views;            /* child views built per run */
+  int32_t n_probe_groups;     /* merged views probed by the root scan */
+  int32_t z_len;              /* length of the per-row vector z = [1, x_root, view means] */
+  int32_t n_gram_aggs;        /* aggregates read off the root Gram */
+  int32_t n_grouped_aggs;     /* aggregates with group-by attributes */
+  int32_t n_filtered_aggs;    /* aggregates with threshold indicators */
+  int32_t n_kernels_per_run;  /* kernel launches per lmf_run */
+  int32_t unique_keys;        /* 1 when every child key is unique (no fan-out) */
+  int32_t root_grid;          /* CTAs of the root scan */
+  int32_t precision;          /* precision actually used */
+  int64_t root_rows;          /* rows of the root relation */
+  int64_t scratch_bytes;      /* device bytes owned by the plan */
+} lmf_plan_stats;
+
+/*
+ * Create a context on CUDA device `device` (Sec. 1.2: one engine instance
+ * per batch workload).  *out receives the context.  Errors: LMF_ERR_ARG,
+ * LMF_ERR_CUDA when the device cannot be used.
+ */
+lmf_status lmf_create(int device, lmf_ctx** out);
+
+/* Free every device buffer the context owns and the context itself. */
+lmf_status lmf_destroy(lmf_ctx* ctx);
+
+/*
+ * Register a relation R(omega_R) of the database (Sec. 2, query language):
+ * `ncols` columns of `nrows` rows each, columnar.  Column memory is borrowed:
+ * the caller keeps it alive and unmodified until the last lmf_sync that uses
+ * it.  Names must be unique inside the relation; a non-key name must not occur
+ * in another relation (the natural join would join on it).  *rel_id receives
+ * the relation's id (0, 1, ... in registration order).
+ * Errors: LMF_ERR_ARG, LMF_ERR_DTYPE (key/cat columns must be LMF_I32,
+ * continuous ones LMF_F32 or LMF_F64), LMF_ERR_STATE after lmf_declare_join.
+ */
+lmf_status lmf_register_relation(lmf_ctx* ctx, const char* name, int64_t nrows,
+                                 const lmf_column* cols, int ncols, int* rel_id);
+
+/*
+ * Declare the join tree (Sec. 3.1): edge e joins child_rel[e] to its parent
+ * parent_rel[e] on the int32 attribute key_attr[e], present in both.  The
+ * edges must form a tree over all registered relations; its root is the
+ * relation that is nobody's child.  Child keys are indexed here (the engine's
+ * analogue of load time, Sec. 4 setup: not part of a run): key range and
+ * multiplicity are measured on the device.
+ * Errors: LMF_ERR_NOT_TREE, LMF_ERR_ARG (unknown attribute), LMF_ERR_DTYPE,
+ * LMF_ERR_KEY (negative keys, or keys too sparse for direct addressing:
+ * max key >= 4 * rows + 4096), LMF_ERR_UNSUPPORTED (two relations sharing
+ * an attribute other than their edge key).
+ */
+lmf_status lmf_declare_join(lmf_ctx* ctx, int n_edges, const int* parent_rel,
+                            const int* child_rel, const char* const* key_attr);
+
+/*
+ * Declare a batch of n aggregates (Sec. 1.1, Eq. query).  *batch_id receives
+ * its id.  Results of aggregate i: an exact int64 count per group when no
+ * factor is a power (COUNT, possibly filtered), otherwise a float64 sum per
+ * group.  Groups are dense, row-major over the group-by attributes' values;
+ * empty groups read 0.
+ * Errors: LMF_ERR_ARG (unknown attribute, bad factor), LMF_ERR_DTYPE (group-by
+ * on a non-categorical attribute), LMF_ERR_STATE (before lmf_declare_join).
+ */
+lmf_status lmf_declare_batch(lmf_ctx* ctx, const lmf_agg_spec* aggs, int n, int* batch_id);
+
+/*
+ * Plan a batch (Sec. 3.2-3.5 analogue): decompose every aggregate into the
+ * child views it needs, merge views that share a parent key, pick the root
+ * scan's form and tiles, allocate all device buffers, and measure value
+ * ranges of the columns the batch reads (for the exact fixed-point
+ * accumulators).  opts may be NULL (defaults: split-bf16 Gram, graph batching).
+ * Errors: LMF_ERR_UNSUPPORTED for aggregate shapes outside this engine
+ * (e.g. group-by attributes reached through a non-unique key, degree-2
+ * monomials under a group-by), LMF_ERR_OOM, LMF_ERR_CUDA.
+ */
+lmf_status lmf_plan(lmf_ctx* ctx, int batch_id, const lmf_plan_opts* opts);
+
+/* Report statistics of a planned batch. */
+lmf_status lmf_plan_info(lmf_ctx* ctx, int batch_id, lmf_plan_stats* info);
+
+/*
+ * Run a planned batch on `cuda_stream` (a cudaStream_t; NULL = the context's
+ * own stream).  Asynchronous: it only enqueues work (host-resident columns
+ * are copied in on the same stream first).  Device-detected errors are
+ * latched and returned by lmf_sync.
+ */
+lmf_status lmf_run(lmf_ctx* ctx, int batch_id, void* cuda_stream);
+
+/*
+ * Wait for the last run of the batch and return its device status: LMF_OK,
+ * LMF_ERR_KEY (a category outside its domain), LMF_ERR_OVERFLOW,
+ * LMF_ERR_TIMEOUT, or LMF_ERR_CUDA.
+ */
+lmf_status lmf_sync(lmf_ctx* ctx, int batch_id);
+
+/*
+ * Shape of aggregate `agg`'s result: *n_groups cells of *dtype (LMF_I64 or
+ * LMF_F64), stored at *offset in the batch's int64 or float64 result array.
+ */
+lmf_status lmf_result_info(lmf_ctx* ctx, int batch_id, int agg, int64_t* n_groups,
+                           int32_t* dtype, int64_t* offset);
+
+/* Total cells of the batch's int64 and float64 result arrays. */
+lmf_status lmf_result_sizes(lmf_ctx* ctx, int batch_id, int64_t* n_i64, int64_t* n_f64);
+
+/*
+ * Copy all results of the last run: n_i64 int64 cells to dst_i64 and n_f64
+ * doubles to dst_f64 (either may be NULL to skip), host or device memory
+ * (dst_is_device).  Enqueued on `cuda_stream` after the run; a host copy
+ * waits for it.
+ */
+lmf_status lmf_read_results(lmf_ctx* ctx, int batch_id, int64_t* dst_i64, double* dst_f64,
+                            int dst_is_device, void* cuda_stream);
+
+/* Copy one aggregate's result (n_groups cells of its dtype) to host memory. */
+lmf_status lmf_read_result(lmf_ctx* ctx, int batch_id, int agg, void* dst);
+
+/* Static text of a status code. */
+const char* lmf_status_string(lmf_status s);
+
+/* Detail of the last failure on ctx (empty string when none). */
+const char* lmf_error_message(lmf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LMF_H_ */

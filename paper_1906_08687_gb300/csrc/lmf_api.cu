@@ -1,0 +1,1271 @@
+// lmf_api.cu -- the C ABI (include/lmf.h) and the host planner.
+//
+// Planning follows the paper's logical layers in a GPU form:
+//   join tree (Sec. 3.1)            -> lmf_declare_join validates the tree, indexes child keys
+//   aggregate pushdown (Sec. 3.2)   -> every child relation gets one view carrying its
+//                                      subtree count, the means of the subtree features the
+//                                      batch needs and the categories it groups by
+//   view merging (Sec. 3.4)         -> views of children joined on the same parent key share
+//                                      one record array (a probe group); one view per edge
+//                                      serves every aggregate that needs it
+//   view groups / ordering (Sec. 3.4) -> child views are built deepest first
+//   multi-output plan (Sec. 3.5)    -> one root scan produces the Gram, the counts, the
+//                                      reverse views and the per-row grouped tables at once
+#include "lmf.h"
+#include "lmf_internal.h"
+#include "lmf_tree.h"
+#include "lmf_gram_tc.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <set>
+#include <string>
+#include <vector>
+
+using namespace lmf;
+
+namespace {
+
+struct ColumnH {
+  std::string name;
+  int dtype, role, dom, on_host;
+  const void* data;      // user pointer
+  void* dev = nullptr;   // device copy of a host column
+  const void* dptr() const { return on_host ? dev : data; }
+  size_t esize() const { return dtype == LMF_F64 ? 8 : 4; }
+};
+
+struct RelationH {
+  std::string name;
+  int64_t nrows = 0;
+  std::vector<ColumnH> cols;
+  int parent = -1;
+  std::string key;            // join attribute towards the parent
+  std::vector<int> children;
+  int K = 0;                  // child key space 0..K-1
+  int max_mult = 0;           // largest number of rows sharing a key
+  int find(const std::string& n) const {
+    for (size_t i = 0; i < cols.size(); ++i)
+      if (cols[i].name == n) return (int)i;
+    return -1;
+  }
+};
+
+struct FactorH {
+  std::string attr;
+  int kind, power;
+  double thr;
+};
+struct AggH {
+  std::vector<std::string> gb;
+  std::vector<FactorH> f;
+};
+
+// ---- plan ------------------------------------------------------------------
+struct Arena {
+  char* base = nullptr;
+  size_t size = 0, used = 0;
+  size_t take(size_t n) {
+    size_t off = (used + 255) & ~size_t(255);
+    used = off + n;
+    return off;
+  }
+};
+
+struct GroupH {                  // a probe group of relation `owner`
+  int owner;
+  std::string fk;                // FK column in owner
+  std::vector<int> children;     // child relations
+  int K = 0, stride = 0, n_cnt = 0, n_mu = 0, n_cat = 0;
+  size_t rec_off = 0;            // arena offset of the record array
+  std::vector<int> child_mu_off, child_cat_off;
+};
+
+struct RelPlan {
+  std::vector<int> own_feat;     // column indices of needed own continuous columns
+  std::vector<int> own_cat;      // column indices of needed own categorical columns
+  std::vector<int> groups;       // indices into Plan::groups (this relation's children)
+  int d = 0;                     // subtree feature count (section mean words)
+  int ncat = 0;                  // subtree category count
+  bool unique = true;            // every subtree count is 0 or 1
+  double maxcnt = 1;             // bound on the subtree count of one key
+  std::vector<std::string> feat_names;   // subtree features in section order
+  std::vector<std::string> cat_names;    // subtree categories in section order
+  std::vector<double> feat_bound;        // max |x| per subtree feature
+  // general path buffers
+  size_t cnt64_off = 0, S_off = 0, Q_off = 0, sc_off = 0;
+  float s_scale[kMaxOwn + kMaxZ];
+  double q_scale = 1;
+  int group = -1, slot = -1;     // the parent's group holding this relation, child index in it
+};
+
+struct Plan {
+  lmf_plan_opts opts{};
+  std::vector<GroupH> groups;
+  std::vector<RelPlan> rp;
+  std::vector<int> post;         // non-root relations, children before parents
+  Arena arena;
+  size_t zero_off = 0, zero_len = 0;
+  // root
+  RootParams rootp{};
+  int mp = 16, grid = 1;
+  int64_t n_tiles = 0;
+  size_t smem = 0;
+  size_t part_off = 0, cntp_off = 0, G_off = 0, count_off = 0, status_off = 0;
+  std::map<std::string, int> zidx;          // feature -> z index
+  std::map<std::string, int> rowcat;        // category -> row category index
+  std::map<std::string, std::pair<int, int>> catword;  // category -> (root group, word)
+  std::map<std::string, int> feat_group;    // feature -> root group owning it (-1 root)
+  std::vector<RvTask> rv_tasks;
+  std::vector<DirectAgg> direct;
+  std::vector<CorrTask> corr;
+  std::vector<OutMap> maps;
+  size_t rvtask_off = 0, direct_off = 0, corr_off = 0, maps_off = 0;
+  int max_group_K = 0;
+  // filtered aggregates (tree-node batches)
+  std::unique_ptr<TreePlan> tree;
+  // tensor-core Gram
+  std::unique_ptr<GramTcPlan> tc;
+  // results
+  int64_t n_i64 = 0, n_f64 = 0;
+  size_t res_i64_off = 0, res_f64_off = 0;
+  std::vector<int32_t> agg_dtype;
+  std::vector<int64_t> agg_off, agg_n;
+  // graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  int n_kernels = 0;
+  bool unique_all = true;
+  int n_views = 0, n_gram = 0, n_grouped = 0, n_filtered = 0;
+  template <class T>
+  T* at(size_t off) const { return reinterpret_cast<T*>(arena.base + off); }
+};
+
+struct BatchH {
+  std::vector<AggH> aggs;
+  std::unique_ptr<Plan> plan;
+  cudaStream_t last_stream = nullptr;
+};
+
+}  // namespace
+
+struct lmf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  std::vector<RelationH> rels;
+  bool joined = false;
+  int root = -1;
+  std::vector<std::unique_ptr<BatchH>> batches;
+  std::string err;
+};
+
+namespace {
+
+lmf_status fail(lmf_ctx* c, lmf_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+#define CUDA_TRY(ctx, expr)                                                              \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? LMF_ERR_OOM : LMF_ERR_CUDA,      \
+                  "%s: %s", #expr, cudaGetErrorString(e_));                              \
+  } while (0)
+
+void free_plan(Plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->graph_stream) cudaStreamDestroy(p->graph_stream);
+  if (p->arena.base) cudaFree(p->arena.base);
+  p->exec = nullptr;
+  p->graph = nullptr;
+  p->arena.base = nullptr;
+}
+
+// which relation holds attribute `a` (non-key attributes are unique)
+int owner_of(const lmf_ctx* c, const std::string& a, int* col) {
+  for (size_t r = 0; r < c->rels.size(); ++r) {
+    int i = c->rels[r].find(a);
+    if (i >= 0 && c->rels[r].cols[i].role != LMF_KEY) {
+      *col = i;
+      return (int)r;
+    }
+  }
+  return -1;
+}
+
+int fixp_exp(double bound) {  // exponent e with bound * 2^e <= 2^62
+  if (!(bound > 0) || !std::isfinite(bound)) return 40;
+  int e = 62 - (int)std::ceil(std::log2(bound));
+  return std::max(-120, std::min(120, e));
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char* lmf_status_string(lmf_status s) {
+  switch (s) {
+    case LMF_OK: return "ok";
+    case LMF_ERR_ARG: return "bad argument";
+    case LMF_ERR_NOT_TREE: return "edges do not form a join tree";
+    case LMF_ERR_DTYPE: return "column dtype or role does not fit its use";
+    case LMF_ERR_KEY: return "key or category out of range";
+    case LMF_ERR_OOM: return "device out of memory";
+    case LMF_ERR_CUDA: return "CUDA error";
+    case LMF_ERR_TIMEOUT: return "device wait timed out";
+    case LMF_ERR_OVERFLOW: return "exact count overflow";
+    case LMF_ERR_STATE: return "call out of order";
+    case LMF_ERR_UNSUPPORTED: return "unsupported aggregate shape";
+    default: return "unknown status";
+  }
+}
+
+const char* lmf_error_message(lmf_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+lmf_status lmf_create(int device, lmf_ctx** out) {
+  if (!out) return LMF_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return LMF_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return LMF_ERR_CUDA;
+  auto* c = new lmf_ctx();
+  c->device = device;
+  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return LMF_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  *out = c;
+  return LMF_OK;
+}
+
+lmf_status lmf_destroy(lmf_ctx* c) {
+  if (!c) return LMF_ERR_ARG;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  for (auto& b : c->batches)
+    if (b && b->plan) free_plan(b->plan.get());
+  for (auto& r : c->rels)
+    for (auto& col : r.cols)
+      if (col.dev) cudaFree(col.dev);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return LMF_OK;
+}
+
+lmf_status lmf_register_relation(lmf_ctx* c, const char* name, int64_t nrows, const lmf_column* cols,
+                                 int ncols, int* rel_id) {
+  if (!c || !name || nrows < 0 || ncols < 0 || (ncols > 0 && !cols) || !rel_id)
+    return fail(c, LMF_ERR_ARG, "register_relation: bad argument");
+  if (c->joined) return fail(c, LMF_ERR_STATE, "register_relation after declare_join");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LMF_ERR_CUDA, "cudaSetDevice");
+  RelationH r;
+  r.name = name;
+  r.nrows = nrows;
+  for (int i = 0; i < ncols; ++i) {
+    const lmf_column& s = cols[i];
+    if (!s.name || (!s.data && nrows > 0)) return fail(c, LMF_ERR_ARG, "column %d: null name/data", i);
+    if (r.find(s.name) >= 0) return fail(c, LMF_ERR_ARG, "duplicate column %s", s.name);
+    bool ok = (s.role == LMF_KEY || s.role == LMF_CAT) ? s.dtype == LMF_I32
+              : s.role == LMF_CONT                     ? (s.dtype == LMF_F32 || s.dtype == LMF_F64)
+                                                       : false;
+    if (!ok) return fail(c, LMF_ERR_DTYPE, "column %s: dtype %d does not fit role %d", s.name, s.dtype, s.role);
+    if (s.role == LMF_CAT && s.cat_domain <= 0)
+      return fail(c, LMF_ERR_ARG, "column %s: cat_domain must be positive", s.name);
+    ColumnH h{s.name, s.dtype, s.role, s.cat_domain, s.on_host ? 1 : 0, s.data};
+    if (h.on_host && nrows > 0) {
+      if (cudaMalloc(&h.dev, (size_t)nrows * h.esize()) != cudaSuccess)
+        return fail(c, LMF_ERR_OOM, "staging buffer for %s", s.name);
+      cudaMemcpy(h.dev, h.data, (size_t)nrows * h.esize(), cudaMemcpyHostToDevice);
+    }
+    r.cols.push_back(h);
+  }
+  for (auto& other : c->rels) {
+    if (other.name == r.name) return fail(c, LMF_ERR_ARG, "duplicate relation %s", name);
+    for (auto& col : r.cols)
+      if (col.role != LMF_KEY && other.find(col.name) >= 0)
+        return fail(c, LMF_ERR_UNSUPPORTED, "non-key attribute %s occurs in %s and %s", col.name.c_str(),
+                    other.name.c_str(), name);
+  }
+  *rel_id = (int)c->rels.size();
+  c->rels.push_back(std::move(r));
+  return LMF_OK;
+}
+
+lmf_status lmf_declare_join(lmf_ctx* c, int n_edges, const int* parent_rel, const int* child_rel,
+                            const char* const* key_attr) {
+  if (!c) return LMF_ERR_ARG;
+  if (c->joined) return fail(c, LMF_ERR_STATE, "declare_join called twice");
+  const int n = (int)c->rels.size();
+  if (n == 0) return fail(c, LMF_ERR_STATE, "no relations");
+  if (n_edges != n - 1) return fail(c, LMF_ERR_NOT_TREE, "%d relations need %d edges", n, n - 1);
+  if (n_edges > 0 && (!parent_rel || !child_rel || !key_attr)) return fail(c, LMF_ERR_ARG, "null edges");
+  cudaSetDevice(c->device);
+  for (auto& r : c->rels) {
+    r.parent = -1;
+    r.children.clear();
+  }
+  for (int e = 0; e < n_edges; ++e) {
+    int p = parent_rel[e], ch = child_rel[e];
+    if (p < 0 || p >= n || ch < 0 || ch >= n || p == ch || !key_attr[e])
+      return fail(c, LMF_ERR_ARG, "edge %d: bad relation id", e);
+    if (c->rels[ch].parent != -1) return fail(c, LMF_ERR_NOT_TREE, "relation %d has two parents", ch);
+    c->rels[ch].parent = p;
+    c->rels[ch].key = key_attr[e];
+    c->rels[p].children.push_back(ch);
+  }
+  int root = -1;
+  for (int r = 0; r < n; ++r)
+    if (c->rels[r].parent == -1) {
+      if (root != -1) return fail(c, LMF_ERR_NOT_TREE, "more than one root");
+      root = r;
+    }
+  if (root < 0) return fail(c, LMF_ERR_NOT_TREE, "no root (cycle)");
+  // reachability from the root (no cycles)
+  std::vector<int> seen(n, 0), stack{root};
+  int cnt = 0;
+  while (!stack.empty()) {
+    int r = stack.back();
+    stack.pop_back();
+    if (seen[r]++) return fail(c, LMF_ERR_NOT_TREE, "cycle");
+    ++cnt;
+    for (int ch : c->rels[r].children) stack.push_back(ch);
+  }
+  if (cnt != n) return fail(c, LMF_ERR_NOT_TREE, "edges do not connect all relations");
+  // edge keys: int32 key columns on both sides; no other shared attribute
+  for (int ch = 0; ch < n; ++ch) {
+    RelationH& R = c->rels[ch];
+    if (R.parent < 0) continue;
+    RelationH& P = c->rels[R.parent];
+    int kc = R.find(R.key), kp = P.find(R.key);
+    if (kc < 0 || kp < 0) return fail(c, LMF_ERR_ARG, "edge %s-%s: key %s missing", P.name.c_str(), R.name.c_str(), R.key.c_str());
+    if (R.cols[kc].role != LMF_KEY || P.cols[kp].role != LMF_KEY)
+      return fail(c, LMF_ERR_DTYPE, "edge key %s must have role LMF_KEY on both sides", R.key.c_str());
+    for (auto& col : R.cols)
+      if (col.name != R.key && P.find(col.name) >= 0)
+        return fail(c, LMF_ERR_UNSUPPORTED, "%s and %s share %s besides their edge key", P.name.c_str(),
+                    R.name.c_str(), col.name.c_str());
+  }
+  // running intersection for key names shared by non-adjacent relations: every
+  // relation on the path must carry the name
+  for (int a = 0; a < n; ++a)
+    for (int b = a + 1; b < n; ++b)
+      for (auto& col : c->rels[a].cols) {
+        if (c->rels[b].find(col.name) < 0) continue;
+        // path a -> lca -> b
+        std::vector<int> pa, pb;
+        for (int x = a; x >= 0; x = c->rels[x].parent) pa.push_back(x);
+        for (int x = b; x >= 0; x = c->rels[x].parent) pb.push_back(x);
+        std::set<int> sa(pa.begin(), pa.end());
+        int lca = b;
+        for (int x : pb)
+          if (sa.count(x)) {
+            lca = x;
+            break;
+          }
+        for (int x = a; x != lca; x = c->rels[x].parent)
+          if (c->rels[x].find(col.name) < 0) return fail(c, LMF_ERR_NOT_TREE, "attribute %s breaks running intersection", col.name.c_str());
+        for (int x = b; x != lca; x = c->rels[x].parent)
+          if (c->rels[x].find(col.name) < 0) return fail(c, LMF_ERR_NOT_TREE, "attribute %s breaks running intersection", col.name.c_str());
+        if (c->rels[lca].find(col.name) < 0) return fail(c, LMF_ERR_NOT_TREE, "attribute %s breaks running intersection", col.name.c_str());
+      }
+  // key index of every child: range and multiplicity (A1)
+  int* mm = nullptr;
+  CUDA_TRY(c, cudaMalloc(&mm, 2 * sizeof(int)));
+  for (int ch = 0; ch < n; ++ch) {
+    RelationH& R = c->rels[ch];
+    if (R.parent < 0) continue;
+    const ColumnH& kc = R.cols[R.find(R.key)];
+    if (R.nrows == 0) {
+      R.K = 0;
+      R.max_mult = 0;
+      continue;
+    }
+    int h_mm[2] = {0x7fffffff, -0x7fffffff - 1};
+    CUDA_TRY(c, cudaMemcpy(mm, h_mm, sizeof(h_mm), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, launch_key_stats(static_cast<const int32_t*>(kc.dptr()), R.nrows, nullptr, 0, mm, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(h_mm, mm, sizeof(h_mm), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (h_mm[0] < 0) {
+      cudaFree(mm);
+      return fail(c, LMF_ERR_KEY, "relation %s: negative key %d", R.name.c_str(), h_mm[0]);
+    }
+    if ((int64_t)h_mm[1] >= 4 * R.nrows + 4096) {
+      cudaFree(mm);
+      return fail(c, LMF_ERR_KEY, "relation %s: keys too sparse for direct addressing (max %d, %lld rows)",
+                  R.name.c_str(), h_mm[1], (long long)R.nrows);
+    }
+    R.K = h_mm[1] + 1;
+    unsigned int* hist = nullptr;
+    CUDA_TRY(c, cudaMalloc(&hist, sizeof(unsigned int) * R.K));
+    CUDA_TRY(c, cudaMemsetAsync(hist, 0, sizeof(unsigned int) * R.K, c->stream));
+    CUDA_TRY(c, launch_key_stats(static_cast<const int32_t*>(kc.dptr()), R.nrows, hist, R.K, nullptr, c->stream));
+    std::vector<unsigned int> h(R.K);
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), hist, sizeof(unsigned int) * R.K, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    cudaFree(hist);
+    R.max_mult = (int)*std::max_element(h.begin(), h.end());
+  }
+  cudaFree(mm);
+  c->root = root;
+  c->joined = true;
+  return LMF_OK;
+}
+
+lmf_status lmf_declare_batch(lmf_ctx* c, const lmf_agg_spec* aggs, int n, int* batch_id) {
+  if (!c || n < 0 || (n > 0 && !aggs) || !batch_id) return fail(c, LMF_ERR_ARG, "declare_batch: bad argument");
+  if (!c->joined) return fail(c, LMF_ERR_STATE, "declare_batch before declare_join");
+  auto b = std::make_unique<BatchH>();
+  for (int a = 0; a < n; ++a) {
+    const lmf_agg_spec& s = aggs[a];
+    if (s.n_group_by < 0 || s.n_group_by > LMF_MAX_GROUP_BY || s.n_factors < 0 ||
+        s.n_factors > LMF_MAX_FACTORS || (s.n_factors > 0 && !s.factors))
+      return fail(c, LMF_ERR_ARG, "aggregate %d: bad sizes", a);
+    AggH h;
+    for (int g = 0; g < s.n_group_by; ++g) {
+      if (!s.group_by[g]) return fail(c, LMF_ERR_ARG, "aggregate %d: null group-by", a);
+      int col, r = owner_of(c, s.group_by[g], &col);
+      if (r < 0) return fail(c, LMF_ERR_ARG, "aggregate %d: unknown attribute %s", a, s.group_by[g]);
+      if (c->rels[r].cols[col].role != LMF_CAT)
+        return fail(c, LMF_ERR_DTYPE, "aggregate %d: group-by %s is not categorical", a, s.group_by[g]);
+      h.gb.push_back(s.group_by[g]);
+    }
+    for (int f = 0; f < s.n_factors; ++f) {
+      const lmf_factor& x = s.factors[f];
+      if (!x.attr) return fail(c, LMF_ERR_ARG, "aggregate %d: null factor attribute", a);
+      int col, r = owner_of(c, x.attr, &col);
+      if (r < 0) return fail(c, LMF_ERR_ARG, "aggregate %d: unknown attribute %s", a, x.attr);
+      if (c->rels[r].cols[col].role != LMF_CONT)
+        return fail(c, LMF_ERR_DTYPE, "aggregate %d: factor on non-continuous %s", a, x.attr);
+      if (x.kind == LMF_POW) {
+        if (x.power != 1 && x.power != 2) return fail(c, LMF_ERR_ARG, "aggregate %d: power %d", a, x.power);
+      } else if (x.kind != LMF_LE && x.kind != LMF_GT) {
+        return fail(c, LMF_ERR_ARG, "aggregate %d: factor kind %d", a, x.kind);
+      }
+      h.f.push_back({x.attr, x.kind, x.power, x.threshold});
+    }
+    b->aggs.push_back(std::move(h));
+  }
+  *batch_id = (int)c->batches.size();
+  c->batches.push_back(std::move(b));
+  return LMF_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// planner
+namespace {
+
+struct AggClass {
+  int kind;              // 0 gram, 1 grouped, 2 filtered
+  std::vector<std::string> mono;   // monomial attributes with multiplicity (degree <= 2)
+};
+
+lmf_status classify(lmf_ctx* c, const AggH& a, int idx, AggClass* out) {
+  bool filt = false;
+  out->mono.clear();
+  for (auto& f : a.f) {
+    if (f.kind == LMF_POW) {
+      for (int e = 0; e < f.power; ++e) out->mono.push_back(f.attr);
+    } else {
+      filt = true;
+    }
+  }
+  if (filt) {
+    if (!a.gb.empty()) return fail(c, LMF_ERR_UNSUPPORTED, "aggregate %d: group-by with threshold factors", idx);
+    if (out->mono.size() > 2) return fail(c, LMF_ERR_UNSUPPORTED, "aggregate %d: filtered monomial of degree > 2", idx);
+    out->kind = 2;
+    return LMF_OK;
+  }
+  if (!a.gb.empty()) {
+    if (out->mono.size() > 1)
+      return fail(c, LMF_ERR_UNSUPPORTED, "aggregate %d: grouped monomial of degree > 1", idx);
+    out->kind = 1;
+    return LMF_OK;
+  }
+  if (out->mono.size() > 2) return fail(c, LMF_ERR_UNSUPPORTED, "aggregate %d: monomial of degree > 2", idx);
+  out->kind = 0;
+  return LMF_OK;
+}
+
+// post-order layout of the views
+void layout_rel(lmf_ctx* c, Plan& P, int r, const std::set<std::string>& need_feat,
+                const std::set<std::string>& need_cat) {
+  RelationH& R = c->rels[r];
+  RelPlan& rp = P.rp[r];
+  for (size_t i = 0; i < R.cols.size(); ++i) {
+    if (R.cols[i].role == LMF_CONT && need_feat.count(R.cols[i].name)) rp.own_feat.push_back((int)i);
+    if (R.cols[i].role == LMF_CAT && need_cat.count(R.cols[i].name)) rp.own_cat.push_back((int)i);
+  }
+  // groups: children sharing the FK column name
+  std::vector<std::string> order;
+  std::map<std::string, int> gid;
+  for (int ch : R.children) {
+    const std::string& k = c->rels[ch].key;
+    if (!gid.count(k)) {
+      GroupH g;
+      g.owner = r;
+      g.fk = k;
+      gid[k] = (int)P.groups.size();
+      rp.groups.push_back((int)P.groups.size());
+      P.groups.push_back(g);
+    }
+    P.groups[gid[k]].children.push_back(ch);
+  }
+  for (int gi : rp.groups)
+    for (int ch : P.groups[gi].children) layout_rel(c, P, ch, need_feat, need_cat);
+  // own section
+  rp.unique = (r == c->root) || R.max_mult <= 1;
+  rp.maxcnt = (r == c->root) ? 1.0 : std::max(1, R.max_mult);
+  for (int i : rp.own_feat) rp.feat_names.push_back(R.cols[i].name);
+  for (int i : rp.own_cat) rp.cat_names.push_back(R.cols[i].name);
+  for (int gi : rp.groups) {
+    GroupH& g = P.groups[gi];
+    g.n_cnt = (int)g.children.size();
+    g.n_mu = 0;
+    g.n_cat = 0;
+    g.K = 0;
+    for (size_t q = 0; q < g.children.size(); ++q) {
+      int ch = g.children[q];
+      RelPlan& cp = P.rp[ch];
+      cp.group = gi;
+      cp.slot = (int)q;
+      g.child_mu_off.push_back(g.n_cnt + g.n_mu);
+      g.n_mu += cp.d;
+      g.K = std::max(g.K, c->rels[ch].K);
+      rp.unique = rp.unique && cp.unique;
+      rp.maxcnt *= cp.maxcnt;
+      for (auto& f : cp.feat_names) rp.feat_names.push_back(f);
+    }
+    for (size_t q = 0; q < g.children.size(); ++q) {
+      int ch = g.children[q];
+      RelPlan& cp = P.rp[ch];
+      g.child_cat_off.push_back(g.n_cnt + g.n_mu + g.n_cat);
+      g.n_cat += cp.ncat;
+      for (auto& f : cp.cat_names) rp.cat_names.push_back(f);
+    }
+    g.stride = (g.n_cnt + g.n_mu + g.n_cat + 3) & ~3;
+  }
+  rp.d = (int)rp.feat_names.size();
+  rp.ncat = (int)rp.cat_names.size();
+  if (r != c->root) P.post.push_back(r);
+}
+
+}  // namespace
+
+extern "C" lmf_status lmf_plan(lmf_ctx* c, int batch_id, const lmf_plan_opts* opts) {
+  if (!c || batch_id < 0 || batch_id >= (int)c->batches.size()) return fail(c, LMF_ERR_ARG, "plan: bad batch id");
+  cudaSetDevice(c->device);
+  BatchH& B = *c->batches[batch_id];
+  if (B.plan) {
+    cudaStreamSynchronize(c->stream);
+    free_plan(B.plan.get());
+    B.plan.reset();
+  }
+  auto P = std::make_unique<Plan>();
+  if (opts) {
+    P->opts = *opts;
+  } else {
+    P->opts.precision = LMF_PREC_SPLIT_BF16;
+    P->opts.batching = LMF_BATCH_GRAPH;
+  }
+  const int nrel = (int)c->rels.size();
+  const int root = c->root;
+  RelationH& Root = c->rels[root];
+
+  // ---- classify aggregates; needed features and categories
+  std::vector<AggClass> cls(B.aggs.size());
+  std::set<std::string> need_feat, need_cat;
+  for (size_t a = 0; a < B.aggs.size(); ++a) {
+    lmf_status s = classify(c, B.aggs[a], (int)a, &cls[a]);
+    if (s) return s;
+    for (auto& m : cls[a].mono) need_feat.insert(m);
+    for (auto& g : B.aggs[a].gb) need_cat.insert(g);
+    for (auto& f : B.aggs[a].f) need_feat.insert(f.attr);
+  }
+  P->rp.resize(nrel);
+  layout_rel(c, *P, root, need_feat, need_cat);
+  RelPlan& RR = P->rp[root];
+
+  // ---- z layout: [1, root features, root groups' means]
+  int m = 1;
+  for (int i : RR.own_feat) P->zidx[Root.cols[i].name] = m++;
+  int ncat = 0;
+  for (size_t q = 0; q < RR.groups.size(); ++q) {
+    GroupH& g = P->groups[RR.groups[q]];
+    int word = g.n_cnt;
+    for (size_t k = 0; k < g.children.size(); ++k) {
+      for (auto& f : P->rp[g.children[k]].feat_names) {
+        P->zidx[f] = m++;
+        P->feat_group[f] = (int)q;
+        ++word;
+      }
+    }
+    for (size_t k = 0; k < g.children.size(); ++k)
+      for (auto& f : P->rp[g.children[k]].cat_names) {
+        P->catword[f] = {(int)q, word++};
+        P->rowcat[f] = ncat++;
+      }
+  }
+  for (int i : RR.own_cat) {
+    P->rowcat[Root.cols[i].name] = ncat++;
+    P->catword[Root.cols[i].name] = {-1, -1};
+  }
+  for (int i : RR.own_feat) P->feat_group[Root.cols[i].name] = -1;
+  if (m > kMaxZ) return fail(c, LMF_ERR_UNSUPPORTED, "batch needs %d features, at most %d", m - 1, kMaxZ - 1);
+  if (ncat > kMaxCat) return fail(c, LMF_ERR_UNSUPPORTED, "batch needs %d categories, at most %d", ncat, kMaxCat);
+  if (RR.groups.size() > (size_t)kMaxGroups) return fail(c, LMF_ERR_UNSUPPORTED, "too many join keys at the root");
+  for (int r = 0; r < nrel; ++r) {
+    if ((int)P->rp[r].own_feat.size() > kMaxOwn || (int)P->rp[r].own_cat.size() > kMaxCat ||
+        P->rp[r].groups.size() > (size_t)kMaxGroups || P->rp[r].d > kMaxZ)
+      return fail(c, LMF_ERR_UNSUPPORTED, "relation %s: too many columns in one view", c->rels[r].name.c_str());
+    if (r != root && !P->rp[r].unique && P->rp[r].ncat > 0)
+      return fail(c, LMF_ERR_UNSUPPORTED, "group-by attribute below the fanning-out key of %s", c->rels[r].name.c_str());
+  }
+  for (int r : P->post)
+    if (!P->rp[r].unique) P->unique_all = false;
+
+  // ---- value bounds of every needed continuous column (fixed-point scales)
+  std::map<std::string, double> bound;
+  {
+    std::vector<Col> cols;
+    std::vector<std::string> names;
+    std::vector<int64_t> rows;
+    for (int r = 0; r < nrel; ++r)
+      for (auto& col : c->rels[r].cols)
+        if (col.role == LMF_CONT && need_feat.count(col.name)) {
+          cols.push_back({col.dptr(), col.dtype == LMF_F64 ? 2 : 1});
+          names.push_back(col.name);
+          rows.push_back(c->rels[r].nrows);
+        }
+    if (!cols.empty()) {
+      double* d = nullptr;
+      CUDA_TRY(c, cudaMalloc(&d, sizeof(double) * cols.size()));
+      CUDA_TRY(c, cudaMemsetAsync(d, 0, sizeof(double) * cols.size(), c->stream));
+      for (size_t i = 0; i < cols.size(); ++i) CUDA_TRY(c, launch_colmaxabs(&cols[i], 1, rows[i], d + i, c->stream));
+      std::vector<double> h(cols.size());
+      CUDA_TRY(c, cudaMemcpyAsync(h.data(), d, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      cudaFree(d);
+      for (size_t i = 0; i < h.size(); ++i) bound[names[i]] = h[i];
+    }
+  }
+  const double W = std::max<double>(1.0, (double)Root.nrows) * RR.maxcnt;  // bound on sum of w
+
+  // ---- arena layout
+  Arena& A = P->arena;
+  A.take(0);
+  // zero region first: everything that must start at zero every run
+  size_t zero_begin = A.take(0);
+  for (auto& g : P->groups) g.rec_off = A.take((size_t)g.K * g.stride * 4);
+  for (int r : P->post) {
+    RelPlan& rp = P->rp[r];
+    if (rp.unique) continue;
+    int K = P->groups[rp.group].K;
+    int dq = rp.d * (rp.d + 1) / 2;
+    rp.cnt64_off = A.take((size_t)K * 8);
+    rp.S_off = A.take((size_t)K * rp.d * 8 + 8);
+    rp.Q_off = A.take((size_t)K * dq * 8 + 8);
+  }
+  P->status_off = A.take(16);
+
+  // ---- root parameters
+  RootParams& rp = P->rootp;
+  rp.N = Root.nrows;
+  rp.m = m;
+  rp.n_grp = (int)RR.groups.size();
+  {
+    int zoff = 1 + (int)RR.own_feat.size(), coff = 0;
+    for (int q = 0; q < rp.n_grp; ++q) {
+      GroupH& g = P->groups[RR.groups[q]];
+      rp.grp_zoff[q] = zoff;
+      rp.grp_catoff[q] = coff;
+      zoff += g.n_mu;
+      coff += g.n_cat;
+    }
+  }
+  rp.n_x = (int)RR.own_feat.size();
+  for (int i = 0; i < rp.n_x; ++i) {
+    const ColumnH& col = Root.cols[RR.own_feat[i]];
+    rp.x[i] = {col.dptr(), col.dtype == LMF_F64 ? 2 : 1};
+  }
+  rp.n_rcat = (int)RR.own_cat.size();
+  for (int i = 0; i < rp.n_rcat; ++i) {
+    rp.rcat[i] = static_cast<const int32_t*>(Root.cols[RR.own_cat[i]].dptr());
+    rp.rcat_dom[i] = Root.cols[RR.own_cat[i]].dom;
+  }
+  rp.n_rowcat = ncat;
+
+  // ---- grouped aggregates
+  std::vector<size_t> rv_hist_off(rp.n_grp, 0), rv_R_off(rp.n_grp, 0);
+  std::vector<std::vector<int>> rv_slots(rp.n_grp);     // z index per slot
+  std::vector<int> rv_used(rp.n_grp, 0);
+  struct GPlan { int mode; int grp; int slot; int mu_word; int direct; double scale; int64_t cells; size_t out_off; };
+  std::vector<GPlan> gplan(B.aggs.size());
+  for (size_t a = 0; a < B.aggs.size(); ++a) {
+    if (cls[a].kind != 1) continue;
+    const AggH& ag = B.aggs[a];
+    int64_t cells = 1;
+    int gsrc = -2;
+    for (auto& g : ag.gb) {
+      int col, r = owner_of(c, g, &col);
+      cells *= c->rels[r].cols[col].dom;
+      int q = P->catword.at(g).first;
+      gsrc = (gsrc == -2 || gsrc == q) ? q : -3;
+    }
+    GPlan gp{};
+    gp.cells = cells;
+    gp.direct = (gsrc < 0) ? 1 : 0;   // root categories or several keys: per-row table
+    std::string f = cls[a].mono.empty() ? "" : cls[a].mono[0];
+    gp.scale = f.empty() ? 1.0 : std::ldexp(1.0, fixp_exp(W * bound[f]));
+    if (!gp.direct) {
+      gp.grp = gsrc;
+      rv_used[gsrc] = 1;
+      if (f.empty()) {
+        gp.mode = 0;
+      } else if (P->feat_group.at(f) == gsrc) {
+        gp.mode = 2;
+        GroupH& g = P->groups[RR.groups[gsrc]];
+        gp.mu_word = g.n_cnt + (P->zidx.at(f) - rp.grp_zoff[gsrc]);
+      } else {
+        gp.mode = 1;
+        auto& sl = rv_slots[gsrc];
+        int z = P->zidx.at(f);
+        auto it = std::find(sl.begin(), sl.end(), z);
+        gp.slot = (int)(it - sl.begin());
+        if (it == sl.end()) sl.push_back(z);
+      }
+    }
+    gplan[a] = gp;
+    ++P->n_grouped;
+  }
+  for (int q = 0; q < rp.n_grp; ++q) {
+    if (!rv_used[q]) continue;
+    GroupH& g = P->groups[RR.groups[q]];
+    rv_hist_off[q] = A.take((size_t)g.K * 8);
+    rv_R_off[q] = A.take((size_t)g.K * rv_slots[q].size() * 8 + 8);
+  }
+  for (size_t a = 0; a < B.aggs.size(); ++a)
+    if (cls[a].kind == 1) gplan[a].out_off = A.take((size_t)gplan[a].cells * 8);
+  // omega accumulators of fanning-out root children
+  std::vector<std::pair<int, size_t>> omega;  // child relation, offset
+  for (int q = 0; q < rp.n_grp; ++q)
+    for (int ch : P->groups[RR.groups[q]].children)
+      if (!P->rp[ch].unique) omega.push_back({ch, A.take((size_t)P->groups[RR.groups[q]].K * 8)});
+  // tree-node (filtered) batches
+  std::vector<int> filt_idx;
+  for (size_t a = 0; a < B.aggs.size(); ++a)
+    if (cls[a].kind == 2) filt_idx.push_back((int)a);
+  if (!filt_idx.empty()) {
+    P->tree = std::make_unique<TreePlan>();
+    std::vector<TreeAggIn> in;
+    for (int a : filt_idx) {
+      TreeAggIn t;
+      for (auto& f : B.aggs[a].f) {
+        TreeFactorIn x{f.attr, f.kind, f.power, f.thr};
+        t.factors.push_back(x);
+      }
+      in.push_back(t);
+    }
+    std::string msg;
+    lmf_status s = tree_plan(in, P->zidx, P->tree.get(), &msg);
+    if (s) return fail(c, s, "%s", msg.c_str());
+    P->n_filtered = (int)filt_idx.size();
+  }
+  if (P->tree) tree_alloc_zeroed(P->tree.get(), [&](size_t n) { return A.take(n); });
+  P->zero_off = zero_begin;
+  P->zero_len = A.take(0) - zero_begin;
+  // within-key scatter of fanning-out views: fully rewritten by every run
+  for (int r : P->post) {
+    RelPlan& cp = P->rp[r];
+    if (cp.unique) continue;
+    cp.sc_off = A.take((size_t)P->groups[cp.group].K * (cp.d * (cp.d + 1) / 2) * 8 + 8);
+  }
+
+  // root scan shape
+  int mp = 16;
+  while (mp < m) mp += 16;
+  P->mp = mp;
+  const int T = root_plain_tile_rows();
+  P->n_tiles = (Root.nrows + T - 1) / T;
+  P->smem = root_plain_smem(mp, ncat);
+  int cps = P->opts.ctas_per_sm > 0 ? P->opts.ctas_per_sm : (mp <= 32 ? 2 : 1);
+  P->grid = (int)std::max<int64_t>(1, std::min<int64_t>(P->n_tiles, (int64_t)c->num_sms * cps));
+  CUDA_TRY(c, root_plain_prepare(mp, P->smem));
+  bool use_tc = P->opts.precision == LMF_PREC_SPLIT_BF16 && gram_tc_supported(m);
+  if (P->opts.precision == LMF_PREC_SPLIT_BF16 && !use_tc) P->opts.precision = LMF_PREC_PLAIN_FP32;
+  if (use_tc) {
+    P->tc = std::make_unique<GramTcPlan>();
+    gram_tc_shape(m, Root.nrows, c->num_sms, P->opts.tile_rows, P->tc.get());
+    P->grid = P->tc->grid;
+  }
+  P->part_off = A.take((size_t)P->grid * mp * mp * 8);
+  P->cntp_off = A.take((size_t)P->grid * 8);
+  P->G_off = A.take((size_t)m * m * 8);
+  P->count_off = A.take(8);
+  if (use_tc) gram_tc_alloc(P->tc.get(), [&](size_t n) { return A.take(n); });
+  if (P->tree) tree_alloc(P->tree.get(), [&](size_t n) { return A.take(n); });
+
+  // results
+  P->agg_dtype.resize(B.aggs.size());
+  P->agg_off.resize(B.aggs.size());
+  P->agg_n.resize(B.aggs.size());
+  for (size_t a = 0; a < B.aggs.size(); ++a) {
+    bool is_count = cls[a].mono.empty();
+    int64_t cells = cls[a].kind == 1 ? gplan[a].cells : 1;
+    P->agg_dtype[a] = is_count ? LMF_I64 : LMF_F64;
+    P->agg_n[a] = cells;
+    if (is_count) {
+      P->agg_off[a] = P->n_i64;
+      P->n_i64 += cells;
+    } else {
+      P->agg_off[a] = P->n_f64;
+      P->n_f64 += cells;
+    }
+  }
+  P->res_i64_off = A.take((size_t)std::max<int64_t>(1, P->n_i64) * 8);
+  P->res_f64_off = A.take((size_t)std::max<int64_t>(1, P->n_f64) * 8);
+  // device tables
+  size_t n_rvt_est = B.aggs.size() + 1;
+  P->rvtask_off = A.take(sizeof(RvTask) * n_rvt_est);
+  P->direct_off = A.take(sizeof(DirectAgg) * n_rvt_est);
+  P->corr_off = A.take(sizeof(CorrTask) * (omega.size() + 1));
+  P->maps_off = A.take(sizeof(OutMap) * (B.aggs.size() + 1));
+
+  // ---- allocate
+  A.size = A.used + 256;
+  {
+    void* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, A.size);
+    if (e != cudaSuccess) return fail(c, LMF_ERR_OOM, "plan arena of %zu bytes", A.size);
+    A.base = static_cast<char*>(base);
+  }
+
+  // ---- fill device descriptors
+  auto gdesc = [&](int gi) {
+    GroupH& g = P->groups[gi];
+    const RelationH& O = c->rels[g.owner];
+    GroupDesc d;
+    d.fk = static_cast<const int32_t*>(O.cols[O.find(g.fk)].dptr());
+    d.rec = P->at<uint32_t>(g.rec_off);
+    d.K = g.K;
+    d.stride = g.stride;
+    d.n_cnt = g.n_cnt;
+    d.n_mu = g.n_mu;
+    d.n_cat = g.n_cat;
+    return d;
+  };
+  for (int q = 0; q < rp.n_grp; ++q) rp.grp[q] = gdesc(RR.groups[q]);
+  rp.gram_part = P->at<double>(P->part_off);
+  rp.cnt_part = P->at<long long>(P->cntp_off);
+  rp.status = P->at<uint32_t>(P->status_off);
+  rp.n_rv = 0;
+  std::vector<int> rv_index(rp.n_grp, -1);
+  for (int q = 0; q < rp.n_grp; ++q) {
+    if (!rv_used[q]) continue;
+    if ((int)rv_slots[q].size() > kMaxZ) return fail(c, LMF_ERR_UNSUPPORTED, "too many reverse-view slots");
+    RevView& R = rp.rv[rp.n_rv];
+    R.hist = P->at<unsigned long long>(rv_hist_off[q]);
+    R.R = P->at<long long>(rv_R_off[q]);
+    R.grp = q;
+    R.n_slot = (int)rv_slots[q].size();
+    for (int s = 0; s < R.n_slot; ++s) {
+      R.slot_z[s] = (int16_t)rv_slots[q][s];
+      std::string fname;
+      for (auto& kv : P->zidx)
+        if (kv.second == rv_slots[q][s]) fname = kv.first;
+      R.slot_scale[s] = (float)std::ldexp(1.0, fixp_exp(W * bound[fname]));
+    }
+    rv_index[q] = rp.n_rv++;
+  }
+  std::vector<RvTask> tasks;
+  std::vector<DirectAgg> direct;
+  for (size_t a = 0; a < B.aggs.size(); ++a) {
+    if (cls[a].kind != 1) continue;
+    const GPlan& gp = gplan[a];
+    const AggH& ag = B.aggs[a];
+    std::string f = cls[a].mono.empty() ? "" : cls[a].mono[0];
+    if (gp.direct) {
+      DirectAgg d{};
+      d.n_gb = (int)ag.gb.size();
+      for (int q = 0; q < d.n_gb; ++q) {
+        int col, r = owner_of(c, ag.gb[q], &col);
+        d.cat[q] = P->rowcat.at(ag.gb[q]);
+        d.dom[q] = c->rels[r].cols[col].dom;
+      }
+      d.z = f.empty() ? -1 : P->zidx.at(f);
+      d.scale = (float)gp.scale;
+      d.out = P->at<long long>(gp.out_off);
+      direct.push_back(d);
+    } else {
+      RvTask t{};
+      t.rv = rv_index[gp.grp];
+      t.n_gb = (int)ag.gb.size();
+      for (int q = 0; q < t.n_gb; ++q) {
+        int col, r = owner_of(c, ag.gb[q], &col);
+        t.cat_word[q] = P->catword.at(ag.gb[q]).second;
+        t.dom[q] = c->rels[r].cols[col].dom;
+      }
+      t.mode = gp.mode;
+      t.slot = gp.slot;
+      t.mu_word = gp.mu_word;
+      t.scale = (float)gp.scale;
+      t.out = P->at<long long>(gp.out_off);
+      tasks.push_back(t);
+      P->max_group_K = std::max(P->max_group_K, P->groups[RR.groups[gp.grp]].K);
+    }
+  }
+  P->rv_tasks = tasks;
+  P->direct = direct;
+  rp.n_direct = (int)direct.size();
+  rp.direct = P->at<DirectAgg>(P->direct_off);
+  rp.n_om = 0;
+  std::vector<CorrTask> corr;
+  for (auto& o : omega) {
+    int ch = o.first;
+    RelPlan& cp = P->rp[ch];
+    int q = 0;
+    for (; q < rp.n_grp; ++q)
+      if (RR.groups[q] == cp.group) break;
+    OmegaAcc& O = rp.om[rp.n_om++];
+    O.grp = q;
+    O.cnt_word = cp.slot;
+    O.omega = P->at<unsigned long long>(o.second);
+    CorrTask t;
+    t.omega = O.omega;
+    t.sc = P->at<double>(cp.sc_off);
+    t.K = P->groups[cp.group].K;
+    t.d = cp.d;
+    t.zoff = rp.grp_zoff[q] + (P->groups[cp.group].child_mu_off[cp.slot] - P->groups[cp.group].n_cnt);
+    corr.push_back(t);
+  }
+  // out maps
+  std::vector<OutMap> maps;
+  for (size_t a = 0; a < B.aggs.size(); ++a) {
+    OutMap o{};
+    o.dst = P->agg_off[a];
+    o.n = P->agg_n[a];
+    if (cls[a].kind == 0) {
+      const auto& mo = cls[a].mono;
+      if (mo.empty()) {
+        o.kind = 0;
+      } else {
+        o.kind = 1;
+        o.i = mo.size() == 2 ? P->zidx.at(mo[0]) : 0;
+        o.j = P->zidx.at(mo.back());
+        if (o.i > o.j) std::swap(o.i, o.j);
+        ++P->n_gram;
+      }
+    } else if (cls[a].kind == 1) {
+      o.kind = cls[a].mono.empty() ? 2 : 3;
+      o.src = P->at<long long>(gplan[a].out_off);
+      o.inv_scale = 1.0 / gplan[a].scale;
+    } else {
+      continue;  // filtered aggregates are placed by the tree kernels
+    }
+    maps.push_back(o);
+  }
+  P->maps = maps;
+  P->corr = corr;
+  CUDA_TRY(c, cudaMemcpy(P->arena.base + P->rvtask_off, tasks.data(), sizeof(RvTask) * tasks.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(P->arena.base + P->direct_off, direct.data(), sizeof(DirectAgg) * direct.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(P->arena.base + P->corr_off, corr.data(), sizeof(CorrTask) * corr.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(P->arena.base + P->maps_off, maps.data(), sizeof(OutMap) * maps.size(), cudaMemcpyHostToDevice));
+
+  // general-path scales
+  for (int r : P->post) {
+    RelPlan& cp = P->rp[r];
+    if (cp.unique) continue;
+    double Wc = std::max<double>(1.0, (double)c->rels[r].nrows) * cp.maxcnt;
+    double bmax = 0;
+    for (int i = 0; i < cp.d; ++i) {
+      double b = bound[cp.feat_names[i]];
+      cp.s_scale[i] = (float)std::ldexp(1.0, fixp_exp(Wc * b));
+      bmax = std::max(bmax, b);
+    }
+    cp.q_scale = std::ldexp(1.0, fixp_exp(Wc * bmax * bmax));
+  }
+  if (P->tree) {
+    lmf_status s = tree_finish(P->tree.get(), P->arena.base, P->at<long long>(P->res_i64_off),
+                               P->at<double>(P->res_f64_off), P->agg_off, filt_idx, P->agg_dtype,
+                               P->at<uint32_t>(P->status_off), Root.nrows, c->num_sms, bound, W, rp);
+    if (s) return fail(c, s, "tree plan: device tables");
+  }
+  if (use_tc) {
+    gram_tc_finish(P->tc.get(), rp, P->arena.base);
+  }
+  P->n_views = (int)P->post.size();
+  B.plan = std::move(P);
+  return LMF_OK;
+}
+
+namespace {
+
+lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s) {
+  Plan* P = B.plan.get();
+  int nk = 0;
+  // host-resident columns are copied in first
+  for (auto& r : c->rels)
+    for (auto& col : r.cols)
+      if (col.on_host && r.nrows > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(col.dev, col.data, (size_t)r.nrows * col.esize(), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaMemsetAsync(P->arena.base + P->zero_off, 0, P->zero_len, s));
+  // child views, deepest first
+  for (int r : P->post) {
+    RelPlan& cp = P->rp[r];
+    const RelationH& R = c->rels[r];
+    GroupH& g = P->groups[cp.group];
+    ViewArgs a{};
+    a.nrows = R.nrows;
+    a.key = static_cast<const int32_t*>(R.cols[R.find(R.key)].dptr());
+    a.K = g.K;
+    a.dst = P->at<uint32_t>(g.rec_off);
+    a.dst_stride = g.stride;
+    a.cnt_word = cp.slot;
+    a.mu_off = g.child_mu_off[cp.slot];
+    a.cat_off = g.child_cat_off[cp.slot];
+    a.n_own = (int)cp.own_feat.size();
+    for (int i = 0; i < a.n_own; ++i)
+      a.own[i] = {R.cols[cp.own_feat[i]].dptr(), R.cols[cp.own_feat[i]].dtype == LMF_F64 ? 2 : 1};
+    a.n_owncat = (int)cp.own_cat.size();
+    for (int i = 0; i < a.n_owncat; ++i) {
+      a.owncat[i] = static_cast<const int32_t*>(R.cols[cp.own_cat[i]].dptr());
+      a.owncat_dom[i] = R.cols[cp.own_cat[i]].dom;
+    }
+    a.n_grp = (int)cp.groups.size();
+    for (int q = 0; q < a.n_grp; ++q) {
+      GroupH& cg = P->groups[cp.groups[q]];
+      GroupDesc d;
+      d.fk = static_cast<const int32_t*>(R.cols[R.find(cg.fk)].dptr());
+      d.rec = P->at<uint32_t>(cg.rec_off);
+      d.K = cg.K;
+      d.stride = cg.stride;
+      d.n_cnt = cg.n_cnt;
+      d.n_mu = cg.n_mu;
+      d.n_cat = cg.n_cat;
+      a.grp[q] = d;
+    }
+    a.status = P->at<uint32_t>(P->status_off);
+    if (cp.unique) {
+      CUDA_TRY(c, launch_view_unique(a, s));
+      ++nk;
+      continue;
+    }
+    a.d = cp.d;
+    a.dq = cp.d * (cp.d + 1) / 2;
+    a.cnt64 = P->at<unsigned long long>(cp.cnt64_off);
+    a.S = P->at<long long>(cp.S_off);
+    a.Q = P->at<long long>(cp.Q_off);
+    for (int i = 0; i < cp.d; ++i) a.s_scale[i] = cp.s_scale[i];
+    a.q_scale = cp.q_scale;
+    a.n_sc = 0;
+    int f0 = (int)cp.own_feat.size();
+    for (int q = 0; q < a.n_grp; ++q) {
+      GroupH& cg = P->groups[cp.groups[q]];
+      for (size_t k = 0; k < cg.children.size(); ++k) {
+        RelPlan& ep = P->rp[cg.children[k]];
+        if (!ep.unique) {
+          a.sc[a.n_sc] = P->at<double>(ep.sc_off);
+          a.sc_grp[a.n_sc] = q;
+          a.sc_cntword[a.n_sc] = (int)k;
+          a.sc_feat0[a.n_sc] = f0;
+          a.sc_d[a.n_sc] = ep.d;
+          ++a.n_sc;
+        }
+        f0 += ep.d;
+      }
+    }
+    CUDA_TRY(c, launch_view_general(a, s));
+    ViewFinalizeArgs f{};
+    f.K = g.K;
+    f.d = cp.d;
+    f.dq = a.dq;
+    f.cnt64 = a.cnt64;
+    f.S = a.S;
+    f.Q = a.Q;
+    for (int i = 0; i < cp.d; ++i) f.s_scale[i] = cp.s_scale[i];
+    f.q_scale = cp.q_scale;
+    f.dst = a.dst;
+    f.dst_stride = g.stride;
+    f.cnt_word = cp.slot;
+    f.mu_off = a.mu_off;
+    f.sc = P->at<double>(cp.sc_off);
+    f.status = a.status;
+    CUDA_TRY(c, launch_view_finalize(f, s));
+    nk += 2;
+  }
+  // root scan: Gram, counts, reverse views, per-row grouped tables
+  if (P->tc) {
+    CUDA_TRY(c, gram_tc_launch(P->tc.get(), P->rootp, s));
+    nk += 1;
+  } else {
+    CUDA_TRY(c, launch_root_plain(P->rootp, P->mp, P->grid, P->n_tiles, P->smem, s));
+    ++nk;
+  }
+  if (P->tree) {
+    CUDA_TRY(c, tree_launch(P->tree.get(), P->rootp, s, &nk));
+  }
+  CUDA_TRY(c, launch_combine(P->at<double>(P->part_off), P->grid, P->mp, P->rootp.m,
+                             P->at<long long>(P->cntp_off), P->at<double>(P->G_off),
+                             P->at<long long>(P->count_off), s));
+  ++nk;
+  if (!P->corr.empty()) {
+    CUDA_TRY(c, launch_corr(P->arena.base + P->corr_off, (int)P->corr.size(), P->at<double>(P->G_off), P->rootp.m, s));
+    ++nk;
+  }
+  if (!P->rv_tasks.empty()) {
+    CUDA_TRY(c, launch_rv_tasks(P->at<RvTask>(P->rvtask_off), (int)P->rv_tasks.size(), P->rootp, P->max_group_K, s));
+    ++nk;
+  }
+  if (!P->maps.empty()) {
+    CUDA_TRY(c, launch_out_map(P->at<OutMap>(P->maps_off), (int)P->maps.size(), P->at<double>(P->G_off), P->rootp.m,
+                               P->at<long long>(P->count_off), P->at<long long>(P->res_i64_off),
+                               P->at<double>(P->res_f64_off), s));
+    ++nk;
+  }
+  P->n_kernels = nk;
+  return LMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lmf_status lmf_plan_info(lmf_ctx* c, int batch_id, lmf_plan_stats* info) {
+  if (!c || !info || batch_id < 0 || batch_id >= (int)c->batches.size()) return LMF_ERR_ARG;
+  Plan* P = c->batches[batch_id]->plan.get();
+  if (!P) return fail(c, LMF_ERR_STATE, "batch not planned");
+  std::memset(info, 0, sizeof(*info));
+  info->n_views = P->n_views;
+  info->n_probe_groups = P->rootp.n_grp;
+  info->z_len = P->rootp.m;
+  info->n_gram_aggs = P->n_gram;
+  info->n_grouped_aggs = P->n_grouped;
+  info->n_filtered_aggs = P->n_filtered;
+  info->n_kernels_per_run = P->n_kernels;
+  info->unique_keys = P->unique_all ? 1 : 0;
+  info->root_grid = P->grid;
+  info->precision = P->tc ? LMF_PREC_SPLIT_BF16 : LMF_PREC_PLAIN_FP32;
+  info->root_rows = P->rootp.N;
+  info->scratch_bytes = (int64_t)P->arena.size;
+  return LMF_OK;
+}
+
+lmf_status lmf_run(lmf_ctx* c, int batch_id, void* cuda_stream) {
+  if (!c || batch_id < 0 || batch_id >= (int)c->batches.size()) return fail(c, LMF_ERR_ARG, "run: bad batch id");
+  BatchH& B = *c->batches[batch_id];
+  Plan* P = B.plan.get();
+  if (!P) return fail(c, LMF_ERR_STATE, "run before plan");
+  cudaSetDevice(c->device);
+  cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
+  B.last_stream = s;
+  if (P->opts.batching == LMF_BATCH_GRAPH) {
+    if (!P->exec) {
+      if (!P->graph_stream) CUDA_TRY(c, cudaStreamCreateWithFlags(&P->graph_stream, cudaStreamNonBlocking));
+      CUDA_TRY(c, cudaStreamBeginCapture(P->graph_stream, cudaStreamCaptureModeThreadLocal));
+      lmf_status st = enqueue(c, B, P->graph_stream);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(P->graph_stream, &g);
+      if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return fail(c, LMF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+      P->graph = g;
+      CUDA_TRY(c, cudaGraphInstantiate(&P->exec, g, 0));
+    }
+    CUDA_TRY(c, cudaGraphLaunch(P->exec, s));
+    return LMF_OK;
+  }
+  return enqueue(c, B, s);
+}
+
+lmf_status lmf_sync(lmf_ctx* c, int batch_id) {
+  if (!c || batch_id < 0 || batch_id >= (int)c->batches.size()) return fail(c, LMF_ERR_ARG, "sync: bad batch id");
+  BatchH& B = *c->batches[batch_id];
+  Plan* P = B.plan.get();
+  if (!P) return fail(c, LMF_ERR_STATE, "sync before plan");
+  cudaSetDevice(c->device);
+  cudaStream_t s = B.last_stream ? B.last_stream : c->stream;
+  uint32_t st = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&st, P->arena.base + P->status_off, sizeof(st), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(c, cudaStreamSynchronize(s));
+  if (st & kStatusTimeout) return fail(c, LMF_ERR_TIMEOUT, "a device wait gave up");
+  if (st & kStatusOverflow) return fail(c, LMF_ERR_OVERFLOW, "a subtree count exceeded int32");
+  if (st & (kStatusCatRange | kStatusKeyRange)) return fail(c, LMF_ERR_KEY, "category or key out of range (status %u)", st);
+  return LMF_OK;
+}
+
+lmf_status lmf_result_info(lmf_ctx* c, int batch_id, int agg, int64_t* n_groups, int32_t* dtype, int64_t* offset) {
+  if (!c || batch_id < 0 || batch_id >= (int)c->batches.size()) return LMF_ERR_ARG;
+  Plan* P = c->batches[batch_id]->plan.get();
+  if (!P) return fail(c, LMF_ERR_STATE, "batch not planned");
+  if (agg < 0 || agg >= (int)P->agg_n.size()) return fail(c, LMF_ERR_ARG, "bad aggregate index");
+  if (n_groups) *n_groups = P->agg_n[agg];
+  if (dtype) *dtype = P->agg_dtype[agg];
+  if (offset) *offset = P->agg_off[agg];
+  return LMF_OK;
+}
+
+lmf_status lmf_result_sizes(lmf_ctx* c, int batch_id, int64_t* n_i64, int64_t* n_f64) {
+  if (!c || batch_id < 0 || batch_id >= (int)c->batches.size()) return LMF_ERR_ARG;
+  Plan* P = c->batches[batch_id]->plan.get();
+  if (!P) return fail(c, LMF_ERR_STATE, "batch not planned");
+  if (n_i64) *n_i64 = P->n_i64;
+  if (n_f64) *n_f64 = P->n_f64;
+  return LMF_OK;
+}
+
+lmf_status lmf_read_results(lmf_ctx* c, int batch_id, int64_t* dst_i64, double* dst_f64, int dst_is_device,
+                            void* cuda_stream) {
+  if (!c || batch_id < 0 || batch_id >= (int)c->batches.size()) return LMF_ERR_ARG;
+  BatchH& B = *c->batches[batch_id];
+  Plan* P = B.plan.get();
+  if (!P) return fail(c, LMF_ERR_STATE, "batch not planned");
+  cudaSetDevice(c->device);
+  cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : (B.last_stream ? B.last_stream : c->stream);
+  cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (dst_i64 && P->n_i64 > 0)
+    CUDA_TRY(c, cudaMemcpyAsync(dst_i64, P->arena.base + P->res_i64_off, P->n_i64 * 8, k, s));
+  if (dst_f64 && P->n_f64 > 0)
+    CUDA_TRY(c, cudaMemcpyAsync(dst_f64, P->arena.base + P->res_f64_off, P->n_f64 * 8, k, s));
+  if (!dst_is_device) CUDA_TRY(c, cudaStreamSynchronize(s));
+  return LMF_OK;
+}
+
+lmf_status lmf_read_result(lmf_ctx* c, int batch_id, int agg, void* dst) {
+  if (!c || !dst || batch_id < 0 || batch_id >= (int)c->batches.size()) return LMF_ERR_ARG;
+  BatchH& B = *c->batches[batch_id];
+  Plan* P = B.plan.get();
+  if (!P) return fail(c, LMF_ERR_STATE, "batch not planned");
+  if (agg < 0 || agg >= (int)P->agg_n.size()) return fail(c, LMF_ERR_ARG, "bad aggregate index");
+  cudaSetDevice(c->device);
+  cudaStream_t s = B.last_stream ? B.last_stream : c->stream;
+  size_t base = P->agg_dtype[agg] == LMF_I64 ? P->res_i64_off : P->res_f64_off;
+  CUDA_TRY(c, cudaMemcpyAsync(dst, P->arena.base + base + P->agg_off[agg] * 8, P->agg_n[agg] * 8,
+                              cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(c, cudaStreamSynchronize(s));
+  return LMF_OK;
+}
+
+}  // extern "C"

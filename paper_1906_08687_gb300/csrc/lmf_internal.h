@@ -1,0 +1,200 @@
+// lmf_internal.h -- plan structures shared by the host planner (lmf_api.cu)
+// and the device kernels (lmf_kernels.cu, lmf_gram_tc.cu, lmf_tree.cu).
+//
+// Vocabulary follows the paper: a *view* is the directional view of a child
+// relation towards its parent (Sec. 3.2), keyed by the join key; views that
+// leave their children towards the same parent key are merged into one
+// record array (merge case (1) of Sec. 3.4) called a *probe group* here.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lmf {
+
+constexpr int kMaxGroups = 8;        // probe groups of one relation (distinct FK columns)
+constexpr int kMaxZ = 64;            // length of z = [1, root features, view means]
+constexpr int kMaxOwn = 48;          // own continuous columns of one relation
+constexpr int kMaxCat = 32;          // categorical words of one record / root row
+constexpr int kMaxQ = kMaxZ * (kMaxZ + 1) / 2;
+
+// device status bits (OR-ed by kernels, read by lmf_sync)
+constexpr uint32_t kStatusCatRange = 1u;      // category outside [0, domain)
+constexpr uint32_t kStatusOverflow = 2u;      // an exact count left its integer range
+constexpr uint32_t kStatusTimeout = 4u;       // a bounded device wait gave up
+constexpr uint32_t kStatusKeyRange = 8u;      // a child key outside the indexed range
+
+struct Col {
+  const void* p;
+  int32_t dtype;                     // 0 i32, 1 f32, 2 f64
+};
+
+// One merged view record array (probe group).  Record k of a group holds, for
+// every child c of the group, its subtree count at word cnt[c] (int32), the
+// means of its subtree features (float) and its carried categories (int32).
+// Word layout: [n_cnt counts][n_mu means][n_cat categories], stride padded to
+// a multiple of 4 words so one record is read with 128-bit loads.
+struct GroupDesc {
+  const int32_t* fk;                 // foreign-key column of the probing relation
+  uint32_t* rec;                     // [K][stride] words
+  int32_t K;                         // keys 0..K-1 (direct addressing)
+  int32_t stride;                    // words per record
+  int32_t n_cnt, n_mu, n_cat;
+};
+
+// Build of one child relation's section of its parent's group record (A2).
+struct ViewArgs {
+  int64_t nrows;
+  const int32_t* key;                // the child's join key column
+  int32_t K;                         // size of the parent group's key space
+  uint32_t* dst;                     // parent's group record array
+  int32_t dst_stride;
+  int32_t cnt_word;                  // word of this child's count
+  int32_t mu_off;                    // first mean word of this child's section
+  int32_t cat_off;                   // first category word of this child's section
+  int32_t n_own;                     // own continuous columns -> first means
+  Col own[kMaxOwn];
+  int32_t n_owncat;                  // own categorical columns -> first categories
+  const int32_t* owncat[kMaxCat];
+  int32_t owncat_dom[kMaxCat];
+  int32_t n_grp;                     // the child's own probe groups (its children)
+  GroupDesc grp[kMaxGroups];
+  // general (non-unique) path only
+  int32_t d;                         // subtree features of the child
+  int32_t dq;                        // d (d + 1) / 2
+  unsigned long long* cnt64;         // [K] subtree counts
+  long long* S;                      // [K][d] fixed-point sums
+  long long* Q;                      // [K][dq] fixed-point second moments
+  float s_scale[kMaxOwn + kMaxZ];    // fixed-point scale of S per feature (power of 2)
+  double q_scale;                    // fixed-point scale of Q (power of 2)
+  // second moments of the grand-children that fan out: per group child
+  int32_t n_sc;
+  const double* sc[kMaxGroups * 4];  // [K_e][dq_e] within-key scatter of child e
+  int32_t sc_grp[kMaxGroups * 4];    // group of e in this relation
+  int32_t sc_cntword[kMaxGroups * 4];// count word of e in that group's record
+  int32_t sc_feat0[kMaxGroups * 4];  // first subtree feature of e in this child's vector
+  int32_t sc_d[kMaxGroups * 4];      // subtree features of e
+  uint32_t* status;
+};
+
+// finalize of a general view: counts, means and within-key scatter per key
+struct ViewFinalizeArgs {
+  int32_t K, d, dq;
+  const unsigned long long* cnt64;
+  const long long* S;
+  const long long* Q;
+  float s_scale[kMaxOwn + kMaxZ];
+  double q_scale;
+  uint32_t* dst;                      // parent's group record array
+  int32_t dst_stride, cnt_word, mu_off;
+  double* sc;                         // [K][dq]
+  uint32_t* status;
+};
+
+// reverse view of the root towards one probe group: per key of the group,
+// SUM(w) and SUM(w * z_s) for the slots s (the view from the root towards a
+// dimension, Sec. 3.2 directional views; used for grouped outputs).
+struct RevView {
+  unsigned long long* hist;          // [K]
+  long long* R;                      // [K][n_slot]
+  int32_t grp;                       // root probe group
+  int32_t n_slot;
+  int16_t slot_z[kMaxZ];             // z index of each slot
+  float slot_scale[kMaxZ];           // fixed-point scale per slot (power of 2)
+};
+
+// one grouped aggregate accumulated row by row (group-by categories that are
+// not all functions of one foreign key)
+struct DirectAgg {
+  int32_t n_gb;
+  int32_t cat[3];                    // positions in the row's category vector
+  int32_t dom[3];
+  int32_t z;                         // -1: count; else z index of SUM(z)
+  float scale;
+  long long* out;                    // [cells] fixed-point / counts
+};
+
+struct OmegaAcc {                    // SUM over root rows of w / cnt_e per key of e
+  int32_t grp;
+  int32_t cnt_word;
+  unsigned long long* omega;         // [K]
+};
+
+struct RootParams {
+  int64_t N;                         // root rows
+  int32_t n_grp;
+  GroupDesc grp[kMaxGroups];
+  int32_t grp_zoff[kMaxGroups];      // z index of the group's first mean
+  int32_t grp_catoff[kMaxGroups];    // row-category index of the group's first category
+  int32_t n_x;                       // root continuous columns: z[1 + i]
+  Col x[kMaxZ];
+  int32_t n_rcat;                    // root categorical columns, after the groups' ones
+  const int32_t* rcat[kMaxCat];
+  int32_t rcat_dom[kMaxCat];
+  int32_t n_rowcat;                  // length of the row's category vector
+  int32_t m;                         // length of z
+  double* gram_part;                 // [grid][MP * MP]
+  long long* cnt_part;               // [grid]
+  int32_t n_rv;
+  RevView rv[kMaxGroups];
+  int32_t n_direct;
+  const DirectAgg* direct;           // device array
+  int32_t n_om;
+  OmegaAcc om[kMaxGroups * 4];
+  uint32_t* status;
+};
+
+// answering a grouped aggregate from a reverse view: loop over the group's keys
+struct RvTask {
+  int32_t rv;                        // index into RootParams::rv
+  int32_t n_gb;
+  int32_t cat_word[3];               // category words in the group record
+  int32_t dom[3];
+  int32_t mode;                      // 0 count, 1 reverse-view slot, 2 hist * mean
+  int32_t slot;                      // mode 1
+  int32_t mu_word;                   // mode 2
+  float scale;                       // modes 1, 2
+  long long* out;                    // [cells]
+};
+
+// within-key scatter of a fanning-out root child e:  G[e's block] += sum_k omega[k] Sc_e[k]
+struct CorrTask {
+  const unsigned long long* omega;
+  const double* sc;
+  int32_t K, d, zoff;
+};
+
+// final placement of one aggregate's result
+struct OutMap {
+  int32_t kind;                      // 0 COUNT, 1 Gram entry, 2 grouped count, 3 grouped sum,
+                                     // 4 filtered count, 5 filtered sum
+  int32_t i, j;                      // Gram entry (kind 1)
+  int64_t n;                         // cells
+  int64_t dst;                       // offset in the int64 or float64 result array
+  const long long* src;              // kinds 2, 3: fixed-point cells
+  double inv_scale;                  // kind 3
+};
+
+// ---------------------------------------------------------------------------
+// kernel launchers (lmf_kernels.cu)
+cudaError_t launch_view_unique(const ViewArgs& a, cudaStream_t s);
+cudaError_t launch_view_general(const ViewArgs& a, cudaStream_t s);
+cudaError_t launch_view_finalize(const ViewFinalizeArgs& a, cudaStream_t s);
+cudaError_t launch_root_plain(const RootParams& p, int mp, int grid, int64_t n_tiles,
+                              size_t smem, cudaStream_t s);
+size_t root_plain_smem(int mp, int n_rowcat);
+cudaError_t root_plain_prepare(int mp, size_t smem);
+int root_plain_tile_rows();
+cudaError_t launch_combine(const double* part, int grid, int mp, int m, const long long* cnt_part,
+                           double* G, long long* count, cudaStream_t s);
+cudaError_t launch_corr(const void* tasks_dev, int n, double* G, int m, cudaStream_t s);
+cudaError_t launch_rv_tasks(const RvTask* tasks, int n_tasks, const RootParams& p,
+                            int max_K, cudaStream_t s);
+cudaError_t launch_out_map(const OutMap* maps, int n_maps, const double* G, int m,
+                           const long long* count, long long* res_i64, double* res_f64,
+                           cudaStream_t s);
+cudaError_t launch_colmaxabs(const Col* cols, int n, int64_t nrows, double* out, cudaStream_t s);
+cudaError_t launch_key_stats(const int32_t* key, int64_t n, unsigned int* hist, int K,
+                             int* minmax, cudaStream_t s);
+
+}  // namespace lmf

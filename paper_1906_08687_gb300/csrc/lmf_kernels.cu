@@ -1,0 +1,570 @@
+// lmf_kernels.cu -- view build, plain root scan, combine and finalize kernels.
+//
+// Step map (method -> kernel):
+//   child views, Sec. 3.2 (directional views) and Ex. 3.1     -> k_view_unique / k_view_general
+//   merged views probed at the root, Sec. 3.4 case (1)        -> GroupDesc records
+//   one scan of the root with view lookups, Sec. 3.5          -> k_root_plain (and lmf_gram_tc.cu)
+//   covar entries SUM(x_i x_j), Eq. lr-sigma of Sec. 2        -> Gram of z = [1, x, view means]
+//   grouped covar entries Covar(X_j; X_k), Covar(X_j, X_k; 1) -> reverse views + k_rv_tasks / DirectAgg
+//   cross-block combine and placement                          -> k_combine, k_corr, k_out_map
+#include "lmf_internal.h"
+
+#include <cstdint>
+#include <cstdio>
+
+namespace lmf {
+
+// ---------------------------------------------------------------------------
+// helpers
+__device__ __forceinline__ float load_f(const Col& c, int64_t i) {
+  return c.dtype == 2 ? static_cast<float>(static_cast<const double*>(c.p)[i])
+                      : static_cast<const float*>(c.p)[i];
+}
+__device__ __forceinline__ double load_d(const Col& c, int64_t i) {
+  return c.dtype == 2 ? static_cast<const double*>(c.p)[i]
+                      : static_cast<double>(static_cast<const float*>(c.p)[i]);
+}
+__device__ __forceinline__ void add_ll(long long* p, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+}
+// exact fixed-point image of w * x: x * scale is a power-of-two scaling of a
+// float (exact unless it underflows), its integer part is taken with rounding
+__device__ __forceinline__ long long fixp(long long w, float x, float scale) {
+  return w * __float2ll_rn(x * scale);
+}
+// Knuth's TwoSum: s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
+  float s = hi + x;
+  float bp = s - hi;
+  float e = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += e;
+}
+
+// ---------------------------------------------------------------------------
+// A1: key statistics and value ranges (declare / plan time)
+__global__ void k_minmax_i32(const int32_t* key, int64_t n, int* mm) {
+  int lo = 0x7fffffff, hi = -0x7fffffff - 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int v = key[i];
+    lo = min(lo, v);
+    hi = max(hi, v);
+  }
+  for (int o = 16; o; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(mm, lo);
+    atomicMax(mm + 1, hi);
+  }
+}
+
+__global__ void k_hist_i32(const int32_t* key, int64_t n, unsigned int* hist, int K) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int v = key[i];
+    if (v >= 0 && v < K) atomicAdd(hist + v, 1u);
+  }
+}
+
+cudaError_t launch_key_stats(const int32_t* key, int64_t n, unsigned int* hist, int K, int* minmax,
+                             cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int64_t gb = (n + 255) / 256;
+  int grid = (int)(gb < 4096 ? gb : 4096);
+  if (hist == nullptr) {
+    k_minmax_i32<<<grid, 256, 0, s>>>(key, n, minmax);
+  } else {
+    k_hist_i32<<<grid, 256, 0, s>>>(key, n, hist, K);
+  }
+  return cudaGetLastError();
+}
+
+__global__ void k_colmaxabs(const Col c, int64_t n, unsigned long long* out) {
+  double m = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v = fabs(load_d(c, i));
+    m = v > m ? v : m;  // NaN is dropped
+  }
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  // non-negative doubles order like their bit patterns
+  if ((threadIdx.x & 31) == 0) atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(m)));
+}
+
+cudaError_t launch_colmaxabs(const Col* cols, int n, int64_t nrows, double* out, cudaStream_t s) {
+  for (int i = 0; i < n; ++i) {
+    if (nrows <= 0) continue;
+    int64_t gb = (nrows + 255) / 256;
+    int grid = (int)(gb < 2048 ? gb : 2048);
+    k_colmaxabs<<<grid, 256, 0, s>>>(cols[i], nrows, reinterpret_cast<unsigned long long*>(out + i));
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// A2: child views, unique keys (every key has at most one row and every
+// subtree count is 0 or 1): the record of key k is written by its one row.
+__global__ void k_view_unique(const __grid_constant__ ViewArgs a) {
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= a.nrows) return;
+  const int32_t k = a.key[row];
+  if (k < 0 || k >= a.K) {
+    atomicOr(a.status, kStatusKeyRange);
+    return;
+  }
+  uint32_t* dst = a.dst + (int64_t)k * a.dst_stride;
+  long long cnt = 1;
+  int mu = a.mu_off, cat = a.cat_off;
+  for (int i = 0; i < a.n_own; ++i) dst[mu++] = __float_as_uint(load_f(a.own[i], row));
+  for (int i = 0; i < a.n_owncat; ++i) {
+    int32_t v = a.owncat[i][row];
+    if (v < 0 || v >= a.owncat_dom[i]) {
+      atomicOr(a.status, kStatusCatRange);
+      v = 0;
+    }
+    dst[cat++] = static_cast<uint32_t>(v);
+  }
+  for (int g = 0; g < a.n_grp; ++g) {
+    const GroupDesc& G = a.grp[g];
+    const int32_t fk = G.fk[row];
+    const bool hit = fk >= 0 && fk < G.K;
+    const uint32_t* rec = G.rec + (hit ? (int64_t)fk * G.stride : 0);
+    for (int c = 0; c < G.n_cnt; ++c) cnt *= hit ? static_cast<long long>(rec[c]) : 0;
+    for (int j = 0; j < G.n_mu; ++j) dst[mu++] = hit ? rec[G.n_cnt + j] : 0u;
+    for (int j = 0; j < G.n_cat; ++j) dst[cat++] = hit ? rec[G.n_cnt + G.n_mu + j] : 0u;
+  }
+  dst[a.cnt_word] = static_cast<uint32_t>(cnt);
+}
+
+cudaError_t launch_view_unique(const ViewArgs& a, cudaStream_t s) {
+  if (a.nrows <= 0) return cudaSuccess;
+  k_view_unique<<<(unsigned)((a.nrows + 255) / 256), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// A2, general keys: subtree counts, sums and second moments per key, in
+// exact fixed-point integers (order-independent, so deterministic).  With
+// e's subtree count c_e and within-key scatter Sc_e, a row's contribution to
+// its key is  c * xt xt^T  +  sum_e (c / c_e) * Sc_e  (placed on e's block),
+// c = prod_e c_e, xt = [own features, means of the children's subtrees].
+__device__ __forceinline__ int tri_index(int i, int j, int d) {  // i <= j
+  return i * d - i * (i - 1) / 2 + (j - i);
+}
+
+__global__ void k_view_general(const __grid_constant__ ViewArgs a) {
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= a.nrows) return;
+  const int32_t k = a.key[row];
+  if (k < 0 || k >= a.K) {
+    atomicOr(a.status, kStatusKeyRange);
+    return;
+  }
+  double xt[kMaxZ];
+  long long wc[kMaxGroups * 4];
+  int nwc = 0;
+  int d = 0;
+  for (int i = 0; i < a.n_own; ++i) xt[d++] = load_d(a.own[i], row);
+  long long cnt = 1;
+  const uint32_t* recs[kMaxGroups];
+  int32_t fks[kMaxGroups];
+  for (int g = 0; g < a.n_grp; ++g) {
+    const GroupDesc& G = a.grp[g];
+    const int32_t fk = G.fk[row];
+    const bool hit = fk >= 0 && fk < G.K;
+    fks[g] = hit ? fk : -1;
+    recs[g] = hit ? G.rec + (int64_t)fk * G.stride : nullptr;
+    for (int c = 0; c < G.n_cnt; ++c) {
+      long long v = hit ? static_cast<long long>(recs[g][c]) : 0;
+      wc[nwc++] = v;
+      cnt *= v;
+    }
+    for (int j = 0; j < G.n_mu; ++j) xt[d++] = hit ? (double)__uint_as_float(recs[g][G.n_cnt + j]) : 0.0;
+  }
+  if (cnt == 0) return;
+  add_ll(reinterpret_cast<long long*>(a.cnt64 + k), cnt);
+  long long* S = a.S + (int64_t)k * a.d;
+  long long* Q = a.Q + (int64_t)k * a.dq;
+  const double c = static_cast<double>(cnt);
+  for (int i = 0; i < a.d; ++i) add_ll(S + i, llrint(c * xt[i] * (double)a.s_scale[i]));
+  for (int i = 0; i < a.d; ++i)
+    for (int j = i; j < a.d; ++j) add_ll(Q + tri_index(i, j, a.d), llrint(c * xt[i] * xt[j] * a.q_scale));
+  // scatter of fanning-out grandchildren, weighted by the other counts
+  int wbase[kMaxGroups + 1];
+  wbase[0] = 0;
+  for (int g = 0; g < a.n_grp; ++g) wbase[g + 1] = wbase[g] + a.grp[g].n_cnt;
+  for (int e = 0; e < a.n_sc; ++e) {
+    const int g = a.sc_grp[e];
+    if (fks[g] < 0) continue;
+    long long other = 1;
+    const int self = wbase[g] + a.sc_cntword[e];
+    for (int q = 0; q < nwc; ++q)
+      if (q != self) other *= wc[q];
+    const int de = a.sc_d[e], f0 = a.sc_feat0[e];
+    const double* sc = a.sc[e] + (int64_t)fks[g] * (de * (de + 1) / 2);
+    for (int i = 0; i < de; ++i)
+      for (int j = i; j < de; ++j)
+        add_ll(Q + tri_index(f0 + i, f0 + j, a.d),
+               llrint((double)other * sc[tri_index(i, j, de)] * a.q_scale));
+  }
+}
+
+cudaError_t launch_view_general(const ViewArgs& a, cudaStream_t s) {
+  if (a.nrows <= 0) return cudaSuccess;
+  k_view_general<<<(unsigned)((a.nrows + 127) / 128), 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+__global__ void k_view_finalize(const __grid_constant__ ViewFinalizeArgs a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.K) return;
+  const unsigned long long c = a.cnt64[k];
+  uint32_t* dst = a.dst + (int64_t)k * a.dst_stride;
+  if (c > 0x7fffffffull) atomicOr(a.status, kStatusOverflow);
+  dst[a.cnt_word] = static_cast<uint32_t>(c > 0x7fffffffull ? 0x7fffffffull : c);
+  double s[kMaxZ];
+  for (int i = 0; i < a.d; ++i) {
+    s[i] = c ? (double)a.S[(int64_t)k * a.d + i] / (double)a.s_scale[i] : 0.0;
+    dst[a.mu_off + i] = __float_as_uint(c ? (float)(s[i] / (double)c) : 0.f);
+  }
+  double* sc = a.sc + (int64_t)k * a.dq;
+  for (int i = 0; i < a.d; ++i)
+    for (int j = i; j < a.d; ++j) {
+      const int t = tri_index(i, j, a.d);
+      sc[t] = c ? (double)a.Q[(int64_t)k * a.dq + t] / a.q_scale - s[i] * s[j] / (double)c : 0.0;
+    }
+}
+
+cudaError_t launch_view_finalize(const ViewFinalizeArgs& a, cudaStream_t s) {
+  if (a.K <= 0) return cudaSuccess;
+  k_view_finalize<<<(a.K + 127) / 128, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// A3-A5: the plain root scan.  Tiles of 256 root rows; phase 1 gives every row
+// to one thread (foreign keys, view records, z, w, grouped updates) and writes
+// w*z and z to shared memory; phase 2 accumulates the upper triangle of
+// sum_r w_r z_r z_r^T in 4x4 register blocks with FP32 FMAs, folded after
+// every tile into a two-float (TwoSum) accumulator; each CTA writes its FP64
+// partial Gram.
+constexpr int kPlainT = 256;
+
+__device__ __forceinline__ void put_word(float* zrow, int32_t* crow, const RootParams& p, int g, int w,
+                                         uint32_t v, long long& cnt) {
+  const GroupDesc& G = p.grp[g];
+  if (w < G.n_cnt) {
+    cnt *= static_cast<long long>(v);
+  } else if (w < G.n_cnt + G.n_mu) {
+    zrow[p.grp_zoff[g] + (w - G.n_cnt)] = __uint_as_float(v);
+  } else if (w < G.n_cnt + G.n_mu + G.n_cat) {
+    crow[p.grp_catoff[g] + (w - G.n_cnt - G.n_mu)] = static_cast<int32_t>(v);
+  }
+}
+
+template <int MP>
+__global__ void __launch_bounds__(256) k_root_plain(const __grid_constant__ RootParams p, int64_t n_tiles) {
+  constexpr int T = kPlainT;
+  constexpr int LD = MP + 4;
+  constexpr int NBK = MP / 4;
+  constexpr int NB = NBK * (NBK + 1) / 2;
+  constexpr int RG = NB >= 256 ? 1 : 256 / NB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Za = reinterpret_cast<float*>(smem_raw);
+  float* Zb = Za + T * LD;
+  int32_t* Cs = reinterpret_cast<int32_t*>(Zb + T * LD);
+  const int tid = threadIdx.x;
+  const int gblk = tid % NB, grow = tid / NB;
+  const bool active = grow < RG;
+  int bi = 0, t = gblk;
+  while (t >= NBK - bi) {
+    t -= NBK - bi;
+    ++bi;
+  }
+  const int bj = bi + t;
+  float hi[16], lo[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) hi[q] = lo[q] = 0.f;
+  long long cnt_acc = 0;
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    // ---------------- phase 1: one row per thread
+    {
+      const int64_t row = tile * T + tid;
+      float* zrow = Zb + tid * LD;
+      int32_t* crow = Cs + tid * (p.n_rowcat > 0 ? p.n_rowcat : 1);
+      long long w = 0;
+#pragma unroll
+      for (int i = 0; i < MP; ++i) zrow[i] = 0.f;
+      if (row < p.N) {
+        w = 1;
+        zrow[0] = 1.f;
+        for (int i = 0; i < p.n_x; ++i) zrow[1 + i] = load_f(p.x[i], row);
+        for (int g = 0; g < p.n_grp; ++g) {
+          const GroupDesc& G = p.grp[g];
+          const int32_t fk = G.fk[row];
+          if (fk < 0 || fk >= G.K) {
+            w = 0;
+            continue;
+          }
+          const uint4* rec = reinterpret_cast<const uint4*>(G.rec + (int64_t)fk * G.stride);
+          const int nw = G.n_cnt + G.n_mu + G.n_cat;
+          for (int q = 0; q < (nw + 3) / 4; ++q) {
+            const uint4 v = __ldg(rec + q);
+            put_word(zrow, crow, p, g, 4 * q + 0, v.x, w);
+            put_word(zrow, crow, p, g, 4 * q + 1, v.y, w);
+            put_word(zrow, crow, p, g, 4 * q + 2, v.z, w);
+            put_word(zrow, crow, p, g, 4 * q + 3, v.w, w);
+          }
+        }
+        for (int i = 0; i < p.n_rcat; ++i) {
+          int32_t v = p.rcat[i][row];
+          if (v < 0 || v >= p.rcat_dom[i]) {
+            atomicOr(p.status, kStatusCatRange);
+            v = 0;
+          }
+          crow[p.n_rowcat - p.n_rcat + i] = v;
+        }
+      }
+      if (w == 0) {
+#pragma unroll
+        for (int i = 0; i < MP; ++i) zrow[i] = 0.f;
+      }
+      cnt_acc += w;
+      // w * z for the left operand
+      const float wf = static_cast<float>(w);
+      float* arow = Za + tid * LD;
+#pragma unroll
+      for (int q = 0; q < MP / 4; ++q) {
+        float4 v = *reinterpret_cast<const float4*>(zrow + 4 * q);
+        v.x *= wf;
+        v.y *= wf;
+        v.z *= wf;
+        v.w *= wf;
+        *reinterpret_cast<float4*>(arow + 4 * q) = v;
+      }
+      // grouped updates of this row
+      if (w != 0) {
+        for (int r = 0; r < p.n_rv; ++r) {
+          const RevView& R = p.rv[r];
+          const int32_t fk = p.grp[R.grp].fk[row];
+          atomicAdd(R.hist + fk, static_cast<unsigned long long>(w));
+          long long* dst = R.R + (int64_t)fk * R.n_slot;
+          for (int s = 0; s < R.n_slot; ++s) add_ll(dst + s, fixp(w, zrow[R.slot_z[s]], R.slot_scale[s]));
+        }
+        for (int d = 0; d < p.n_direct; ++d) {
+          const DirectAgg& A = p.direct[d];
+          int64_t cell = 0;
+          for (int q = 0; q < A.n_gb; ++q) cell = cell * A.dom[q] + crow[A.cat[q]];
+          add_ll(A.out + cell, A.z < 0 ? w : fixp(w, zrow[A.z], A.scale));
+        }
+        for (int o = 0; o < p.n_om; ++o) {
+          const OmegaAcc& O = p.om[o];
+          const GroupDesc& G = p.grp[O.grp];
+          const int32_t fk = G.fk[row];
+          const long long ce = static_cast<long long>(G.rec[(int64_t)fk * G.stride + O.cnt_word]);
+          atomicAdd(O.omega + fk, static_cast<unsigned long long>(w / ce));
+        }
+      }
+    }
+    __syncthreads();
+    // ---------------- phase 2: Gram blocks
+    if (active) {
+      float acc[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+      for (int r = grow; r < T; r += RG) {
+        const float4 a = *reinterpret_cast<const float4*>(Za + r * LD + 4 * bi);
+        const float4 b = *reinterpret_cast<const float4*>(Zb + r * LD + 4 * bj);
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fmaf(av[u], bv[v], acc[u * 4 + v]);
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) two_sum(hi[q], lo[q], acc[q]);
+    }
+    __syncthreads();
+  }
+
+  // ---------------- CTA reduction of the row groups, FP64 partial out
+  double* red = reinterpret_cast<double*>(smem_raw);  // [NB * 16][RG]
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) red[(gblk * 16 + q) * RG + grow] = (double)hi[q] + (double)lo[q];
+  }
+  __syncthreads();
+  double* out = p.gram_part + (int64_t)blockIdx.x * MP * MP;
+  for (int e = tid; e < NB * 16; e += blockDim.x) {
+    const int b = e / 16, q = e % 16;
+    int ii = 0, tt = b;
+    while (tt >= NBK - ii) {
+      tt -= NBK - ii;
+      ++ii;
+    }
+    const int jj = ii + tt;
+    double s = 0.0;
+    for (int g = 0; g < RG; ++g) s += red[e * RG + g];
+    out[(4 * ii + q / 4) * MP + 4 * jj + q % 4] = s;
+  }
+  // count
+  __shared__ long long cred[8];
+  long long c = cnt_acc;
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((tid & 31) == 0) cred[tid >> 5] = c;
+  __syncthreads();
+  if (tid == 0) {
+    long long s = 0;
+    for (int wv = 0; wv < 8; ++wv) s += cred[wv];
+    p.cnt_part[blockIdx.x] = s;
+  }
+}
+
+size_t root_plain_smem(int mp, int n_rowcat) {
+  size_t z = (size_t)2 * kPlainT * (mp + 4) * sizeof(float);
+  size_t c = (size_t)kPlainT * (n_rowcat > 0 ? n_rowcat : 1) * sizeof(int32_t);
+  return z + c;
+}
+int root_plain_tile_rows() { return kPlainT; }
+
+template <int MP>
+static cudaError_t launch_plain_mp(const RootParams& p, int grid, int64_t n_tiles, size_t smem,
+                                   cudaStream_t s) {
+  k_root_plain<MP><<<grid, 256, smem, s>>>(p, n_tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t root_plain_prepare(int mp, size_t smem) {
+  const int v = (int)smem;
+  switch (mp) {
+    case 16: return cudaFuncSetAttribute(k_root_plain<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+    case 32: return cudaFuncSetAttribute(k_root_plain<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+    case 48: return cudaFuncSetAttribute(k_root_plain<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+    case 64: return cudaFuncSetAttribute(k_root_plain<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_root_plain(const RootParams& p, int mp, int grid, int64_t n_tiles, size_t smem,
+                              cudaStream_t s) {
+  switch (mp) {
+    case 16: return launch_plain_mp<16>(p, grid, n_tiles, smem, s);
+    case 32: return launch_plain_mp<32>(p, grid, n_tiles, smem, s);
+    case 48: return launch_plain_mp<48>(p, grid, n_tiles, smem, s);
+    case 64: return launch_plain_mp<64>(p, grid, n_tiles, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A9: ordered FP64 combine of the per-CTA partials (deterministic)
+__global__ void k_combine(const double* part, int grid, int mp, int m, const long long* cnt_part,
+                          double* G, long long* count) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < m * m) {
+    const int i = e / m, j = e % m;
+    if (i <= j) {
+      double s = 0.0;
+      for (int c = 0; c < grid; ++c) s += part[(int64_t)c * mp * mp + i * mp + j];
+      G[i * m + j] = s;
+      G[j * m + i] = s;
+    }
+  }
+  if (e == 0) {
+    long long s = 0;
+    for (int c = 0; c < grid; ++c) s += cnt_part[c];
+    *count = s;
+  }
+}
+
+cudaError_t launch_combine(const double* part, int grid, int mp, int m, const long long* cnt_part,
+                           double* G, long long* count, cudaStream_t s) {
+  k_combine<<<(m * m + 127) / 128, 128, 0, s>>>(part, grid, mp, m, cnt_part, G, count);
+  return cudaGetLastError();
+}
+
+__global__ void k_corr(const CorrTask* tasks, double* G, int m) {
+  const CorrTask t = tasks[blockIdx.x];
+  const int dq = t.d * (t.d + 1) / 2;
+  for (int e = threadIdx.x; e < dq; e += blockDim.x) {
+    int i = 0, r = e;
+    while (r >= t.d - i) {
+      r -= t.d - i;
+      ++i;
+    }
+    const int j = i + r;
+    double s = 0.0;
+    for (int k = 0; k < t.K; ++k) s += (double)t.omega[k] * t.sc[(int64_t)k * dq + e];
+    const int a = t.zoff + i, b = t.zoff + j;
+    G[a * m + b] += s;
+    if (a != b) G[b * m + a] += s;
+  }
+}
+
+cudaError_t launch_corr(const void* tasks_dev, int n, double* G, int m, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_corr<<<n, 128, 0, s>>>(static_cast<const CorrTask*>(tasks_dev), G, m);
+  return cudaGetLastError();
+}
+
+// grouped aggregates answered from a reverse view: one pass over the group's keys
+__global__ void k_rv_tasks(const RvTask* tasks, int n_tasks, const __grid_constant__ RootParams p) {
+  const RvTask t = tasks[blockIdx.y];
+  const RevView& R = p.rv[t.rv];
+  const GroupDesc& G = p.grp[R.grp];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G.K; k += gridDim.x * blockDim.x) {
+    const unsigned long long h = R.hist[k];
+    if (h == 0) continue;
+    const uint32_t* rec = G.rec + (int64_t)k * G.stride;
+    int64_t cell = 0;
+    for (int q = 0; q < t.n_gb; ++q) cell = cell * t.dom[q] + static_cast<int32_t>(rec[t.cat_word[q]]);
+    long long v;
+    if (t.mode == 0) v = static_cast<long long>(h);
+    else if (t.mode == 1) v = R.R[(int64_t)k * R.n_slot + t.slot];
+    else v = fixp(static_cast<long long>(h), __uint_as_float(rec[t.mu_word]), t.scale);
+    add_ll(t.out + cell, v);
+  }
+}
+
+cudaError_t launch_rv_tasks(const RvTask* tasks, int n_tasks, const RootParams& p, int max_K,
+                            cudaStream_t s) {
+  if (n_tasks <= 0) return cudaSuccess;
+  dim3 grid((unsigned)min((max_K + 255) / 256, 64), (unsigned)n_tasks);
+  k_rv_tasks<<<grid, 256, 0, s>>>(tasks, n_tasks, p);
+  return cudaGetLastError();
+}
+
+// final placement of every aggregate
+__global__ void k_out_map(const OutMap* maps, const double* G, int m, const long long* count,
+                          long long* res_i64, double* res_f64) {
+  const OutMap o = maps[blockIdx.x];
+  switch (o.kind) {
+    case 0:
+      if (threadIdx.x == 0) res_i64[o.dst] = *count;
+      break;
+    case 1:
+      if (threadIdx.x == 0) res_f64[o.dst] = G[o.i * m + o.j];
+      break;
+    case 2:
+    case 4:
+      for (int64_t c = threadIdx.x; c < o.n; c += blockDim.x) res_i64[o.dst + c] = o.src[c];
+      break;
+    default:
+      for (int64_t c = threadIdx.x; c < o.n; c += blockDim.x)
+        res_f64[o.dst + c] = (double)o.src[c] * o.inv_scale;
+      break;
+  }
+}
+
+cudaError_t launch_out_map(const OutMap* maps, int n_maps, const double* G, int m, const long long* count,
+                           long long* res_i64, double* res_f64, cudaStream_t s) {
+  if (n_maps <= 0) return cudaSuccess;
+  k_out_map<<<n_maps, 128, 0, s>>>(maps, G, m, count, res_i64, res_f64);
+  return cudaGetLastError();
+}
+
+}  // namespace lmf

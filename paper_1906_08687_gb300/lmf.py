@@ -1,0 +1,280 @@
+"""Thin ctypes binding of the C ABI in include/lmf.h (argument marshalling only).
+
+Every computation runs in liblmf.so's CUDA kernels.  Loading fails loudly
+when the library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+# status codes and enums (include/lmf.h)
+LMF_OK = 0
+LMF_ERR_ARG, LMF_ERR_NOT_TREE, LMF_ERR_DTYPE, LMF_ERR_KEY = -1, -2, -3, -4
+LMF_ERR_OOM, LMF_ERR_CUDA, LMF_ERR_TIMEOUT, LMF_ERR_OVERFLOW = -5, -6, -7, -8
+LMF_ERR_STATE, LMF_ERR_UNSUPPORTED = -9, -10
+LMF_I32, LMF_F32, LMF_F64, LMF_I64 = 0, 1, 2, 3
+LMF_KEY, LMF_CONT, LMF_CAT = 0, 1, 2
+LMF_POW, LMF_LE, LMF_GT = 0, 1, 2
+LMF_PREC_PLAIN_FP32, LMF_PREC_SPLIT_BF16 = 0, 1
+LMF_BATCH_SINGLE, LMF_BATCH_GRAPH = 0, 1
+LMF_MAX_GROUP_BY = 3
+
+_ROLE = {'key': LMF_KEY, 'cont': LMF_CONT, 'cat': LMF_CAT}
+_KIND = {'pow': LMF_POW, 'le': LMF_LE, 'gt': LMF_GT}
+
+
+class lmf_column(ctypes.Structure):
+    _fields_ = [('name', ctypes.c_char_p), ('dtype', ctypes.c_int32), ('role', ctypes.c_int32),
+                ('data', ctypes.c_void_p), ('cat_domain', ctypes.c_int32),
+                ('on_host', ctypes.c_int32)]
+
+
+class lmf_factor(ctypes.Structure):
+    _fields_ = [('attr', ctypes.c_char_p), ('kind', ctypes.c_int32), ('power', ctypes.c_int32),
+                ('threshold', ctypes.c_double)]
+
+
+class lmf_agg_spec(ctypes.Structure):
+    _fields_ = [('n_group_by', ctypes.c_int32), ('group_by', ctypes.c_char_p * LMF_MAX_GROUP_BY),
+                ('n_factors', ctypes.c_int32), ('factors', ctypes.POINTER(lmf_factor))]
+
+
+class lmf_plan_opts(ctypes.Structure):
+    _fields_ = [('precision', ctypes.c_int32), ('batching', ctypes.c_int32),
+                ('tile_rows', ctypes.c_int32), ('ctas_per_sm', ctypes.c_int32),
+                ('root_mode', ctypes.c_int32), ('reserved', ctypes.c_int32 * 3)]
+
+
+class lmf_plan_stats(ctypes.Structure):
+    _fields_ = [('n_views', ctypes.c_int32), ('n_probe_groups', ctypes.c_int32),
+                ('z_len', ctypes.c_int32), ('n_gram_aggs', ctypes.c_int32),
+                ('n_grouped_aggs', ctypes.c_int32), ('n_filtered_aggs', ctypes.c_int32),
+                ('n_kernels_per_run', ctypes.c_int32), ('unique_keys', ctypes.c_int32),
+                ('root_grid', ctypes.c_int32), ('precision', ctypes.c_int32),
+                ('root_rows', ctypes.c_int64), ('scratch_bytes', ctypes.c_int64)]
+
+
+# every symbol include/lmf.h declares, with its ctypes signature
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGNATURES = {
+    'lmf_create': (_I, [_I, ctypes.POINTER(_P)]),
+    'lmf_destroy': (_I, [_P]),
+    'lmf_register_relation': (_I, [_P, ctypes.c_char_p, ctypes.c_int64, ctypes.POINTER(lmf_column),
+                                   _I, ctypes.POINTER(_I)]),
+    'lmf_declare_join': (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                              ctypes.POINTER(ctypes.c_char_p)]),
+    'lmf_declare_batch': (_I, [_P, ctypes.POINTER(lmf_agg_spec), _I, ctypes.POINTER(_I)]),
+    'lmf_plan': (_I, [_P, _I, ctypes.POINTER(lmf_plan_opts)]),
+    'lmf_plan_info': (_I, [_P, _I, ctypes.POINTER(lmf_plan_stats)]),
+    'lmf_run': (_I, [_P, _I, _P]),
+    'lmf_sync': (_I, [_P, _I]),
+    'lmf_result_info': (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_int64),
+                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
+    'lmf_result_sizes': (_I, [_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    'lmf_read_results': (_I, [_P, _I, _P, _P, _I, _P]),
+    'lmf_read_result': (_I, [_P, _I, _I, _P]),
+    'lmf_status_string': (ctypes.c_char_p, [_I]),
+    'lmf_error_message': (ctypes.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load liblmf.so; raise if it has not been built (no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f'liblmf.so is not built ({_build.LIB}); run '
+                              'paper_1906_08687_gb300.build.build() first')
+        lib = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class LmfError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ''):
+        self.status = status
+        msg = load().lmf_status_string(status).decode()
+        super().__init__(f'{what}: {msg} ({status}){": " + detail if detail else ""}')
+
+
+class Engine:
+    """One lmf_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        self._check(self.lib.lmf_create(device, ctypes.byref(h)), 'lmf_create', ctx=False)
+        self.ctx = h
+        self._keep = []
+        self.rel_ids = {}
+
+    # -- helpers --------------------------------------------------------------
+    def _check(self, st: int, what: str, ctx: bool = True):
+        if st != LMF_OK:
+            detail = self.lib.lmf_error_message(self.ctx).decode() if ctx and self.ctx else ''
+            raise LmfError(st, what, detail)
+
+    def close(self):
+        if getattr(self, 'ctx', None):
+            self.lib.lmf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C ABI ------------------------------------------------------------------
+    def register_relation(self, name: str, nrows: int, columns: Sequence[dict]) -> int:
+        """columns: dicts with name, dtype (LMF_*), role, data (pointer int),
+        cat_domain, on_host."""
+        arr = (lmf_column * max(1, len(columns)))()
+        for i, c in enumerate(columns):
+            nm = c['name'].encode()
+            self._keep.append(nm)
+            arr[i].name = nm
+            arr[i].dtype = c['dtype']
+            arr[i].role = c['role']
+            arr[i].data = c['data']
+            arr[i].cat_domain = c.get('cat_domain', 0)
+            arr[i].on_host = c.get('on_host', 0)
+        rid = ctypes.c_int()
+        self._check(self.lib.lmf_register_relation(self.ctx, name.encode(), nrows, arr, len(columns),
+                                                   ctypes.byref(rid)), 'lmf_register_relation')
+        self.rel_ids[name] = rid.value
+        return rid.value
+
+    def declare_join(self, edges: Sequence[Tuple[int, int, str]]):
+        n = len(edges)
+        par = (ctypes.c_int * max(1, n))(*[e[0] for e in edges])
+        chi = (ctypes.c_int * max(1, n))(*[e[1] for e in edges])
+        keys = [e[2].encode() for e in edges]
+        ka = (ctypes.c_char_p * max(1, n))(*keys)
+        self._check(self.lib.lmf_declare_join(self.ctx, n, par, chi, ka), 'lmf_declare_join')
+
+    def declare_batch(self, aggs: Sequence) -> int:
+        """aggs: objects with .group_by (names) and .factors ((attr, 'pow'|'le'|'gt', p_or_t))."""
+        arr = (lmf_agg_spec * max(1, len(aggs)))()
+        for i, a in enumerate(aggs):
+            arr[i].n_group_by = len(a.group_by)
+            for q, g in enumerate(a.group_by):
+                b = g.encode()
+                self._keep.append(b)
+                arr[i].group_by[q] = b
+            fs = (lmf_factor * max(1, len(a.factors)))()
+            for q, (attr, kind, val) in enumerate(a.factors):
+                b = attr.encode()
+                self._keep.append(b)
+                fs[q].attr = b
+                fs[q].kind = _KIND[kind]
+                fs[q].power = int(val) if kind == 'pow' else 0
+                fs[q].threshold = float(val) if kind != 'pow' else 0.0
+            self._keep.append(fs)
+            arr[i].n_factors = len(a.factors)
+            arr[i].factors = fs
+        bid = ctypes.c_int()
+        self._check(self.lib.lmf_declare_batch(self.ctx, arr, len(aggs), ctypes.byref(bid)),
+                    'lmf_declare_batch')
+        return bid.value
+
+    def plan(self, batch: int, precision: int = LMF_PREC_SPLIT_BF16, batching: int = LMF_BATCH_GRAPH,
+             tile_rows: int = 0, ctas_per_sm: int = 0):
+        o = lmf_plan_opts(precision, batching, tile_rows, ctas_per_sm, 0)
+        self._check(self.lib.lmf_plan(self.ctx, batch, ctypes.byref(o)), 'lmf_plan')
+
+    def plan_info(self, batch: int) -> dict:
+        s = lmf_plan_stats()
+        self._check(self.lib.lmf_plan_info(self.ctx, batch, ctypes.byref(s)), 'lmf_plan_info')
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def run(self, batch: int, stream: int = 0):
+        self._check(self.lib.lmf_run(self.ctx, batch, ctypes.c_void_p(stream)), 'lmf_run')
+
+    def sync(self, batch: int):
+        self._check(self.lib.lmf_sync(self.ctx, batch), 'lmf_sync')
+
+    def result_layout(self, batch: int, n_aggs: int) -> List[Tuple[int, int, int]]:
+        out = []
+        n, dt, off = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+        for a in range(n_aggs):
+            self._check(self.lib.lmf_result_info(self.ctx, batch, a, ctypes.byref(n), ctypes.byref(dt),
+                                                 ctypes.byref(off)), 'lmf_result_info')
+            out.append((n.value, dt.value, off.value))
+        return out
+
+    def result_sizes(self, batch: int) -> Tuple[int, int]:
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.lmf_result_sizes(self.ctx, batch, ctypes.byref(a), ctypes.byref(b)),
+                    'lmf_result_sizes')
+        return a.value, b.value
+
+    def read_results(self, batch: int, dst_i64: int, dst_f64: int, dst_is_device: bool,
+                     stream: int = 0):
+        self._check(self.lib.lmf_read_results(self.ctx, batch, ctypes.c_void_p(dst_i64),
+                                              ctypes.c_void_p(dst_f64), int(dst_is_device),
+                                              ctypes.c_void_p(stream)), 'lmf_read_results')
+
+    def read_result(self, batch: int, agg: int, dst: int):
+        self._check(self.lib.lmf_read_result(self.ctx, batch, agg, ctypes.c_void_p(dst)),
+                    'lmf_read_result')
+
+    # -- convenience: all results as numpy arrays ------------------------------
+    def results(self, batch: int, n_aggs: int) -> List[np.ndarray]:
+        n_i64, n_f64 = self.result_sizes(batch)
+        i64 = np.zeros(max(1, n_i64), np.int64)
+        f64 = np.zeros(max(1, n_f64), np.float64)
+        self.read_results(batch, i64.ctypes.data, f64.ctypes.data, False)
+        out = []
+        for n, dt, off in self.result_layout(batch, n_aggs):
+            out.append((i64 if dt == LMF_I64 else f64)[off:off + n].copy())
+        return out
+
+
+def column_dtype(arr) -> int:
+    """LMF dtype of a numpy array or torch tensor."""
+    s = str(arr.dtype)
+    if s.endswith('int32'):
+        return LMF_I32
+    if s.endswith('float32'):
+        return LMF_F32
+    if s.endswith('float64'):
+        return LMF_F64
+    raise TypeError(f'unsupported column dtype {s}')
+
+
+def register_schema(engine: Engine, schema, tensors: dict, on_host: bool = False) -> None:
+    """Register every relation of `schema` and its join tree.
+
+    schema: object with .relations (each .name, .columns with .name, .role
+    ('key'|'cont'|'cat'), .cat_domain), .edges ((parent, child, key)) and
+    .root.  tensors[(relation, column)] is the buffer holding that column
+    (device tensor, or pinned host tensor when on_host); its .data_ptr() is
+    passed to the C ABI.
+    """
+    for r in schema.relations:
+        cols = []
+        for c in r.columns:
+            t = tensors[(r.name, c.name)]
+            cols.append(dict(name=c.name, dtype=column_dtype(t), role=_ROLE[c.role], data=t.data_ptr(),
+                             cat_domain=int(c.cat_domain), on_host=int(on_host)))
+        engine.register_relation(r.name, int(r.nrows), cols)
+    ids = engine.rel_ids
+    engine.declare_join([(ids[p], ids[c], k) for p, c, k in schema.edges])
