@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Benchmark of one aggregate batch over a snowflake join (config 2 shape).
+
+Workload: fact table of 20M rows (3 int32 foreign keys, 8 FP32 features)
+joined to a 3-level snowflake of 6 dimension relations (22 more continuous
+features, 10 categorical attributes); the batch is COUNT, all 495 degree <= 2
+monomial SUMs over the 30 features, SUM(x_i) and COUNT grouped by each
+categorical attribute, and COUNT grouped by every categorical pair: 851
+aggregates (Sec. 2, covar matrix with one-hot categorical group-bys).
+
+A step is one lmf_run of the whole batch (child views, root scan, combine,
+placement) with the inputs resident in HBM.  Metric: joined tuples x
+aggregates / step time, in G joined-tuple-aggregates/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs its own seeded instance (weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = 'G joined-tuple-aggregates/s, HBM % of peak; speedup vs plain at ≤1e-6 rel err'
+UNIT = 'G joined-tuple-aggregates/s'
+PROFILE_SUMMARY = os.path.join(ROOT, 'profiles', 'root_scan_snowflake20M.md')
+KERNEL_SOURCES = ['paper_1906_08687_gb300/csrc/lmf_kernels.cu',
+                  'paper_1906_08687_gb300/csrc/lmf_gram_tc.cu']
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=20)
+    ap.add_argument('--warmup', type=int, default=5)
+    ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--n-fact', type=int, default=20_000_000)
+    ap.add_argument('--precision', default='split', choices=['split', 'plain'])
+    ap.add_argument('--cpu-sample-rows', type=int, default=10_000_000)
+    ap.add_argument('--ref-sample-rows', type=int, default=200_000)
+    ap.add_argument('--check-aggs', type=int, default=48,
+                    help='aggregates re-evaluated by the oracle over the full join (0: skip)')
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device='cuda')
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+         'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+         'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(['nvidia-smi', f'--query-gpu={self.Q}', '--format=csv,noheader,nounits',
+                                          '-i', str(self.index), '-lms', '200'],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['nvidia-smi unavailable']}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=5)
+        sm, smax, reasons = [], None, set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(',')]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == 'active':
+                    reasons.add(n)
+        return {'sm_mhz': statistics.median(sm) if sm else None, 'sm_max_mhz': smax,
+                'reasons': sorted(reasons), 'samples': len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, 'MEASURED_PEAKS.json')
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {'hbm_gbs': d['hbm_gbs'], 'bf16_tflops': d['bf16_tflops'], 'source': 'measured'}
+    return {'hbm_gbs': 6800.0, 'bf16_tflops': 1900.0, 'source': 'fallback'}
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), 'rb') as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(precision: str):
+    """DRAM bytes per root-scan launch from the committed ncu summary, when it
+    was taken on the current kernel sources (else None)."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    with open(PROFILE_SUMMARY) as f:
+        text = f.read()
+    m = re.search(rf'traffic_bytes_per_launch\[{precision}\]:\s*([0-9.e+]+)\s+sources:\s*([0-9a-f]+)', text)
+    if not m or m.group(2) != kernel_hash():
+        return None
+    return float(m.group(1))
+
+
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    """The oracle on this host's cores, one bounded sample of the workload per step."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle
+    from workloads import config2
+    oracle.build()
+    sch, batch = config2(args.n_fact)
+    S = min(args.ref_sample_rows, args.n_fact)
+    nt = oracle.max_threads()
+    times = []
+    for i in range(args.warmup + args.steps):
+        b = (i * S) % max(1, args.n_fact - S + 1)
+        t0 = time.perf_counter()
+        res = oracle.evaluate(sch, batch, root_range=(b, b + S), nthreads=nt)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    t = sum(times) / len(times)
+    value = res.join_size * len(batch) / t / 1e9
+    sample = (f'{S} consecutive fact rows per step (of {args.n_fact}), all {len(batch)} aggregates, '
+              f'full dimension tables')
+    line = {
+        'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': ws,
+        'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': t * 1e3, 'higher_is_better': True,
+        'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+        'config': {'workload': f'snowflake-{args.n_fact}', 'n_aggregates': len(batch),
+                   'sample_rows_per_step': S},
+        'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': nt, 'kind': 'oracle', 'sample': sample},
+        'e2e': {'value': value, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == 'reference':
+        return run_reference(args)
+    ws, rank, local = dist_env()
+    import numpy as np
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl')
+    torch.cuda.set_device(local)
+    sys.path.insert(0, os.path.join(ROOT, 'tests'))
+    from paper_1906_08687_gb300 import build as engine_build
+    engine_build.build()
+    from paper_1906_08687_gb300 import Engine, register_schema
+    from paper_1906_08687_gb300.lmf import STAGE_NAMES
+    from workloads import config2, SEED_BASE
+    from lmf_testlib import compare, to_device, to_pinned
+
+    sch, batch = config2(args.n_fact, seed=SEED_BASE + 2 + 1000 * rank)
+    n_agg = len(batch)
+    dev = to_device(sch, f'cuda:{local}')
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    prec = 1 if args.precision == 'split' else 0
+
+    def make(precision, batching, tensors, on_host=False):
+        eng = Engine(local)
+        register_schema(eng, sch, tensors, on_host=on_host)
+        bid = eng.declare_batch(batch)
+        eng.plan(bid, precision=precision, batching=batching)
+        return eng, bid
+
+    def timed(eng, bid, steps, warmup, sampler=None):
+        for _ in range(warmup):
+            eng.run(bid, sh)
+        torch.cuda.synchronize()
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if sampler:
+            sampler.start()
+        e0.record(stream)
+        for _ in range(steps):
+            eng.run(bid, sh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        barrier(ws)
+        eng.sync(bid)
+        return max_over_ranks(ws, e0.elapsed_time(e1) / steps), clocks
+
+    # chosen form: split-bf16 Gram (when planned), one CUDA graph per run
+    eng, bid = make(prec, 1, dev)
+    info = eng.plan_info(bid)
+    join_rows = info['root_rows']   # unique dimension keys: |join| = fact rows
+    sampler = ClockSampler(local)
+    ms, clocks = timed(eng, bid, args.steps, args.warmup, sampler)
+    value = ws * join_rows * n_agg / (ms * 1e-3) / 1e9
+
+    info = eng.plan_info(bid)   # kernel count is known once the plan has run
+    # per-stage device times (same plan, launched stage by stage with events)
+    stage = np.zeros(len(STAGE_NAMES))
+    for _ in range(args.steps):
+        stage += np.array(eng.run_profiled(bid, sh))
+    stage /= args.steps
+    root_ms = float(stage[STAGE_NAMES.index('root_scan')])
+
+    # results of the chosen form for the accuracy check
+    got = eng.results(bid, n_agg)
+
+    # plain form: FP32 CUDA-core Gram, kernels enqueued one by one
+    eng_p, bid_p = make(0, 0, dev)
+    ms_plain, _ = timed(eng_p, bid_p, args.steps, args.warmup)
+    eng_p.close()
+
+    # end to end through the C ABI from pinned host buffers
+    host = to_pinned(sch)
+    eng_e, bid_e = make(prec, 1, host, on_host=True)
+    n_i64, n_f64 = eng_e.result_sizes(bid_e)
+    out_i = torch.empty(max(1, n_i64), dtype=torch.int64).pin_memory()
+    out_f = torch.empty(max(1, n_f64), dtype=torch.float64).pin_memory()
+    for _ in range(args.warmup):
+        eng_e.run(bid_e, sh)
+        eng_e.read_results(bid_e, out_i.data_ptr(), out_f.data_ptr(), False, sh)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        eng_e.run(bid_e, sh)
+        eng_e.read_results(bid_e, out_i.data_ptr(), out_f.data_ptr(), False, sh)
+    e2e_ms = max_over_ranks(ws, (time.perf_counter() - t0) * 1e3 / args.steps)
+    eng_e.sync(bid_e)
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = 8 * (n_i64 + n_f64)
+    eng_e.close()
+
+    # roofline of the root scan: algorithmic bytes = fact columns read once
+    # plus every probed view record once
+    R = sch.rel(sch.root)
+    fact_bytes = sum(c.data.dtype.itemsize * R.nrows for c in R.columns)
+    view_bytes = 0
+    for r in sch.relations:
+        if r.name != sch.root:
+            view_bytes += sum(c.data.dtype.itemsize * r.nrows for c in r.columns)
+    algo = fact_bytes + view_bytes
+    peaks = measured_peaks()
+    achieved = algo / (root_ms * 1e-3) / 1e9
+    roof = {'bound': 'hbm', 'achieved': achieved, 'peak': peaks['hbm_gbs'], 'unit': 'GB/s',
+            'frac': achieved / peaks['hbm_gbs'], 'traffic': profiled_traffic(args.precision),
+            'peak_source': peaks['source'], 'kernel': 'root scan (stage root_scan)',
+            'algorithmic_bytes_per_launch': algo, 'launch_ms': root_ms,
+            'stage_ms': {n: float(v) for n, v in zip(STAGE_NAMES, stage)}}
+
+    line = {
+        'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': ws, 'steps': args.steps,
+        'warmup': args.warmup, 'ms_per_step': ms, 'higher_is_better': True, 'scaling': 'weak',
+        'vs_baseline': None,
+        'dtype': 'bf16-split3/f32-acc' if info['precision'] == 1 else 'f32',
+        'data': 'synthetic',
+        'config': {'workload': f'snowflake-{args.n_fact} (3 FKs, 8 fact + 22 dimension features, '
+                               f'10 categoricals; covar + grouped + pair counts)',
+                   'n_aggregates': n_agg, 'join_rows': join_rows, 'precision': info['precision'],
+                   'batching': 'cuda-graph', 'kernels_per_step': info['n_kernels_per_run'],
+                   'l2': f'inputs larger than L2 ({fact_bytes / 1e6:.0f} MB fact table per step)',
+                   'parallelism': f'replicas x{ws}'},
+        'hbm_pct_of_peak': 100.0 * roof['frac'],
+        'speedup_vs_plain': ms_plain / ms, 'plain_ms_per_step': ms_plain,
+        'roofline': roof,
+        'e2e': {'value': ws * join_rows * n_agg / (e2e_ms * 1e-3) / 1e9, 'unit': UNIT,
+                'h2d_bytes_per_step': h2d, 'd2h_bytes_per_step': d2h, 'ms_per_step': e2e_ms},
+        'gpu_launches': info['n_kernels_per_run'] * args.steps,
+        'clocks': clocks,
+    }
+
+    if rank == 0 and args.check_aggs > 0:
+        from oracle import oracle
+        oracle.build()
+        rng = np.random.default_rng(0)
+        pick = sorted(set([0] + list(rng.choice(n_agg, size=min(args.check_aggs, n_agg), replace=False))))
+        want = oracle.evaluate(sch, [batch[i] for i in pick])
+        fails, stats = compare([got[i] for i in pick], want)
+        line['accuracy'] = {'checked_aggregates': len(pick), 'failures': len(fails), **stats,
+                            'rule': '|g-r| <= 1e-6*max(|r|, 1e-3*sum|v|); counts exact'}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import oracle
+        oracle.build()
+        S = min(args.cpu_sample_rows, args.n_fact)
+        nt = oracle.max_threads()
+        t0 = time.perf_counter()
+        res = oracle.evaluate(sch, batch, root_range=(0, S), nthreads=nt)
+        dt = time.perf_counter() - t0
+        line['cpu_baseline'] = {'value': res.join_size * n_agg / dt / 1e9, 'unit': UNIT, 'cores': nt,
+                                'kind': 'oracle',
+                                'sample': f'first {S} fact rows of the same workload, all {n_agg} '
+                                          f'aggregates ({dt:.1f} s)'}
+    eng.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == '__main__':
+    sys.exit(main())

@@ -196,6 +196,21 @@ lmf_status lmf_plan_info(lmf_ctx* ctx, int batch_id, lmf_plan_stats* info);
  */
 lmf_status lmf_run(lmf_ctx* ctx, int batch_id, void* cuda_stream);
 
+/* stages reported by lmf_run_profiled, in launch order */
+#define LMF_STAGE_INPUT    0   /* host-resident column copies, accumulator reset */
+#define LMF_STAGE_VIEWS    1   /* child views, deepest first (Sec. 3.2) */
+#define LMF_STAGE_ROOT     2   /* the root scan: Gram, counts, grouped tables (Sec. 3.5) */
+#define LMF_STAGE_TREE     3   /* threshold-filtered histograms (Sec. 2, regression trees) */
+#define LMF_STAGE_FINALIZE 4   /* ordered combine of partials and result placement */
+#define LMF_STAGES         5
+
+/*
+ * Like lmf_run without graph replay, with a CUDA event recorded on
+ * `cuda_stream` at every stage boundary; waits for the run and writes the
+ * LMF_STAGES stage durations in milliseconds to stage_ms (host array).
+ */
+lmf_status lmf_run_profiled(lmf_ctx* ctx, int batch_id, void* cuda_stream, float* stage_ms);
+
 /*
  * Wait for the last run of the batch and return its device status: LMF_OK,
  * LMF_ERR_KEY (a category outside its domain), LMF_ERR_OVERFLOW,

@@ -812,11 +812,14 @@ extern "C" lmf_status lmf_plan(lmf_ctx* c, int batch_id, const lmf_plan_opts* op
   int cps = P->opts.ctas_per_sm > 0 ? P->opts.ctas_per_sm : (mp <= 32 ? 2 : 1);
   P->grid = (int)std::max<int64_t>(1, std::min<int64_t>(P->n_tiles, (int64_t)c->num_sms * cps));
   CUDA_TRY(c, root_plain_prepare(mp, P->smem));
-  bool use_tc = P->opts.precision == LMF_PREC_SPLIT_BF16 && gram_tc_supported(m);
+  // the split-bf16 tensor-core Gram needs w in {0, 1} (unique child keys) and
+  // z within one 32-feature block; other plans keep the plain FP32 Gram
+  bool use_tc = P->opts.precision == LMF_PREC_SPLIT_BF16 && gram_tc_supported(m) && P->unique_all;
   if (P->opts.precision == LMF_PREC_SPLIT_BF16 && !use_tc) P->opts.precision = LMF_PREC_PLAIN_FP32;
   if (use_tc) {
     P->tc = std::make_unique<GramTcPlan>();
     gram_tc_shape(m, Root.nrows, c->num_sms, P->opts.tile_rows, P->tc.get());
+    CUDA_TRY(c, gram_tc_configure(P->tc.get(), ncat, P->opts.ctas_per_sm));
     P->grid = P->tc->grid;
   }
   P->part_off = A.take((size_t)P->grid * mp * mp * 8);
@@ -1021,15 +1024,21 @@ extern "C" lmf_status lmf_plan(lmf_ctx* c, int batch_id, const lmf_plan_opts* op
 
 namespace {
 
-lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s) {
+// ev (optional): LMF_STAGES + 1 events recorded on s at the stage boundaries
+lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   Plan* P = B.plan.get();
   int nk = 0;
+  auto mark = [&](int i) {
+    if (ev) cudaEventRecord(ev[i], s);
+  };
+  mark(0);
   // host-resident columns are copied in first
   for (auto& r : c->rels)
     for (auto& col : r.cols)
       if (col.on_host && r.nrows > 0)
         CUDA_TRY(c, cudaMemcpyAsync(col.dev, col.data, (size_t)r.nrows * col.esize(), cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemsetAsync(P->arena.base + P->zero_off, 0, P->zero_len, s));
+  mark(1);
   // child views, deepest first
   for (int r : P->post) {
     RelPlan& cp = P->rp[r];
@@ -1114,6 +1123,7 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s) {
     CUDA_TRY(c, launch_view_finalize(f, s));
     nk += 2;
   }
+  mark(2);
   // root scan: Gram, counts, reverse views, per-row grouped tables
   if (P->tc) {
     CUDA_TRY(c, gram_tc_launch(P->tc.get(), P->rootp, s));
@@ -1122,12 +1132,18 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s) {
     CUDA_TRY(c, launch_root_plain(P->rootp, P->mp, P->grid, P->n_tiles, P->smem, s));
     ++nk;
   }
+  mark(3);
   if (P->tree) {
     CUDA_TRY(c, tree_launch(P->tree.get(), P->rootp, s, &nk));
   }
-  CUDA_TRY(c, launch_combine(P->at<double>(P->part_off), P->grid, P->mp, P->rootp.m,
-                             P->at<long long>(P->cntp_off), P->at<double>(P->G_off),
-                             P->at<long long>(P->count_off), s));
+  mark(4);
+  if (P->tc) {
+    CUDA_TRY(c, gram_tc_combine(P->tc.get(), P->rootp, P->at<double>(P->G_off), P->at<long long>(P->count_off), s));
+  } else {
+    CUDA_TRY(c, launch_combine(P->at<double>(P->part_off), P->grid, P->mp, P->rootp.m,
+                               P->at<long long>(P->cntp_off), P->at<double>(P->G_off),
+                               P->at<long long>(P->count_off), s));
+  }
   ++nk;
   if (!P->corr.empty()) {
     CUDA_TRY(c, launch_corr(P->arena.base + P->corr_off, (int)P->corr.size(), P->at<double>(P->G_off), P->rootp.m, s));
@@ -1138,11 +1154,14 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s) {
     ++nk;
   }
   if (!P->maps.empty()) {
-    CUDA_TRY(c, launch_out_map(P->at<OutMap>(P->maps_off), (int)P->maps.size(), P->at<double>(P->G_off), P->rootp.m,
+    int64_t max_cells = 1;
+    for (auto& o : P->maps) max_cells = std::max<int64_t>(max_cells, o.n);
+    CUDA_TRY(c, launch_out_map(P->at<OutMap>(P->maps_off), (int)P->maps.size(), max_cells, P->at<double>(P->G_off), P->rootp.m,
                                P->at<long long>(P->count_off), P->at<long long>(P->res_i64_off),
                                P->at<double>(P->res_f64_off), s));
     ++nk;
   }
+  mark(5);
   P->n_kernels = nk;
   return LMF_OK;
 }
@@ -1198,6 +1217,25 @@ lmf_status lmf_run(lmf_ctx* c, int batch_id, void* cuda_stream) {
     return LMF_OK;
   }
   return enqueue(c, B, s);
+}
+
+lmf_status lmf_run_profiled(lmf_ctx* c, int batch_id, void* cuda_stream, float* stage_ms) {
+  if (!c || !stage_ms || batch_id < 0 || batch_id >= (int)c->batches.size())
+    return fail(c, LMF_ERR_ARG, "run_profiled: bad argument");
+  BatchH& B = *c->batches[batch_id];
+  if (!B.plan) return fail(c, LMF_ERR_STATE, "run before plan");
+  cudaSetDevice(c->device);
+  cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
+  B.last_stream = s;
+  cudaEvent_t ev[LMF_STAGES + 1];
+  for (auto& e : ev) CUDA_TRY(c, cudaEventCreate(&e));
+  lmf_status st = enqueue(c, B, s, ev);
+  if (st == LMF_OK) {
+    CUDA_TRY(c, cudaEventSynchronize(ev[LMF_STAGES]));
+    for (int i = 0; i < LMF_STAGES; ++i) cudaEventElapsedTime(&stage_ms[i], ev[i], ev[i + 1]);
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return st;
 }
 
 lmf_status lmf_sync(lmf_ctx* c, int batch_id) {

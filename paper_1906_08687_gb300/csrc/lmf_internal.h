@@ -190,7 +190,7 @@ cudaError_t launch_combine(const double* part, int grid, int mp, int m, const lo
 cudaError_t launch_corr(const void* tasks_dev, int n, double* G, int m, cudaStream_t s);
 cudaError_t launch_rv_tasks(const RvTask* tasks, int n_tasks, const RootParams& p,
                             int max_K, cudaStream_t s);
-cudaError_t launch_out_map(const OutMap* maps, int n_maps, const double* G, int m,
+cudaError_t launch_out_map(const OutMap* maps, int n_maps, int64_t max_cells, const double* G, int m,
                            const long long* count, long long* res_i64, double* res_f64,
                            cudaStream_t s);
 cudaError_t launch_colmaxabs(const Col* cols, int n, int64_t nrows, double* out, cudaStream_t s);

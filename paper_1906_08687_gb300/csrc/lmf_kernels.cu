@@ -8,6 +8,7 @@
 //   grouped covar entries Covar(X_j; X_k), Covar(X_j, X_k; 1) -> reverse views + k_rv_tasks / DirectAgg
 //   cross-block combine and placement                          -> k_combine, k_corr, k_out_map
 #include "lmf_internal.h"
+#include "lmf_rowpass.cuh"
 
 #include <cstdint>
 #include <cstdio>
@@ -252,18 +253,6 @@ cudaError_t launch_view_finalize(const ViewFinalizeArgs& a, cudaStream_t s) {
 // partial Gram.
 constexpr int kPlainT = 256;
 
-__device__ __forceinline__ void put_word(float* zrow, int32_t* crow, const RootParams& p, int g, int w,
-                                         uint32_t v, long long& cnt) {
-  const GroupDesc& G = p.grp[g];
-  if (w < G.n_cnt) {
-    cnt *= static_cast<long long>(v);
-  } else if (w < G.n_cnt + G.n_mu) {
-    zrow[p.grp_zoff[g] + (w - G.n_cnt)] = __uint_as_float(v);
-  } else if (w < G.n_cnt + G.n_mu + G.n_cat) {
-    crow[p.grp_catoff[g] + (w - G.n_cnt - G.n_mu)] = static_cast<int32_t>(v);
-  }
-}
-
 template <int MP>
 __global__ void __launch_bounds__(256) k_root_plain(const __grid_constant__ RootParams p, int64_t n_tiles) {
   constexpr int T = kPlainT;
@@ -295,43 +284,7 @@ __global__ void __launch_bounds__(256) k_root_plain(const __grid_constant__ Root
       const int64_t row = tile * T + tid;
       float* zrow = Zb + tid * LD;
       int32_t* crow = Cs + tid * (p.n_rowcat > 0 ? p.n_rowcat : 1);
-      long long w = 0;
-#pragma unroll
-      for (int i = 0; i < MP; ++i) zrow[i] = 0.f;
-      if (row < p.N) {
-        w = 1;
-        zrow[0] = 1.f;
-        for (int i = 0; i < p.n_x; ++i) zrow[1 + i] = load_f(p.x[i], row);
-        for (int g = 0; g < p.n_grp; ++g) {
-          const GroupDesc& G = p.grp[g];
-          const int32_t fk = G.fk[row];
-          if (fk < 0 || fk >= G.K) {
-            w = 0;
-            continue;
-          }
-          const uint4* rec = reinterpret_cast<const uint4*>(G.rec + (int64_t)fk * G.stride);
-          const int nw = G.n_cnt + G.n_mu + G.n_cat;
-          for (int q = 0; q < (nw + 3) / 4; ++q) {
-            const uint4 v = __ldg(rec + q);
-            put_word(zrow, crow, p, g, 4 * q + 0, v.x, w);
-            put_word(zrow, crow, p, g, 4 * q + 1, v.y, w);
-            put_word(zrow, crow, p, g, 4 * q + 2, v.z, w);
-            put_word(zrow, crow, p, g, 4 * q + 3, v.w, w);
-          }
-        }
-        for (int i = 0; i < p.n_rcat; ++i) {
-          int32_t v = p.rcat[i][row];
-          if (v < 0 || v >= p.rcat_dom[i]) {
-            atomicOr(p.status, kStatusCatRange);
-            v = 0;
-          }
-          crow[p.n_rowcat - p.n_rcat + i] = v;
-        }
-      }
-      if (w == 0) {
-#pragma unroll
-        for (int i = 0; i < MP; ++i) zrow[i] = 0.f;
-      }
+      const long long w = root_row_pass<MP>(p, row, zrow, crow);
       cnt_acc += w;
       // w * z for the left operand
       const float wf = static_cast<float>(w);
@@ -344,29 +297,6 @@ __global__ void __launch_bounds__(256) k_root_plain(const __grid_constant__ Root
         v.z *= wf;
         v.w *= wf;
         *reinterpret_cast<float4*>(arow + 4 * q) = v;
-      }
-      // grouped updates of this row
-      if (w != 0) {
-        for (int r = 0; r < p.n_rv; ++r) {
-          const RevView& R = p.rv[r];
-          const int32_t fk = p.grp[R.grp].fk[row];
-          atomicAdd(R.hist + fk, static_cast<unsigned long long>(w));
-          long long* dst = R.R + (int64_t)fk * R.n_slot;
-          for (int s = 0; s < R.n_slot; ++s) add_ll(dst + s, fixp(w, zrow[R.slot_z[s]], R.slot_scale[s]));
-        }
-        for (int d = 0; d < p.n_direct; ++d) {
-          const DirectAgg& A = p.direct[d];
-          int64_t cell = 0;
-          for (int q = 0; q < A.n_gb; ++q) cell = cell * A.dom[q] + crow[A.cat[q]];
-          add_ll(A.out + cell, A.z < 0 ? w : fixp(w, zrow[A.z], A.scale));
-        }
-        for (int o = 0; o < p.n_om; ++o) {
-          const OmegaAcc& O = p.om[o];
-          const GroupDesc& G = p.grp[O.grp];
-          const int32_t fk = G.fk[row];
-          const long long ce = static_cast<long long>(G.rec[(int64_t)fk * G.stride + O.cnt_word]);
-          atomicAdd(O.omega + fk, static_cast<unsigned long long>(w / ce));
-        }
       }
     }
     __syncthreads();
@@ -538,32 +468,35 @@ cudaError_t launch_rv_tasks(const RvTask* tasks, int n_tasks, const RootParams& 
   return cudaGetLastError();
 }
 
-// final placement of every aggregate
+// final placement of every aggregate: blockIdx.y = map, blocks of x stride the cells
 __global__ void k_out_map(const OutMap* maps, const double* G, int m, const long long* count,
                           long long* res_i64, double* res_f64) {
-  const OutMap o = maps[blockIdx.x];
+  const OutMap o = maps[blockIdx.y];
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
   switch (o.kind) {
     case 0:
-      if (threadIdx.x == 0) res_i64[o.dst] = *count;
+      if (t0 == 0) res_i64[o.dst] = *count;
       break;
     case 1:
-      if (threadIdx.x == 0) res_f64[o.dst] = G[o.i * m + o.j];
+      if (t0 == 0) res_f64[o.dst] = G[o.i * m + o.j];
       break;
     case 2:
     case 4:
-      for (int64_t c = threadIdx.x; c < o.n; c += blockDim.x) res_i64[o.dst + c] = o.src[c];
+      for (int64_t c = t0; c < o.n; c += step) res_i64[o.dst + c] = o.src[c];
       break;
     default:
-      for (int64_t c = threadIdx.x; c < o.n; c += blockDim.x)
-        res_f64[o.dst + c] = (double)o.src[c] * o.inv_scale;
+      for (int64_t c = t0; c < o.n; c += step) res_f64[o.dst + c] = (double)o.src[c] * o.inv_scale;
       break;
   }
 }
 
-cudaError_t launch_out_map(const OutMap* maps, int n_maps, const double* G, int m, const long long* count,
-                           long long* res_i64, double* res_f64, cudaStream_t s) {
+cudaError_t launch_out_map(const OutMap* maps, int n_maps, int64_t max_cells, const double* G, int m,
+                           const long long* count, long long* res_i64, double* res_f64, cudaStream_t s) {
   if (n_maps <= 0) return cudaSuccess;
-  k_out_map<<<n_maps, 128, 0, s>>>(maps, G, m, count, res_i64, res_f64);
+  int64_t bx = (max_cells + 255) / 256;
+  dim3 grid((unsigned)(bx < 64 ? (bx > 0 ? bx : 1) : 64), (unsigned)n_maps);
+  k_out_map<<<grid, 256, 0, s>>>(maps, G, m, count, res_i64, res_f64);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,8 @@ LMF_POW, LMF_LE, LMF_GT = 0, 1, 2
 LMF_PREC_PLAIN_FP32, LMF_PREC_SPLIT_BF16 = 0, 1
 LMF_BATCH_SINGLE, LMF_BATCH_GRAPH = 0, 1
 LMF_MAX_GROUP_BY = 3
+LMF_STAGES = 5
+STAGE_NAMES = ['input', 'views', 'root_scan', 'tree', 'finalize']
 
 _ROLE = {'key': LMF_KEY, 'cont': LMF_CONT, 'cat': LMF_CAT}
 _KIND = {'pow': LMF_POW, 'le': LMF_LE, 'gt': LMF_GT}
@@ -75,6 +77,7 @@ _SIGNATURES = {
     'lmf_plan_info': (_I, [_P, _I, ctypes.POINTER(lmf_plan_stats)]),
     'lmf_run': (_I, [_P, _I, _P]),
     'lmf_sync': (_I, [_P, _I]),
+    'lmf_run_profiled': (_I, [_P, _I, _P, ctypes.POINTER(ctypes.c_float)]),
     'lmf_result_info': (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_int64),
                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
     'lmf_result_sizes': (_I, [_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
@@ -207,6 +210,12 @@ class Engine:
 
     def run(self, batch: int, stream: int = 0):
         self._check(self.lib.lmf_run(self.ctx, batch, ctypes.c_void_p(stream)), 'lmf_run')
+
+    def run_profiled(self, batch: int, stream: int = 0) -> List[float]:
+        ms = (ctypes.c_float * LMF_STAGES)()
+        self._check(self.lib.lmf_run_profiled(self.ctx, batch, ctypes.c_void_p(stream), ms),
+                    'lmf_run_profiled')
+        return list(ms)
 
     def sync(self, batch: int):
         self._check(self.lib.lmf_sync(self.ctx, batch), 'lmf_sync')

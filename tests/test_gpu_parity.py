@@ -32,6 +32,7 @@ def test_config1_star_full(precision, batching):
     sch, batch = config1()
     _, info, stats = _check(sch, batch, precision, batching)
     assert info['n_gram_aggs'] == 65 and info['z_len'] == 11
+    assert info['precision'] == precision     # SPLIT runs on the tcgen05 kernel
 
 
 def test_config1_ragged_sizes():
@@ -44,6 +45,7 @@ def test_config1_ragged_sizes():
 def test_config2_snowflake_reduced(precision):
     sch, batch = config2(300_007)
     _, info, stats = _check(sch, batch, precision, GRAPH)
+    assert info['precision'] == precision
     assert info['n_grouped_aggs'] == 10 * 31 + 45
     assert info['n_views'] == 6 and info['n_probe_groups'] == 3
 
