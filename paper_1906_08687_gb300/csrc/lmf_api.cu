@@ -143,6 +143,7 @@ struct Plan {
   int n_kernels = 0;
   bool unique_all = true;
   int n_views = 0, n_gram = 0, n_grouped = 0, n_filtered = 0;
+  bool root_scan = true;         // some aggregate needs the Gram / counts / grouped tables
   template <class T>
   T* at(size_t off) const { return reinterpret_cast<T*>(arena.base + off); }
 };
@@ -777,6 +778,18 @@ extern "C" lmf_status lmf_plan(lmf_ctx* c, int batch_id, const lmf_plan_opts* op
   for (size_t a = 0; a < B.aggs.size(); ++a)
     if (cls[a].kind == 2) filt_idx.push_back((int)a);
   if (!filt_idx.empty()) {
+    // thresholds and squares are not linear in the attribute: they need the
+    // attribute's value in every joined tuple, i.e. a relation reached from the
+    // root through unique keys only (its value is then a function of the root row)
+    for (int a : filt_idx)
+      for (auto& f : B.aggs[a].f) {
+        int col, r = owner_of(c, f.attr, &col);
+        for (int x = r; x != root; x = c->rels[x].parent)
+          if (c->rels[x].max_mult > 1)
+            return fail(c, LMF_ERR_UNSUPPORTED,
+                        "aggregate %d: threshold or power factor on %s below the fanning-out key of %s", a,
+                        f.attr.c_str(), c->rels[x].name.c_str());
+      }
     P->tree = std::make_unique<TreePlan>();
     std::vector<TreeAggIn> in;
     for (int a : filt_idx) {
@@ -792,7 +805,7 @@ extern "C" lmf_status lmf_plan(lmf_ctx* c, int batch_id, const lmf_plan_opts* op
     if (s) return fail(c, s, "%s", msg.c_str());
     P->n_filtered = (int)filt_idx.size();
   }
-  if (P->tree) tree_alloc_zeroed(P->tree.get(), [&](size_t n) { return A.take(n); });
+  if (P->tree) tree_alloc_zeroed(P->tree.get(), Root.nrows, [&](size_t n) { return A.take(n); });
   P->zero_off = zero_begin;
   P->zero_len = A.take(0) - zero_begin;
   // within-key scatter of fanning-out views: fully rewritten by every run
@@ -827,7 +840,7 @@ extern "C" lmf_status lmf_plan(lmf_ctx* c, int batch_id, const lmf_plan_opts* op
   P->G_off = A.take((size_t)m * m * 8);
   P->count_off = A.take(8);
   if (use_tc) gram_tc_alloc(P->tc.get(), [&](size_t n) { return A.take(n); });
-  if (P->tree) tree_alloc(P->tree.get(), [&](size_t n) { return A.take(n); });
+  if (P->tree) tree_alloc(P->tree.get(), Root.nrows, [&](size_t n) { return A.take(n); });
 
   // results
   P->agg_dtype.resize(B.aggs.size());
@@ -1018,6 +1031,7 @@ extern "C" lmf_status lmf_plan(lmf_ctx* c, int batch_id, const lmf_plan_opts* op
     gram_tc_finish(P->tc.get(), rp, P->arena.base);
   }
   P->n_views = (int)P->post.size();
+  P->root_scan = !P->maps.empty();
   B.plan = std::move(P);
   return LMF_OK;
 }
@@ -1124,12 +1138,14 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
     nk += 2;
   }
   mark(2);
-  // root scan: Gram, counts, reverse views, per-row grouped tables
-  if (P->tc) {
-    CUDA_TRY(c, gram_tc_launch(P->tc.get(), P->rootp, s));
-    nk += 1;
-  } else {
-    CUDA_TRY(c, launch_root_plain(P->rootp, P->mp, P->grid, P->n_tiles, P->smem, s));
+  // root scan: Gram, counts, reverse views, per-row grouped tables (skipped when
+  // the batch has only threshold-filtered aggregates)
+  if (P->root_scan) {
+    if (P->tc) {
+      CUDA_TRY(c, gram_tc_launch(P->tc.get(), P->rootp, s));
+    } else {
+      CUDA_TRY(c, launch_root_plain(P->rootp, P->mp, P->grid, P->n_tiles, P->smem, s));
+    }
     ++nk;
   }
   mark(3);
@@ -1137,14 +1153,16 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
     CUDA_TRY(c, tree_launch(P->tree.get(), P->rootp, s, &nk));
   }
   mark(4);
-  if (P->tc) {
-    CUDA_TRY(c, gram_tc_combine(P->tc.get(), P->rootp, P->at<double>(P->G_off), P->at<long long>(P->count_off), s));
-  } else {
-    CUDA_TRY(c, launch_combine(P->at<double>(P->part_off), P->grid, P->mp, P->rootp.m,
-                               P->at<long long>(P->cntp_off), P->at<double>(P->G_off),
-                               P->at<long long>(P->count_off), s));
+  if (P->root_scan) {
+    if (P->tc) {
+      CUDA_TRY(c, gram_tc_combine(P->tc.get(), P->rootp, P->at<double>(P->G_off), P->at<long long>(P->count_off), s));
+    } else {
+      CUDA_TRY(c, launch_combine(P->at<double>(P->part_off), P->grid, P->mp, P->rootp.m,
+                                 P->at<long long>(P->cntp_off), P->at<double>(P->G_off),
+                                 P->at<long long>(P->count_off), s));
+    }
+    ++nk;
   }
-  ++nk;
   if (!P->corr.empty()) {
     CUDA_TRY(c, launch_corr(P->arena.base + P->corr_off, (int)P->corr.size(), P->at<double>(P->G_off), P->rootp.m, s));
     ++nk;
@@ -1163,6 +1181,19 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
   }
   mark(5);
   P->n_kernels = nk;
+  return LMF_OK;
+}
+
+// The tree-node histogram pass is autotuned once, on the first run, before any
+// graph capture: one plain run fills the per-row buffers, then the tuner times
+// its shape candidates on them and keeps the fastest.
+lmf_status ensure_tuned(lmf_ctx* c, BatchH& B, cudaStream_t s) {
+  Plan* P = B.plan.get();
+  if (!P->tree || !tree_needs_tuning(P->tree.get())) return LMF_OK;
+  lmf_status st = enqueue(c, B, s);
+  if (st) return st;
+  CUDA_TRY(c, tree_autotune(P->tree.get(), P->rootp, s));
+  CUDA_TRY(c, cudaStreamSynchronize(s));
   return LMF_OK;
 }
 
@@ -1198,6 +1229,10 @@ lmf_status lmf_run(lmf_ctx* c, int batch_id, void* cuda_stream) {
   cudaSetDevice(c->device);
   cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
   B.last_stream = s;
+  {
+    lmf_status st = ensure_tuned(c, B, s);
+    if (st) return st;
+  }
   if (P->opts.batching == LMF_BATCH_GRAPH) {
     if (!P->exec) {
       if (!P->graph_stream) CUDA_TRY(c, cudaStreamCreateWithFlags(&P->graph_stream, cudaStreamNonBlocking));
@@ -1227,6 +1262,10 @@ lmf_status lmf_run_profiled(lmf_ctx* c, int batch_id, void* cuda_stream, float* 
   cudaSetDevice(c->device);
   cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
   B.last_stream = s;
+  {
+    lmf_status st = ensure_tuned(c, B, s);
+    if (st) return st;
+  }
   cudaEvent_t ev[LMF_STAGES + 1];
   for (auto& e : ev) CUDA_TRY(c, cudaEventCreate(&e));
   lmf_status st = enqueue(c, B, s, ev);

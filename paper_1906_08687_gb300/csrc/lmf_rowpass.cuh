@@ -35,11 +35,10 @@ __device__ __forceinline__ void rp_put_word(float* zrow, int32_t* crow, const Ro
 }
 
 // Fills zrow[0, MP) (z, zero padded; all zero when the row does not join) and
-// crow[0, n_rowcat); applies the grouped updates; returns w (0 when the row is
-// outside the relation or one of its foreign keys dangles).
+// crow[0, n_rowcat); returns w (0 when the row is outside the relation or one of
+// its foreign keys dangles).
 template <int MP>
-__device__ __forceinline__ long long root_row_pass(const RootParams& p, int64_t row, float* zrow,
-                                                   int32_t* crow) {
+__device__ __forceinline__ long long root_row_z(const RootParams& p, int64_t row, float* zrow, int32_t* crow) {
 #pragma unroll
   for (int i = 0; i < MP; ++i) zrow[i] = 0.f;
   if (row >= p.N) return 0;
@@ -74,9 +73,13 @@ __device__ __forceinline__ long long root_row_pass(const RootParams& p, int64_t 
   if (w == 0) {
 #pragma unroll
     for (int i = 0; i < MP; ++i) zrow[i] = 0.f;
-    return 0;
   }
-  // grouped updates
+  return w;
+}
+
+// grouped updates of one joining row (w != 0)
+__device__ __forceinline__ void root_row_grouped(const RootParams& p, int64_t row, const float* zrow,
+                                                 const int32_t* crow, long long w) {
   for (int r = 0; r < p.n_rv; ++r) {
     const RevView& R = p.rv[r];
     const int32_t fk = p.grp[R.grp].fk[row];
@@ -97,6 +100,13 @@ __device__ __forceinline__ long long root_row_pass(const RootParams& p, int64_t 
     const long long ce = static_cast<long long>(G.rec[(int64_t)fk * G.stride + O.cnt_word]);
     atomicAdd(O.omega + fk, static_cast<unsigned long long>(w / ce));
   }
+}
+
+template <int MP>
+__device__ __forceinline__ long long root_row_pass(const RootParams& p, int64_t row, float* zrow,
+                                                   int32_t* crow) {
+  const long long w = root_row_z<MP>(p, row, zrow, crow);
+  if (w != 0) root_row_grouped(p, row, zrow, crow, w);
   return w;
 }
 

@@ -1,23 +1,695 @@
-// lmf_tree.cu -- filtered (tree-node) aggregates.
+// lmf_tree.cu -- threshold-filtered aggregates (regression-tree node batches).
+//
+// An aggregate SUM(m * 1[p_1] * ... * 1[p_k]) (Sec. 1.1: products of Kronecker
+// deltas; Sec. 2, Eq. regression-tree) is read as
+//     node (the conjunction of all but one predicate) x split (the remaining
+//     predicate x <= t or x > t on attribute f) x moment m (degree <= 2),
+// choosing as split the predicate that occurs in the fewest aggregates of the
+// batch (for a tree level: the candidate condition, while the ancestors'
+// conditions form the node).  Any choice gives the same product, so the
+// choice only affects speed.  With the sorted thresholds T_f of attribute f
+// and the bucket b(x) = #{t in T_f : t < x},
+//     x <= T_f[j]  <=>  b(x) <= j,
+// so every (node, f, j, m) aggregate is a prefix (or, for >, suffix) sum of
+// one histogram H[node][f][b][m].  Thresholds are rounded down to FP32, which
+// keeps x <= t exact for FP32 data.
+//
+// Kernels:
+//   k_tree_rows  one pass over the root rows: z from the views, the row's node
+//                in every group of mutually exclusive nodes, its bucket for
+//                every split attribute, its fixed-point moment values.
+//   k_tree_hist  persistent: CTAs own a slice (node range x split range) of the
+//                histogram in shared memory, pull row chunks from a per-slice
+//                work queue, accumulate exact 64-bit sums as two 32-bit atomics
+//                with carry, and flush once to global int64.
+//   k_tree_out   every aggregate as a prefix / suffix sum over the buckets.
 #include "lmf_tree.h"
+#include "lmf_rowpass.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <set>
+#include <tuple>
 
 namespace lmf {
 
-struct TreePlanImpl {};
+constexpr int kTreeMaxMom = 8;
+constexpr uint16_t kNoNode = 0xFFFF;
+
+struct TreePred {
+  int16_t z;
+  int16_t op;     // 0: x <= thr, 1: x > thr
+  float thr;
+};
+
+struct TreeOut {
+  int32_t node, split, j, op, mom, is_count;
+  int64_t dst;
+  double inv_scale;
+};
+
+struct TreeDev {
+  int32_t n_nodes, n_groups, n_split, max_bins, n_mom;
+  const int32_t* pred_off;     // [n_nodes + 1]
+  const TreePred* preds;
+  const int32_t* group_off;    // [n_groups + 1] into group_nodes
+  const int32_t* group_nodes;
+  const int16_t* split_z;      // [n_split]
+  const int32_t* thr_off;      // [n_split + 1]
+  const float* thr;
+  int16_t mom_a[kTreeMaxMom], mom_b[kTreeMaxMom];  // z indices, -1: absent
+  double mom_scale[kTreeMaxMom];                   // 0: the count moment (w itself)
+  uint16_t* node;              // [n_groups][N]
+  uint8_t* bucket;             // [n_split][N]
+  long long* momv;             // [n_mom][N]
+  long long* H;                // [n_nodes][n_split][max_bins][n_mom]
+  uint32_t* queue;             // [n_slices]
+  int64_t N;
+  uint32_t* status;
+};
+
+struct TreeShape {
+  int split_w, node_w, cps, chunk;
+};
+
+struct TreePlanImpl {
+  // host plan
+  std::vector<std::vector<TreePred>> nodes;
+  std::vector<std::vector<int>> groups;
+  std::vector<int16_t> split_z;
+  std::vector<std::string> split_name;
+  std::vector<std::vector<float>> thr;
+  std::vector<std::pair<std::string, std::string>> moms;  // attribute names ("" absent)
+  std::vector<std::pair<int, int>> mom_z;
+  struct OutH {
+    int node, split, j, op, mom;
+  };
+  std::vector<OutH> outs;
+  int max_bins = 1;
+  int mp = 16;
+  // device
+  size_t H_off = 0, queue_off = 0, node_off = 0, bucket_off = 0, momv_off = 0;
+  size_t tab_off = 0, tab_bytes = 0, outs_off = 0;
+  TreeDev dev{};
+  const TreeOut* d_outs = nullptr;
+  int n_outs = 0;
+  long long* res_i64 = nullptr;
+  double* res_f64 = nullptr;
+  int num_sms = 0;
+  TreeShape shape{1, 1, 1, 8192};
+  bool tuned = false;
+  int max_slices = 1;
+};
+
 TreePlan::~TreePlan() { delete impl; }
 
-lmf_status tree_plan(const std::vector<TreeAggIn>&, const std::map<std::string, int>&, TreePlan*,
+namespace {
+
+float round_down_f32(double t) {
+  float f = static_cast<float>(t);
+  if (static_cast<double>(f) > t) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+
+bool disjoint(const std::vector<TreePred>& a, const std::vector<TreePred>& b) {
+  for (const auto& p : a)
+    for (const auto& q : b) {
+      if (p.z != q.z || p.op == q.op) continue;
+      const TreePred& le = p.op == 0 ? p : q;
+      const TreePred& gt = p.op == 0 ? q : p;
+      if (gt.thr >= le.thr) return true;  // x <= t1 and x > t2 >= t1 cannot both hold
+    }
+  return false;
+}
+
+size_t slice_bytes(const TreePlanImpl& T, int node_w, int split_w) {
+  return static_cast<size_t>(node_w) * split_w * T.max_bins * T.dev.n_mom * 8;
+}
+
+int n_slices(const TreePlanImpl& T, const TreeShape& s) {
+  return ((T.dev.n_nodes + s.node_w - 1) / s.node_w) * ((T.dev.n_split + s.split_w - 1) / s.split_w);
+}
+
+}  // namespace
+
+lmf_status tree_plan(const std::vector<TreeAggIn>& in, const std::map<std::string, int>& zidx, TreePlan* tp,
                      std::string* msg) {
-  *msg = "threshold-filtered aggregates are not built yet";
-  return LMF_ERR_UNSUPPORTED;
+  tp->impl = new TreePlanImpl();
+  TreePlanImpl& T = *tp->impl;
+  // Split choice.  Removing predicate k of aggregate a leaves the candidate node
+  // N(a, k).  Every aggregate takes the split whose node is a candidate of the
+  // most aggregates (its "support"), so that aggregates sharing a conjunction
+  // share a node even when a candidate threshold equals one of the
+  // conjunction's own thresholds; ties go to the least frequent predicate.
+  using Key = std::tuple<std::string, int, double>;
+  std::map<Key, int> pid;
+  std::vector<int> freq;
+  std::vector<std::vector<int>> apred(in.size());
+  for (size_t i = 0; i < in.size(); ++i)
+    for (auto& f : in[i].factors)
+      if (f.kind != LMF_POW) {
+        auto it = pid.emplace(Key(f.attr, f.kind, f.thr), (int)pid.size()).first;
+        if ((int)freq.size() <= it->second) freq.push_back(0);
+        freq[it->second]++;
+        apred[i].push_back(it->second);
+      }
+  auto cand_node = [&](size_t i, size_t k) {
+    std::vector<int> n;
+    for (size_t j = 0; j < apred[i].size(); ++j)
+      if (j != k) n.push_back(apred[i][j]);
+    std::sort(n.begin(), n.end());
+    n.erase(std::unique(n.begin(), n.end()), n.end());
+    return n;
+  };
+  std::map<std::vector<int>, int> support;
+  for (size_t i = 0; i < in.size(); ++i) {
+    std::set<std::vector<int>> seen;
+    for (size_t k = 0; k < apred[i].size(); ++k) seen.insert(cand_node(i, k));
+    for (auto& n : seen) support[n]++;
+  }
+  std::vector<int> split_pos(in.size(), -1);  // position among the aggregate's predicates
+  for (size_t i = 0; i < in.size(); ++i) {
+    int best = -1, bs = -1, bf = 1 << 30;
+    for (size_t k = 0; k < apred[i].size(); ++k) {
+      const int s = support[cand_node(i, k)];
+      const int f = freq[apred[i][k]];
+      if (s > bs || (s == bs && f <= bf)) {
+        bs = s;
+        bf = f;
+        best = (int)k;
+      }
+    }
+    split_pos[i] = best;
+  }
+  std::map<std::vector<std::tuple<int, int, float>>, int> node_id;
+  std::map<std::string, int> split_id;
+  std::vector<std::set<float>> split_thr;
+  std::map<std::pair<std::string, std::string>, int> mom_id;
+  struct Pending {
+    int node, split, op, mom;
+    float t;
+  };
+  std::vector<Pending> pend;
+  for (size_t i = 0; i < in.size(); ++i) {
+    const auto& a = in[i];
+    int best = -1;
+    std::vector<std::string> mono;
+    for (size_t k = 0, np = 0; k < a.factors.size(); ++k) {
+      const auto& f = a.factors[k];
+      if (f.kind == LMF_POW) {
+        for (int e = 0; e < f.power; ++e) mono.push_back(f.attr);
+        continue;
+      }
+      if ((int)np++ == split_pos[i]) best = (int)k;
+    }
+    if (best < 0 || mono.size() > 2) {
+      *msg = "filtered aggregate without a threshold factor or with a monomial of degree > 2";
+      return LMF_ERR_UNSUPPORTED;
+    }
+    std::vector<std::tuple<int, int, float>> node;
+    for (size_t k = 0; k < a.factors.size(); ++k) {
+      const auto& f = a.factors[k];
+      if (f.kind == LMF_POW || (int)k == best) continue;
+      node.emplace_back(zidx.at(f.attr), f.kind == LMF_LE ? 0 : 1, round_down_f32(f.thr));
+    }
+    std::sort(node.begin(), node.end());
+    node.erase(std::unique(node.begin(), node.end()), node.end());
+    auto nit = node_id.find(node);
+    int nid;
+    if (nit == node_id.end()) {
+      nid = (int)T.nodes.size();
+      node_id[node] = nid;
+      std::vector<TreePred> preds;
+      for (auto& p : node) preds.push_back({(int16_t)std::get<0>(p), (int16_t)std::get<1>(p), std::get<2>(p)});
+      T.nodes.push_back(preds);
+    } else {
+      nid = nit->second;
+    }
+    const auto& sf = a.factors[best];
+    auto sit = split_id.find(sf.attr);
+    int sid;
+    if (sit == split_id.end()) {
+      sid = (int)T.split_z.size();
+      split_id[sf.attr] = sid;
+      T.split_z.push_back((int16_t)zidx.at(sf.attr));
+      T.split_name.push_back(sf.attr);
+      split_thr.emplace_back();
+    } else {
+      sid = sit->second;
+    }
+    const float t = round_down_f32(sf.thr);
+    split_thr[sid].insert(t);
+    std::pair<std::string, std::string> mk{mono.size() > 0 ? mono[0] : "", mono.size() > 1 ? mono[1] : ""};
+    auto mit = mom_id.find(mk);
+    int mid;
+    if (mit == mom_id.end()) {
+      mid = (int)T.moms.size();
+      if (mid >= kTreeMaxMom) {
+        *msg = "more than 8 distinct monomials among filtered aggregates";
+        return LMF_ERR_UNSUPPORTED;
+      }
+      mom_id[mk] = mid;
+      T.moms.push_back(mk);
+      T.mom_z.push_back({mk.first.empty() ? -1 : zidx.at(mk.first), mk.second.empty() ? -1 : zidx.at(mk.second)});
+    } else {
+      mid = mit->second;
+    }
+    pend.push_back({nid, sid, sf.kind == LMF_LE ? 0 : 1, mid, t});
+  }
+  if (T.nodes.size() >= kNoNode) {
+    *msg = "too many distinct nodes";
+    return LMF_ERR_UNSUPPORTED;
+  }
+  for (auto& s : split_thr) {
+    if (s.size() > 254) {
+      *msg = "more than 254 thresholds on one attribute";
+      return LMF_ERR_UNSUPPORTED;
+    }
+    T.thr.emplace_back(s.begin(), s.end());
+    T.max_bins = std::max<int>(T.max_bins, (int)s.size() + 1);
+  }
+  for (auto& p : pend) {
+    const auto& v = T.thr[p.split];
+    const int j = (int)(std::lower_bound(v.begin(), v.end(), p.t) - v.begin());
+    T.outs.push_back({p.node, p.split, j, p.op, p.mom});
+  }
+  // groups of mutually exclusive nodes (greedy)
+  for (int n = 0; n < (int)T.nodes.size(); ++n) {
+    bool placed = false;
+    for (auto& g : T.groups) {
+      bool ok = true;
+      for (int o : g)
+        if (!disjoint(T.nodes[n], T.nodes[o])) {
+          ok = false;
+          break;
+        }
+      if (ok) {
+        g.push_back(n);
+        placed = true;
+        break;
+      }
+    }
+    if (!placed) T.groups.push_back({n});
+  }
+  int mz = 0;
+  for (auto& kv : zidx) mz = std::max(mz, kv.second + 1);
+  T.mp = 16;
+  while (T.mp < mz) T.mp += 16;
+  T.dev.n_nodes = (int)T.nodes.size();
+  T.dev.n_groups = (int)T.groups.size();
+  T.dev.n_split = (int)T.split_z.size();
+  T.dev.max_bins = T.max_bins;
+  T.dev.n_mom = (int)T.moms.size();
+  // default shape: every node in one slice, as many split attributes as fit in 100 KB
+  const size_t per_split = slice_bytes(T, T.dev.n_nodes, 1);
+  T.shape.node_w = T.dev.n_nodes;
+  while (per_split > 0 && T.shape.node_w > 1 && slice_bytes(T, T.shape.node_w, 1) > 100 * 1024)
+    T.shape.node_w = (T.shape.node_w + 1) / 2;
+  T.shape.split_w = 1;
+  while (T.shape.split_w < T.dev.n_split && slice_bytes(T, T.shape.node_w, T.shape.split_w * 2) <= 100 * 1024)
+    T.shape.split_w *= 2;
+  T.shape.split_w = std::min(T.shape.split_w, T.dev.n_split);
+  T.shape.cps = 2;
+  T.shape.chunk = 8192;
+  // the queue array must cover any shape the autotuner may pick
+  T.max_slices = T.dev.n_nodes * T.dev.n_split;
+  return LMF_OK;
 }
-void tree_alloc_zeroed(TreePlan*, const std::function<size_t(size_t)>&) {}
-void tree_alloc(TreePlan*, const std::function<size_t(size_t)>&) {}
-lmf_status tree_finish(TreePlan*, char*, long long*, double*, const std::vector<int64_t>&,
-                       const std::vector<int>&, const std::vector<int32_t>&, uint32_t*, int64_t, int,
-                       const std::map<std::string, double>&, double, const RootParams&) {
-  return LMF_ERR_UNSUPPORTED;
+
+void tree_alloc_zeroed(TreePlan* tp, int64_t /*N*/, const std::function<size_t(size_t)>& take) {
+  TreePlanImpl& T = *tp->impl;
+  T.H_off = take(static_cast<size_t>(T.dev.n_nodes) * T.dev.n_split * T.max_bins * T.dev.n_mom * 8);
+  T.queue_off = take(static_cast<size_t>(T.max_slices) * 4 + 4);
 }
-cudaError_t tree_launch(TreePlan*, const RootParams&, cudaStream_t, int*) { return cudaErrorNotSupported; }
+
+void tree_alloc(TreePlan* tp, int64_t N, const std::function<size_t(size_t)>& take) {
+  TreePlanImpl& T = *tp->impl;
+  const size_t n = static_cast<size_t>(N > 0 ? N : 1);
+  T.node_off = take(n * 2 * T.dev.n_groups);
+  T.bucket_off = take(n * T.dev.n_split);
+  T.momv_off = take(n * 8 * T.dev.n_mom);
+  size_t npred = 0, nthr = 0;
+  for (auto& v : T.nodes) npred += v.size();
+  for (auto& v : T.thr) nthr += v.size();
+  T.tab_bytes = (T.nodes.size() + 1) * 4 + (npred + 1) * sizeof(TreePred) + (T.groups.size() + 1) * 4 +
+                (T.nodes.size() + 1) * 4 + (T.split_z.size() + 1) * 2 + (T.split_z.size() + 1) * 4 +
+                (nthr + 1) * 4 + 64;
+  T.tab_off = take(T.tab_bytes);
+  T.outs_off = take(sizeof(TreeOut) * (T.outs.size() + 1));
+}
+
+lmf_status tree_finish(TreePlan* tp, char* base, long long* res_i64, double* res_f64,
+                       const std::vector<int64_t>& agg_off, const std::vector<int>& filt_idx,
+                       const std::vector<int32_t>& agg_dtype, uint32_t* status, int64_t N, int num_sms,
+                       const std::map<std::string, double>& bound, double W, const RootParams& /*rp*/) {
+  TreePlanImpl& T = *tp->impl;
+  T.num_sms = num_sms;
+  TreeDev& D = T.dev;
+  D.N = N;
+  D.status = status;
+  D.node = reinterpret_cast<uint16_t*>(base + T.node_off);
+  D.bucket = reinterpret_cast<uint8_t*>(base + T.bucket_off);
+  D.momv = reinterpret_cast<long long*>(base + T.momv_off);
+  D.H = reinterpret_cast<long long*>(base + T.H_off);
+  D.queue = reinterpret_cast<uint32_t*>(base + T.queue_off);
+  // moments: fixed-point scale from the value bounds, 0 for the count
+  std::vector<double> scale(T.moms.size());
+  for (size_t m = 0; m < T.moms.size(); ++m) {
+    D.mom_a[m] = (int16_t)T.mom_z[m].first;
+    D.mom_b[m] = (int16_t)T.mom_z[m].second;
+    if (T.moms[m].first.empty()) {
+      scale[m] = 0.0;
+    } else {
+      double b = bound.at(T.moms[m].first);
+      if (!T.moms[m].second.empty()) b *= bound.at(T.moms[m].second);
+      const double tot = W * b;
+      int e = (tot > 0 && std::isfinite(tot)) ? 62 - (int)std::ceil(std::log2(tot)) : 40;
+      e = std::max(-1000, std::min(1000, e));
+      scale[m] = std::ldexp(1.0, e);
+    }
+    D.mom_scale[m] = scale[m];
+  }
+  // plan tables
+  std::vector<char> tab(T.tab_bytes, 0);
+  size_t off = 0;
+  auto put = [&](const void* src, size_t bytes, size_t align) {
+    off = (off + align - 1) / align * align;
+    size_t at = off;
+    if (bytes) std::memcpy(tab.data() + off, src, bytes);
+    off += bytes;
+    return at;
+  };
+  std::vector<int32_t> pred_off{0};
+  std::vector<TreePred> preds;
+  for (auto& v : T.nodes) {
+    preds.insert(preds.end(), v.begin(), v.end());
+    pred_off.push_back((int32_t)preds.size());
+  }
+  std::vector<int32_t> group_off{0}, group_nodes;
+  for (auto& g : T.groups) {
+    group_nodes.insert(group_nodes.end(), g.begin(), g.end());
+    group_off.push_back((int32_t)group_nodes.size());
+  }
+  std::vector<int32_t> thr_off{0};
+  std::vector<float> thr;
+  for (auto& v : T.thr) {
+    thr.insert(thr.end(), v.begin(), v.end());
+    thr_off.push_back((int32_t)thr.size());
+  }
+  const size_t o_pred_off = put(pred_off.data(), pred_off.size() * 4, 8);
+  const size_t o_preds = put(preds.data(), preds.size() * sizeof(TreePred), 8);
+  const size_t o_group_off = put(group_off.data(), group_off.size() * 4, 8);
+  const size_t o_group_nodes = put(group_nodes.data(), group_nodes.size() * 4, 8);
+  const size_t o_split_z = put(T.split_z.data(), T.split_z.size() * 2, 8);
+  const size_t o_thr_off = put(thr_off.data(), thr_off.size() * 4, 8);
+  const size_t o_thr = put(thr.data(), thr.size() * 4, 8);
+  if (off > T.tab_bytes) return LMF_ERR_ARG;
+  char* dtab = base + T.tab_off;
+  D.pred_off = reinterpret_cast<const int32_t*>(dtab + o_pred_off);
+  D.preds = reinterpret_cast<const TreePred*>(dtab + o_preds);
+  D.group_off = reinterpret_cast<const int32_t*>(dtab + o_group_off);
+  D.group_nodes = reinterpret_cast<const int32_t*>(dtab + o_group_nodes);
+  D.split_z = reinterpret_cast<const int16_t*>(dtab + o_split_z);
+  D.thr_off = reinterpret_cast<const int32_t*>(dtab + o_thr_off);
+  D.thr = reinterpret_cast<const float*>(dtab + o_thr);
+  if (cudaMemcpy(dtab, tab.data(), T.tab_bytes, cudaMemcpyHostToDevice) != cudaSuccess) return LMF_ERR_CUDA;
+  // outputs
+  std::vector<TreeOut> outs;
+  for (size_t k = 0; k < T.outs.size(); ++k) {
+    const auto& o = T.outs[k];
+    const int a = filt_idx[k];
+    TreeOut t;
+    t.node = o.node;
+    t.split = o.split;
+    t.j = o.j;
+    t.op = o.op;
+    t.mom = o.mom;
+    t.is_count = agg_dtype[a] == LMF_I64 ? 1 : 0;
+    t.dst = agg_off[a];
+    t.inv_scale = scale[o.mom] > 0 ? 1.0 / scale[o.mom] : 1.0;
+    outs.push_back(t);
+  }
+  T.n_outs = (int)outs.size();
+  if (!outs.empty() &&
+      cudaMemcpy(base + T.outs_off, outs.data(), sizeof(TreeOut) * outs.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return LMF_ERR_CUDA;
+  T.d_outs = reinterpret_cast<const TreeOut*>(base + T.outs_off);
+  T.res_i64 = res_i64;
+  T.res_f64 = res_f64;
+  return LMF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+
+template <int MP>
+__global__ void __launch_bounds__(128) k_tree_rows(const __grid_constant__ RootParams p, const __grid_constant__ TreeDev d) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* zrow = reinterpret_cast<float*>(smem) + threadIdx.x * (MP + 4);
+  int32_t* crow = reinterpret_cast<int32_t*>(reinterpret_cast<float*>(smem) + blockDim.x * (MP + 4)) +
+                  threadIdx.x * (p.n_rowcat > 0 ? p.n_rowcat : 1);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < d.N; row += stride) {
+    const long long w = root_row_z<MP>(p, row, zrow, crow);
+    for (int g = 0; g < d.n_groups; ++g) {
+      uint16_t hit = kNoNode;
+      if (w != 0) {
+        for (int q = d.group_off[g]; q < d.group_off[g + 1]; ++q) {
+          const int n = d.group_nodes[q];
+          bool ok = true;
+          for (int k = d.pred_off[n]; k < d.pred_off[n + 1] && ok; ++k) {
+            const TreePred pr = d.preds[k];
+            const float x = zrow[pr.z];
+            ok = pr.op == 0 ? (x <= pr.thr) : (x > pr.thr);
+          }
+          if (ok) {
+            hit = static_cast<uint16_t>(n);
+            break;
+          }
+        }
+      }
+      d.node[(int64_t)g * d.N + row] = hit;
+    }
+    for (int f = 0; f < d.n_split; ++f) {
+      const float x = zrow[d.split_z[f]];
+      int lo = d.thr_off[f], hi = d.thr_off[f + 1];
+      const int base = lo;
+      while (lo < hi) {  // first threshold >= x: number of thresholds < x
+        const int mid = (lo + hi) >> 1;
+        if (d.thr[mid] < x) lo = mid + 1;
+        else hi = mid;
+      }
+      d.bucket[(int64_t)f * d.N + row] = static_cast<uint8_t>(lo - base);
+    }
+    for (int m = 0; m < d.n_mom; ++m) {
+      long long v = w;
+      if (d.mom_scale[m] > 0.0 && w != 0) {
+        double x = static_cast<double>(w);
+        if (d.mom_a[m] >= 0) x *= static_cast<double>(zrow[d.mom_a[m]]);
+        if (d.mom_b[m] >= 0) x *= static_cast<double>(zrow[d.mom_b[m]]);
+        v = llrint(x * d.mom_scale[m]);
+      } else if (d.mom_scale[m] > 0.0) {
+        v = 0;
+      }
+      d.momv[(int64_t)m * d.N + row] = v;
+    }
+  }
+}
+
+// exact 64-bit accumulation in two 32-bit shared-memory words (low word with
+// carry detection through the returned old value, high word plain)
+__device__ __forceinline__ void acc64(uint32_t* lo, uint32_t* hi, long long v) {
+  const uint32_t vl = static_cast<uint32_t>(v);
+  const uint32_t vh = static_cast<uint32_t>(static_cast<unsigned long long>(v) >> 32);
+  const uint32_t old = atomicAdd(lo, vl);
+  const uint32_t up = vh + ((old + vl < old) ? 1u : 0u);
+  if (up) atomicAdd(hi, up);
+}
+
+__global__ void __launch_bounds__(256) k_tree_hist(const __grid_constant__ TreeDev d, TreeShape sh, int n_slices) {
+  extern __shared__ __align__(16) uint32_t bins[];  // [cells] lo, then [cells] hi
+  const int slice = blockIdx.x % n_slices;
+  const int n_split_slices = (d.n_split + sh.split_w - 1) / sh.split_w;
+  const int n0 = (slice / n_split_slices) * sh.node_w;
+  const int f0 = (slice % n_split_slices) * sh.split_w;
+  const int nw = min(sh.node_w, d.n_nodes - n0);
+  const int fw = min(sh.split_w, d.n_split - f0);
+  const int cells = nw * fw * d.max_bins * d.n_mom;
+  uint32_t* lo = bins;
+  uint32_t* hi = bins + cells;
+  for (int i = threadIdx.x; i < 2 * cells; i += blockDim.x) bins[i] = 0u;
+  __shared__ uint32_t chunk_s;
+  __syncthreads();
+  const int64_t n_chunks = (d.N + sh.chunk - 1) / sh.chunk;
+  for (;;) {
+    if (threadIdx.x == 0) chunk_s = atomicAdd(d.queue + slice, 1u);
+    __syncthreads();
+    const int64_t c = chunk_s;
+    __syncthreads();
+    if (c >= n_chunks) break;
+    const int64_t r1 = d.N < (c + 1) * sh.chunk ? d.N : (c + 1) * sh.chunk;
+    for (int64_t row = c * sh.chunk + threadIdx.x; row < r1; row += blockDim.x) {
+      long long mv[kTreeMaxMom];
+      bool loaded = false;
+      for (int g = 0; g < d.n_groups; ++g) {
+        const int n = d.node[(int64_t)g * d.N + row];
+        if (n == kNoNode || n < n0 || n >= n0 + nw) continue;
+        if (!loaded) {
+          for (int m = 0; m < d.n_mom; ++m) mv[m] = d.momv[(int64_t)m * d.N + row];
+          loaded = true;
+        }
+        for (int f = 0; f < fw; ++f) {
+          const int b = d.bucket[(int64_t)(f0 + f) * d.N + row];
+          const int cell = (((n - n0) * fw + f) * d.max_bins + b) * d.n_mom;
+          for (int m = 0; m < d.n_mom; ++m)
+            if (mv[m] != 0) acc64(lo + cell + m, hi + cell + m, mv[m]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+    const unsigned long long v = (static_cast<unsigned long long>(hi[i]) << 32) | lo[i];
+    if (v == 0) continue;
+    const int m = i % d.n_mom;
+    const int b = (i / d.n_mom) % d.max_bins;
+    const int f = (i / (d.n_mom * d.max_bins)) % fw;
+    const int n = i / (d.n_mom * d.max_bins * fw);
+    const int64_t at = (((int64_t)(n0 + n) * d.n_split + (f0 + f)) * d.max_bins + b) * d.n_mom + m;
+    atomicAdd(reinterpret_cast<unsigned long long*>(d.H + at), v);
+  }
+}
+
+__global__ void k_tree_out(const __grid_constant__ TreeDev d, const TreeOut* outs, int n, long long* res_i64,
+                           double* res_f64) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const TreeOut o = outs[k];
+  const int nb = d.thr_off[o.split + 1] - d.thr_off[o.split] + 1;
+  const long long* h = d.H + ((int64_t)o.node * d.n_split + o.split) * d.max_bins * d.n_mom + o.mom;
+  long long s = 0;
+  if (o.op == 0) {
+    for (int b = 0; b <= o.j; ++b) s += h[(int64_t)b * d.n_mom];
+  } else {
+    for (int b = o.j + 1; b < nb; ++b) s += h[(int64_t)b * d.n_mom];
+  }
+  if (o.is_count) res_i64[o.dst] = s;
+  else res_f64[o.dst] = static_cast<double>(s) * o.inv_scale;
+}
+
+namespace {
+
+size_t rows_smem(const TreePlanImpl& T, const RootParams& rp) {
+  return static_cast<size_t>(128) * (T.mp + 4) * 4 + static_cast<size_t>(128) * (rp.n_rowcat > 0 ? rp.n_rowcat : 1) * 4;
+}
+
+cudaError_t launch_rows(const TreePlanImpl& T, const RootParams& rp, cudaStream_t s) {
+  const size_t sm = rows_smem(T, rp);
+  const int grid = T.num_sms * 8;
+  cudaError_t e = cudaSuccess;
+  switch (T.mp) {
+    case 16:
+      e = cudaFuncSetAttribute(k_tree_rows<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e == cudaSuccess) k_tree_rows<16><<<grid, 128, sm, s>>>(rp, T.dev);
+      break;
+    case 32:
+      e = cudaFuncSetAttribute(k_tree_rows<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e == cudaSuccess) k_tree_rows<32><<<grid, 128, sm, s>>>(rp, T.dev);
+      break;
+    case 48:
+      e = cudaFuncSetAttribute(k_tree_rows<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e == cudaSuccess) k_tree_rows<48><<<grid, 128, sm, s>>>(rp, T.dev);
+      break;
+    default:
+      e = cudaFuncSetAttribute(k_tree_rows<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e == cudaSuccess) k_tree_rows<64><<<grid, 128, sm, s>>>(rp, T.dev);
+      break;
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hist(const TreePlanImpl& T, const TreeShape& sh, cudaStream_t s) {
+  const int ns = n_slices(T, sh);
+  const size_t sm = slice_bytes(T, sh.node_w, sh.split_w);
+  int per = (int)((static_cast<int64_t>(T.num_sms) * sh.cps + ns - 1) / ns);
+  if (per < 1) per = 1;
+  const int grid = ns * per;
+  cudaError_t e = cudaFuncSetAttribute(k_tree_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_tree_hist<<<grid, 256, sm, s>>>(T.dev, sh, ns);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tree_launch(TreePlan* tp, const RootParams& rp, cudaStream_t s, int* nk) {
+  TreePlanImpl& T = *tp->impl;
+  cudaError_t e = launch_rows(T, rp, s);
+  if (e != cudaSuccess) return e;
+  e = launch_hist(T, T.shape, s);
+  if (e != cudaSuccess) return e;
+  if (T.n_outs > 0) {
+    k_tree_out<<<(T.n_outs + 255) / 256, 256, 0, s>>>(T.dev, T.d_outs, T.n_outs, T.res_i64, T.res_f64);
+  }
+  *nk += 3;
+  return cudaGetLastError();
+}
+
+bool tree_needs_tuning(const TreePlan* tp) { return tp && tp->impl && !tp->impl->tuned; }
+
+cudaError_t tree_autotune(TreePlan* tp, const RootParams& rp, cudaStream_t s) {
+  TreePlanImpl& T = *tp->impl;
+  (void)rp;
+  std::vector<TreeShape> cand;
+  for (int node_w : {T.dev.n_nodes, (T.dev.n_nodes + 1) / 2, (T.dev.n_nodes + 3) / 4})
+    for (int split_w : {1, 2, 4, 8})
+      for (int cps : {1, 2})
+        for (int chunk : {4096, 16384}) {
+          if (node_w < 1 || split_w > std::max(1, T.dev.n_split)) continue;
+          const size_t b = slice_bytes(T, node_w, split_w);
+          if (b * cps > 200 * 1024 || b > 200 * 1024) continue;
+          if (n_slices(T, {split_w, node_w, cps, chunk}) > T.max_slices) continue;
+          cand.push_back({split_w, node_w, cps, chunk});
+        }
+  if (cand.empty()) cand.push_back(T.shape);
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best = 1e30f;
+  TreeShape pick = T.shape;
+  const size_t hbytes = static_cast<size_t>(T.dev.n_nodes) * T.dev.n_split * T.max_bins * T.dev.n_mom * 8;
+  for (const auto& c : cand) {
+    cudaMemsetAsync(T.dev.queue, 0, static_cast<size_t>(T.max_slices) * 4, s);
+    cudaMemsetAsync(T.dev.H, 0, hbytes, s);
+    cudaEventRecord(a, s);
+    cudaError_t e = launch_hist(T, c, s);
+    cudaEventRecord(b, s);
+    if (e != cudaSuccess) continue;
+    if (cudaEventSynchronize(b) != cudaSuccess) break;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  T.shape = pick;
+  T.tuned = true;
+  return cudaGetLastError();
+}
+
+void tree_shape(const TreePlan* tp, int* out5) {
+  const TreePlanImpl& T = *tp->impl;
+  out5[0] = n_slices(T, T.shape);
+  out5[1] = T.shape.split_w;
+  out5[2] = T.shape.node_w;
+  out5[3] = T.shape.cps;
+  out5[4] = T.shape.chunk;
+}
 
 }  // namespace lmf

@@ -1,6 +1,7 @@
-// lmf_tree.h -- filtered aggregates (regression-tree node batches, Sec. 2 Eq.
-// regression-tree): products of threshold indicators times a monomial of
-// degree <= 2, evaluated as per-node histograms over sorted thresholds.
+// lmf_tree.h -- threshold-filtered aggregates: the regression-tree node batch
+// of Sec. 2 (Eq. regression-tree), RT(1 a, y a, y^2 a) with a a product of
+// threshold indicators, evaluated for many (node, attribute, threshold)
+// triples at once as per-node histograms over the sorted thresholds.
 #pragma once
 
 #include <cstdint>
@@ -23,24 +24,31 @@ struct TreeAggIn {
   std::vector<TreeFactorIn> factors;
 };
 
-struct TreePlanImpl;  // defined in lmf_tree.cu
+struct TreePlanImpl;  // lmf_tree.cu
 struct TreePlan {
   TreePlanImpl* impl = nullptr;
   ~TreePlan();
 };
 
-// decompose the batch: nodes, split attributes, threshold lists, moments
+// Decompose the batch into nodes (conjunctions), split attributes with their
+// sorted thresholds and moments (monomials of degree <= 2).
 lmf_status tree_plan(const std::vector<TreeAggIn>& in, const std::map<std::string, int>& zidx,
                      TreePlan* tp, std::string* msg);
-// device buffers: accumulators that every run starts from zero ...
-void tree_alloc_zeroed(TreePlan* tp, const std::function<size_t(size_t)>& take);
-// ... and tables written once at plan time
-void tree_alloc(TreePlan* tp, const std::function<size_t(size_t)>& take);
+// Device buffers: histogram and work queues (reset every run) ...
+void tree_alloc_zeroed(TreePlan* tp, int64_t N, const std::function<size_t(size_t)>& take);
+// ... per-row pass buffers and plan tables (written once or fully every run).
+void tree_alloc(TreePlan* tp, int64_t N, const std::function<size_t(size_t)>& take);
 lmf_status tree_finish(TreePlan* tp, char* base, long long* res_i64, double* res_f64,
                        const std::vector<int64_t>& agg_off, const std::vector<int>& filt_idx,
                        const std::vector<int32_t>& agg_dtype, uint32_t* status, int64_t N,
                        int num_sms, const std::map<std::string, double>& bound, double W,
                        const RootParams& rp);
 cudaError_t tree_launch(TreePlan* tp, const RootParams& rp, cudaStream_t s, int* n_kernels);
+// The autotuner times the histogram pass over its shape candidates once the
+// per-row buffers hold a run's data, and keeps the fastest.
+bool tree_needs_tuning(const TreePlan* tp);
+cudaError_t tree_autotune(TreePlan* tp, const RootParams& rp, cudaStream_t s);
+// chosen histogram shape, for reporting: slices, split attributes and nodes per slice, CTAs per SM, chunk rows
+void tree_shape(const TreePlan* tp, int* out5);
 
 }  // namespace lmf
