@@ -71,6 +71,9 @@ typedef int32_t lmf_status;
 #define LMF_BATCH_SINGLE     0   /* lmf_run enqueues the kernels one by one */
 #define LMF_BATCH_GRAPH      1   /* lmf_run replays one captured CUDA graph */
 #define LMF_ROOT_DECLARED    0   /* the relation that is nobody's child */
+#define LMF_ROOT_EXPLICIT    1   /* lmf_plan_opts.root_rel */
+#define LMF_ROOT_HEURISTIC   2   /* the root rule of Sec. 3.3: largest total group-by
+                                    weight, ties to the largest relation */
 
 #define LMF_MAX_GROUP_BY 3
 #define LMF_MAX_FACTORS  16
@@ -104,8 +107,11 @@ typedef struct {
   int32_t batching;       /* LMF_BATCH_* */
   int32_t tile_rows;      /* root rows per tile; 0 = tuned default */
   int32_t ctas_per_sm;    /* resident CTAs per SM for the root scan; 0 = default */
-  int32_t root_mode;      /* LMF_ROOT_DECLARED */
-  int32_t reserved[3];
+  int32_t root_mode;      /* LMF_ROOT_* */
+  int32_t root_rel;       /* LMF_ROOT_EXPLICIT: relation id of the root */
+  int32_t no_merge;       /* 1: one record array per child view instead of one per
+                             parent key (turns off merge case (1) of Sec. 3.4) */
+  int32_t reserved;
 } lmf_plan_opts;
 
 /* Statistics of a plan, for reporting (lmf_plan_info). */
@@ -120,6 +126,15 @@ typedef struct {
   int32_t unique_keys;        /* 1 when every child key is unique (no fan-out) */
   int32_t root_grid;          /* CTAs of the root scan */
   int32_t precision;          /* precision actually used */
+  int32_t root_rel;           /* relation id of the root actually used */
+  int32_t merged;             /* 1 when views sharing a parent key are merged */
+  int32_t tree_nodes;         /* filtered batches: distinct nodes (conjunctions) */
+  int32_t tree_groups;        /* ... groups of mutually exclusive nodes */
+  int32_t tree_slices;        /* ... histogram slices of the chosen shape */
+  int32_t tree_split_w;       /* ... split attributes per slice */
+  int32_t tree_node_w;        /* ... nodes per slice */
+  int32_t tree_ctas_per_sm;   /* ... CTAs per SM */
+  int32_t tree_chunk;         /* ... rows per work item */
   int64_t root_rows;          /* rows of the root relation */
   int64_t scratch_bytes;      /* device bytes owned by the plan */
 } lmf_plan_stats;
@@ -239,6 +254,66 @@ lmf_status lmf_read_results(lmf_ctx* ctx, int batch_id, int64_t* dst_i64, double
 
 /* Copy one aggregate's result (n_groups cells of its dtype) to host memory. */
 lmf_status lmf_read_result(lmf_ctx* ctx, int batch_id, int agg, void* dst);
+
+/* ---------------------------------------------------------------------------
+ * Plan choice.  The paper picks the root of each query by a weight rule
+ * (Sec. 3.3).  This engine adds a learned cost model over candidate plans
+ * (root, precision, CTAs per SM, view merging); the rule stays the fallback
+ * and the reference its regret is measured against.
+ * ------------------------------------------------------------------------- */
+
+/* Number of features lmf_plan_features writes. */
+#define LMF_PLAN_FEATURES 24
+
+/*
+ * Candidate plans for a declared batch: up to four roots (the declared one,
+ * the Sec. 3.3 rule's one, the largest relations) x precision x CTAs per SM x
+ * view merging, each as explicit plan options derived from *base (NULL: zero
+ * options).  Writes min(max, count) entries to out (may be NULL) and the count
+ * to *n.
+ */
+lmf_status lmf_plan_candidates(lmf_ctx* ctx, int batch_id, const lmf_plan_opts* base,
+                               lmf_plan_opts* out, int max, int* n);
+
+/*
+ * Features of the batch's current plan (host array of n >= LMF_PLAN_FEATURES
+ * floats): sizes, view and group counts, z length, record bytes, aggregate
+ * counts, key multiplicity, precision, CTAs per SM, merging, root position.
+ */
+lmf_status lmf_plan_features(lmf_ctx* ctx, int batch_id, float* feat, int n);
+
+typedef struct lmf_mlp lmf_mlp;
+
+/* An FP32 MLP in -> hidden -> hidden -> 1 (ReLU), weights drawn from seed. */
+lmf_status lmf_mlp_create(int device, int in_dim, int hidden, uint64_t seed, lmf_mlp** out);
+lmf_status lmf_mlp_destroy(lmf_mlp* m);
+/* Parameter count and flat copies (layout W1[in][h] b1[h] W2[h][h] b2[h] w3[h] b3). */
+lmf_status lmf_mlp_num_params(lmf_mlp* m, int64_t* n);
+lmf_status lmf_mlp_get_params(lmf_mlp* m, float* host, int64_t n);
+lmf_status lmf_mlp_set_params(lmf_mlp* m, const float* host, int64_t n);
+/* Input standardisation (x - mean) / std and output scale y = y_std * out + y_mean. */
+lmf_status lmf_mlp_set_norm(lmf_mlp* m, const float* mean, const float* std, float y_mean, float y_std);
+/* Predictions for `batch` feature rows x_dev[batch][in] (device) into y_dev[batch] (device). */
+lmf_status lmf_mlp_forward(lmf_mlp* m, const float* x_dev, int batch, float* y_dev);
+/*
+ * Mean squared error on standardised targets y_dev (device, already
+ * (y - y_mean) / y_std) and its gradient w.r.t. every parameter, written to
+ * grad_dev (device, may be NULL); *loss (host, may be NULL).
+ */
+lmf_status lmf_mlp_grad(lmf_mlp* m, const float* x_dev, const float* y_dev, int batch, float* grad_dev,
+                        float* loss);
+/* One Adam step (beta 0.9 / 0.999) on that loss. */
+lmf_status lmf_mlp_train_step(lmf_mlp* m, const float* x_dev, const float* y_dev, int batch, float lr,
+                              float* loss);
+
+/*
+ * Plan the batch with the candidate the model predicts fastest (every
+ * candidate is planned to compute its features).  model == NULL falls back to
+ * the Sec. 3.3 root rule with *base.  The chosen options go to *chosen (may be
+ * NULL).
+ */
+lmf_status lmf_plan_learned(lmf_ctx* ctx, int batch_id, lmf_mlp* model, const lmf_plan_opts* base,
+                            lmf_plan_opts* chosen);
 
 /* Static text of a status code. */
 const char* lmf_status_string(lmf_status s);

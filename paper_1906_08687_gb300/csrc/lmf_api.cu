@@ -49,6 +49,9 @@ struct RelationH {
   std::vector<int> children;
   int K = 0;                  // child key space 0..K-1
   int max_mult = 0;           // largest number of rows sharing a key
+  // the parent's foreign-key column of this edge (used when a plan reverses it)
+  int fk_K = 0, fk_mult = 0;
+  bool fk_ok = true;
   int find(const std::string& n) const {
     for (size_t i = 0; i < cols.size(); ++i)
       if (cols[i].name == n) return (int)i;
@@ -143,6 +146,12 @@ struct Plan {
   int n_kernels = 0;
   bool unique_all = true;
   int n_views = 0, n_gram = 0, n_grouped = 0, n_filtered = 0;
+  // orientation of the join tree from the plan's root
+  int root = 0;
+  bool merge = true;
+  std::vector<int> par, K, mult;
+  std::vector<std::string> key;
+  std::vector<std::vector<int>> kids;
   bool root_scan = true;         // some aggregate needs the Gram / counts / grouped tables
   template <class T>
   T* at(size_t off) const { return reinterpret_cast<T*>(arena.base + off); }
@@ -426,6 +435,39 @@ lmf_status lmf_declare_join(lmf_ctx* c, int n_edges, const int* parent_rel, cons
     cudaFree(hist);
     R.max_mult = (int)*std::max_element(h.begin(), h.end());
   }
+  // the parent's side of every edge (its foreign-key column), which becomes the
+  // child key when a plan roots the tree below that edge; negative values never
+  // join, sparse columns make the edge irreversible
+  for (int ch = 0; ch < n; ++ch) {
+    RelationH& R = c->rels[ch];
+    if (R.parent < 0) continue;
+    const RelationH& P = c->rels[R.parent];
+    R.fk_K = 0;
+    R.fk_mult = 0;
+    R.fk_ok = true;
+    if (P.nrows == 0) continue;
+    const ColumnH& fc = P.cols[P.find(R.key)];
+    int h_mm[2] = {0x7fffffff, -0x7fffffff - 1};
+    CUDA_TRY(c, cudaMemcpy(mm, h_mm, sizeof(h_mm), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, launch_key_stats(static_cast<const int32_t*>(fc.dptr()), P.nrows, nullptr, 0, mm, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(h_mm, mm, sizeof(h_mm), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (h_mm[1] < 0) continue;
+    if ((int64_t)h_mm[1] >= 4 * P.nrows + 4096) {
+      R.fk_ok = false;
+      continue;
+    }
+    R.fk_K = h_mm[1] + 1;
+    unsigned int* hist = nullptr;
+    CUDA_TRY(c, cudaMalloc(&hist, sizeof(unsigned int) * R.fk_K));
+    CUDA_TRY(c, cudaMemsetAsync(hist, 0, sizeof(unsigned int) * R.fk_K, c->stream));
+    CUDA_TRY(c, launch_key_stats(static_cast<const int32_t*>(fc.dptr()), P.nrows, hist, R.fk_K, nullptr, c->stream));
+    std::vector<unsigned int> h(R.fk_K);
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), hist, sizeof(unsigned int) * R.fk_K, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    cudaFree(hist);
+    R.fk_mult = (int)*std::max_element(h.begin(), h.end());
+  }
   cudaFree(mm);
   c->root = root;
   c->joined = true;
@@ -521,12 +563,13 @@ void layout_rel(lmf_ctx* c, Plan& P, int r, const std::set<std::string>& need_fe
   // groups: children sharing the FK column name
   std::vector<std::string> order;
   std::map<std::string, int> gid;
-  for (int ch : R.children) {
-    const std::string& k = c->rels[ch].key;
+  for (int ch : P.kids[r]) {
+    // merged: one record array per parent key; unmerged: one per child view
+    const std::string k = P.merge ? P.key[ch] : P.key[ch] + "#" + c->rels[ch].name;
     if (!gid.count(k)) {
       GroupH g;
       g.owner = r;
-      g.fk = k;
+      g.fk = P.key[ch];
       gid[k] = (int)P.groups.size();
       rp.groups.push_back((int)P.groups.size());
       P.groups.push_back(g);
@@ -536,8 +579,8 @@ void layout_rel(lmf_ctx* c, Plan& P, int r, const std::set<std::string>& need_fe
   for (int gi : rp.groups)
     for (int ch : P.groups[gi].children) layout_rel(c, P, ch, need_feat, need_cat);
   // own section
-  rp.unique = (r == c->root) || R.max_mult <= 1;
-  rp.maxcnt = (r == c->root) ? 1.0 : std::max(1, R.max_mult);
+  rp.unique = (r == P.root) || P.mult[r] <= 1;
+  rp.maxcnt = (r == P.root) ? 1.0 : std::max(1, P.mult[r]);
   for (int i : rp.own_feat) rp.feat_names.push_back(R.cols[i].name);
   for (int i : rp.own_cat) rp.cat_names.push_back(R.cols[i].name);
   for (int gi : rp.groups) {
@@ -553,7 +596,7 @@ void layout_rel(lmf_ctx* c, Plan& P, int r, const std::set<std::string>& need_fe
       cp.slot = (int)q;
       g.child_mu_off.push_back(g.n_cnt + g.n_mu);
       g.n_mu += cp.d;
-      g.K = std::max(g.K, c->rels[ch].K);
+      g.K = std::max(g.K, P.K[ch]);
       rp.unique = rp.unique && cp.unique;
       rp.maxcnt *= cp.maxcnt;
       for (auto& f : cp.feat_names) rp.feat_names.push_back(f);
@@ -569,13 +612,120 @@ void layout_rel(lmf_ctx* c, Plan& P, int r, const std::set<std::string>& need_fe
   }
   rp.d = (int)rp.feat_names.size();
   rp.ncat = (int)rp.cat_names.size();
-  if (r != c->root) P.post.push_back(r);
+  if (r != P.root) P.post.push_back(r);
 }
+
+}  // namespace
+
+namespace {
+
+// Orient the declared tree from `root`: parent, edge key, children, and the
+// key space and multiplicity of every relation's key towards its parent (a
+// reversed edge uses the old parent's foreign-key column as that key).
+lmf_status orient(lmf_ctx* c, Plan& P, int root) {
+  const int n = (int)c->rels.size();
+  P.root = root;
+  P.par.assign(n, -1);
+  P.key.assign(n, std::string());
+  P.kids.assign(n, std::vector<int>());
+  P.K.assign(n, 0);
+  P.mult.assign(n, 0);
+  struct Adj {
+    int to;
+    std::string key;
+    int K, mult;
+    bool ok;
+  };
+  std::vector<std::vector<Adj>> adj(n);
+  for (int r = 0; r < n; ++r)
+    for (int ch : c->rels[r].children) {
+      const RelationH& R = c->rels[ch];
+      adj[r].push_back({ch, R.key, R.K, R.max_mult, true});
+      adj[ch].push_back({r, R.key, R.fk_K, R.fk_mult, R.fk_ok});
+    }
+  std::vector<int> seen(n, 0), queue{root};
+  seen[root] = 1;
+  for (size_t h = 0; h < queue.size(); ++h) {
+    const int u = queue[h];
+    for (const Adj& a : adj[u]) {
+      if (seen[a.to]) continue;
+      if (!a.ok)
+        return fail(c, LMF_ERR_UNSUPPORTED, "cannot root at %s: the key column %s of %s is too sparse",
+                    c->rels[root].name.c_str(), a.key.c_str(), c->rels[a.to].name.c_str());
+      seen[a.to] = 1;
+      P.par[a.to] = u;
+      P.key[a.to] = a.key;
+      P.K[a.to] = a.K;
+      P.mult[a.to] = a.mult;
+      P.kids[u].push_back(a.to);
+      queue.push_back(a.to);
+    }
+  }
+  return LMF_OK;
+}
+
+// Root rule of Sec. 3.3 for one batch: every query gives each relation the
+// fraction of its group-by attributes held there (an equal share of all
+// relations when it has none); the root is the relation with the largest total
+// weight, ties going to the largest relation.
+int heuristic_root(lmf_ctx* c, const BatchH& B) {
+  const int n = (int)c->rels.size();
+  std::vector<double> w(n, 0.0);
+  for (const auto& a : B.aggs) {
+    if (a.gb.empty()) {
+      for (int r = 0; r < n; ++r) w[r] += 1.0 / n;
+      continue;
+    }
+    for (const auto& g : a.gb) {
+      int col, r = owner_of(c, g, &col);
+      if (r >= 0) w[r] += 1.0 / a.gb.size();
+    }
+  }
+  int best = 0;
+  for (int r = 1; r < n; ++r) {
+    const double d = w[r] - w[best];
+    if (d > 1e-12 || (std::fabs(d) <= 1e-12 && c->rels[r].nrows > c->rels[best].nrows)) best = r;
+  }
+  return best;
+}
+
+lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, int root);
 
 }  // namespace
 
 extern "C" lmf_status lmf_plan(lmf_ctx* c, int batch_id, const lmf_plan_opts* opts) {
   if (!c || batch_id < 0 || batch_id >= (int)c->batches.size()) return fail(c, LMF_ERR_ARG, "plan: bad batch id");
+  if (!c->joined) return fail(c, LMF_ERR_STATE, "plan before declare_join");
+  lmf_plan_opts o{};
+  if (opts) {
+    o = *opts;
+  } else {
+    o.precision = LMF_PREC_SPLIT_BF16;
+    o.batching = LMF_BATCH_GRAPH;
+  }
+  BatchH& B = *c->batches[batch_id];
+  switch (o.root_mode) {
+    case LMF_ROOT_DECLARED:
+      return plan_with_root(c, batch_id, o, c->root);
+    case LMF_ROOT_EXPLICIT:
+      if (o.root_rel < 0 || o.root_rel >= (int)c->rels.size()) return fail(c, LMF_ERR_ARG, "plan: bad root_rel");
+      return plan_with_root(c, batch_id, o, o.root_rel);
+    case LMF_ROOT_HEURISTIC: {
+      const int r = heuristic_root(c, B);
+      lmf_status s = plan_with_root(c, batch_id, o, r);
+      // fall back to the declared root when this engine cannot evaluate the
+      // batch from the rule's root (e.g. group-by attributes below a fan-out)
+      if (s == LMF_ERR_UNSUPPORTED && r != c->root) s = plan_with_root(c, batch_id, o, c->root);
+      return s;
+    }
+    default:
+      return fail(c, LMF_ERR_ARG, "plan: root_mode %d", o.root_mode);
+  }
+}
+
+namespace {
+
+lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, int root) {
   cudaSetDevice(c->device);
   BatchH& B = *c->batches[batch_id];
   if (B.plan) {
@@ -584,14 +734,13 @@ extern "C" lmf_status lmf_plan(lmf_ctx* c, int batch_id, const lmf_plan_opts* op
     B.plan.reset();
   }
   auto P = std::make_unique<Plan>();
-  if (opts) {
-    P->opts = *opts;
-  } else {
-    P->opts.precision = LMF_PREC_SPLIT_BF16;
-    P->opts.batching = LMF_BATCH_GRAPH;
-  }
+  P->opts = opts;
+  P->merge = opts.no_merge == 0;
   const int nrel = (int)c->rels.size();
-  const int root = c->root;
+  {
+    lmf_status s = orient(c, *P, root);
+    if (s) return s;
+  }
   RelationH& Root = c->rels[root];
 
   // ---- classify aggregates; needed features and categories
@@ -784,8 +933,8 @@ extern "C" lmf_status lmf_plan(lmf_ctx* c, int batch_id, const lmf_plan_opts* op
     for (int a : filt_idx)
       for (auto& f : B.aggs[a].f) {
         int col, r = owner_of(c, f.attr, &col);
-        for (int x = r; x != root; x = c->rels[x].parent)
-          if (c->rels[x].max_mult > 1)
+        for (int x = r; x != root; x = P->par[x])
+          if (P->mult[x] > 1)
             return fail(c, LMF_ERR_UNSUPPORTED,
                         "aggregate %d: threshold or power factor on %s below the fanning-out key of %s", a,
                         f.attr.c_str(), c->rels[x].name.c_str());
@@ -1036,6 +1185,8 @@ extern "C" lmf_status lmf_plan(lmf_ctx* c, int batch_id, const lmf_plan_opts* op
   return LMF_OK;
 }
 
+}  // namespace
+
 namespace {
 
 // ev (optional): LMF_STAGES + 1 events recorded on s at the stage boundaries
@@ -1060,7 +1211,7 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
     GroupH& g = P->groups[cp.group];
     ViewArgs a{};
     a.nrows = R.nrows;
-    a.key = static_cast<const int32_t*>(R.cols[R.find(R.key)].dptr());
+    a.key = static_cast<const int32_t*>(R.cols[R.find(P->key[r])].dptr());
     a.K = g.K;
     a.dst = P->at<uint32_t>(g.rec_off);
     a.dst_stride = g.stride;
@@ -1216,6 +1367,18 @@ lmf_status lmf_plan_info(lmf_ctx* c, int batch_id, lmf_plan_stats* info) {
   info->unique_keys = P->unique_all ? 1 : 0;
   info->root_grid = P->grid;
   info->precision = P->tc ? LMF_PREC_SPLIT_BF16 : LMF_PREC_PLAIN_FP32;
+  info->root_rel = P->root;
+  info->merged = P->merge ? 1 : 0;
+  if (P->tree) {
+    int t5[5];
+    tree_shape(P->tree.get(), t5);
+    tree_counts(P->tree.get(), &info->tree_nodes, &info->tree_groups);
+    info->tree_slices = t5[0];
+    info->tree_split_w = t5[1];
+    info->tree_node_w = t5[2];
+    info->tree_ctas_per_sm = t5[3];
+    info->tree_chunk = t5[4];
+  }
   info->root_rows = P->rootp.N;
   info->scratch_bytes = (int64_t)P->arena.size;
   return LMF_OK;
@@ -1343,6 +1506,155 @@ lmf_status lmf_read_result(lmf_ctx* c, int batch_id, int agg, void* dst) {
                               cudaMemcpyDeviceToHost, s));
   CUDA_TRY(c, cudaStreamSynchronize(s));
   return LMF_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// plan choice: candidates, features, learned selection
+namespace {
+
+constexpr int kPlanFeatures = 24;
+
+void plan_features(lmf_ctx* c, const Plan& P, float* f) {
+  double total_rows = 0, max_rows = 1;
+  for (auto& r : c->rels) {
+    total_rows += (double)r.nrows;
+    max_rows = std::max(max_rows, (double)r.nrows);
+  }
+  const double root_rows = (double)std::max<int64_t>(1, P.rootp.N);
+  double rec_bytes = 0, general_work = 0;
+  int non_unique = 0, max_mult = 1;
+  for (auto& g : P.groups) rec_bytes += (double)g.K * g.stride * 4;
+  for (int r : P.post) {
+    max_mult = std::max(max_mult, P.mult[r]);
+    if (!P.rp[r].unique) {
+      ++non_unique;
+      general_work += (double)c->rels[r].nrows * (P.rp[r].d * (P.rp[r].d + 1) / 2 + P.rp[r].d + 1);
+    }
+  }
+  double cells = 0;
+  for (auto& o : P.maps)
+    if (o.kind >= 2) cells += (double)o.n;
+  int slots = 0;
+  for (int q = 0; q < P.rootp.n_rv; ++q) slots += P.rootp.rv[q].n_slot;
+  int fanin = 1;
+  for (int r = 0; r < (int)c->rels.size(); ++r)
+    if (c->rels[r].parent >= 0) fanin = std::max(fanin, c->rels[r].fk_mult);
+  const float v[kPlanFeatures] = {
+      (float)std::log2(root_rows + 1), (float)std::log2(total_rows + 1), (float)c->rels.size(),
+      (float)P.post.size(), (float)P.rootp.n_grp, (float)P.rootp.m, (float)std::log2(rec_bytes + 1),
+      (float)P.n_gram, (float)P.n_grouped, (float)P.n_filtered, (float)std::log2(cells + 1),
+      P.unique_all ? 1.f : 0.f, (float)std::log2((double)max_mult + 1), P.tc ? 1.f : 0.f,
+      (float)P.grid / (float)std::max(1, c->num_sms), P.merge ? 1.f : 0.f,
+      (double)c->rels[P.root].nrows >= max_rows ? 1.f : 0.f, (float)(std::log2(root_rows) - std::log2(max_rows)),
+      (float)non_unique, (float)std::log2(general_work + 1), (float)slots, (float)P.direct.size(),
+      (float)std::log2((double)fanin + 1), P.tree ? 1.f : 0.f};
+  std::memcpy(f, v, sizeof(v));
+}
+
+std::vector<lmf_plan_opts> plan_candidates(lmf_ctx* c, const BatchH& B, const lmf_plan_opts& base) {
+  std::vector<int> roots{c->root};
+  const int h = heuristic_root(c, B);
+  if (h != roots[0]) roots.push_back(h);
+  std::vector<int> by_size;
+  for (int r = 0; r < (int)c->rels.size(); ++r) by_size.push_back(r);
+  std::stable_sort(by_size.begin(), by_size.end(),
+                   [&](int a, int b) { return c->rels[a].nrows > c->rels[b].nrows; });
+  for (int r : by_size) {
+    if ((int)roots.size() >= 4) break;
+    if (std::find(roots.begin(), roots.end(), r) == roots.end()) roots.push_back(r);
+  }
+  std::vector<lmf_plan_opts> out;
+  for (int r : roots)
+    for (int prec : {LMF_PREC_PLAIN_FP32, LMF_PREC_SPLIT_BF16})
+      for (int cps : {0, 1})
+        for (int nm : {0, 1}) {
+          lmf_plan_opts o = base;
+          o.root_mode = LMF_ROOT_EXPLICIT;
+          o.root_rel = r;
+          o.precision = prec;
+          o.ctas_per_sm = cps;
+          o.no_merge = nm;
+          out.push_back(o);
+        }
+  return out;
+}
+
+}  // namespace
+
+extern "C" {
+
+lmf_status lmf_plan_features(lmf_ctx* c, int batch_id, float* feat, int n) {
+  if (!c || !feat || batch_id < 0 || batch_id >= (int)c->batches.size()) return LMF_ERR_ARG;
+  Plan* P = c->batches[batch_id]->plan.get();
+  if (!P) return fail(c, LMF_ERR_STATE, "features before plan");
+  if (n < kPlanFeatures) return fail(c, LMF_ERR_ARG, "need %d feature slots", kPlanFeatures);
+  plan_features(c, *P, feat);
+  return LMF_OK;
+}
+
+lmf_status lmf_plan_candidates(lmf_ctx* c, int batch_id, const lmf_plan_opts* base, lmf_plan_opts* out, int max,
+                               int* n) {
+  if (!c || !n || batch_id < 0 || batch_id >= (int)c->batches.size()) return LMF_ERR_ARG;
+  if (!c->joined) return fail(c, LMF_ERR_STATE, "candidates before declare_join");
+  lmf_plan_opts b{};
+  if (base) b = *base;
+  auto cand = plan_candidates(c, *c->batches[batch_id], b);
+  *n = (int)cand.size();
+  for (int i = 0; i < std::min<int>(max, (int)cand.size()) && out; ++i) out[i] = cand[i];
+  return LMF_OK;
+}
+
+lmf_status lmf_plan_learned(lmf_ctx* c, int batch_id, lmf_mlp* model, const lmf_plan_opts* base,
+                            lmf_plan_opts* chosen) {
+  if (!c || batch_id < 0 || batch_id >= (int)c->batches.size()) return LMF_ERR_ARG;
+  if (!c->joined) return fail(c, LMF_ERR_STATE, "plan before declare_join");
+  lmf_plan_opts b{};
+  if (base) {
+    b = *base;
+  } else {
+    b.precision = LMF_PREC_SPLIT_BF16;
+    b.batching = LMF_BATCH_GRAPH;
+  }
+  if (!model) {  // fallback: the root rule of Sec. 3.3 with the base options
+    b.root_mode = LMF_ROOT_HEURISTIC;
+    lmf_status s = lmf_plan(c, batch_id, &b);
+    if (s == LMF_OK && chosen) {
+      *chosen = b;
+      chosen->root_mode = LMF_ROOT_EXPLICIT;
+      chosen->root_rel = c->batches[batch_id]->plan->root;
+    }
+    return s;
+  }
+  BatchH& B = *c->batches[batch_id];
+  auto cand = plan_candidates(c, B, b);
+  std::vector<float> feats;
+  std::vector<lmf_plan_opts> ok;
+  for (auto& o : cand) {
+    if (lmf_plan(c, batch_id, &o) != LMF_OK) continue;
+    float f[kPlanFeatures];
+    plan_features(c, *B.plan, f);
+    feats.insert(feats.end(), f, f + kPlanFeatures);
+    ok.push_back(o);
+  }
+  if (ok.empty()) return fail(c, LMF_ERR_UNSUPPORTED, "no candidate plan evaluates this batch");
+  float *dx = nullptr, *dy = nullptr;
+  CUDA_TRY(c, cudaMalloc(&dx, feats.size() * 4));
+  CUDA_TRY(c, cudaMalloc(&dy, ok.size() * 4));
+  CUDA_TRY(c, cudaMemcpy(dx, feats.data(), feats.size() * 4, cudaMemcpyHostToDevice));
+  lmf_status s = lmf_mlp_forward(model, dx, (int)ok.size(), dy);
+  std::vector<float> pred(ok.size());
+  if (s == LMF_OK) cudaMemcpy(pred.data(), dy, ok.size() * 4, cudaMemcpyDeviceToHost);
+  cudaFree(dx);
+  cudaFree(dy);
+  if (s) return fail(c, s, "cost model forward failed");
+  size_t best = 0;
+  for (size_t i = 1; i < ok.size(); ++i)
+    if (pred[i] < pred[best]) best = i;
+  s = lmf_plan(c, batch_id, &ok[best]);
+  if (s == LMF_OK && chosen) *chosen = ok[best];
+  return s;
 }
 
 }  // extern "C"

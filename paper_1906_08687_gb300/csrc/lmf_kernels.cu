@@ -112,7 +112,8 @@ __global__ void k_view_unique(const __grid_constant__ ViewArgs a) {
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row >= a.nrows) return;
   const int32_t k = a.key[row];
-  if (k < 0 || k >= a.K) {
+  if (k < 0) return;  // a negative key joins no parent row
+  if (k >= a.K) {
     atomicOr(a.status, kStatusKeyRange);
     return;
   }
@@ -159,7 +160,8 @@ __global__ void k_view_general(const __grid_constant__ ViewArgs a) {
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row >= a.nrows) return;
   const int32_t k = a.key[row];
-  if (k < 0 || k >= a.K) {
+  if (k < 0) return;  // a negative key joins no parent row
+  if (k >= a.K) {
     atomicOr(a.status, kStatusKeyRange);
     return;
   }

@@ -4,10 +4,10 @@
 // deltas; Sec. 2, Eq. regression-tree) is read as
 //     node (the conjunction of all but one predicate) x split (the remaining
 //     predicate x <= t or x > t on attribute f) x moment m (degree <= 2),
-// choosing as split the predicate that occurs in the fewest aggregates of the
-// batch (for a tree level: the candidate condition, while the ancestors'
-// conditions form the node).  Any choice gives the same product, so the
-// choice only affects speed.  With the sorted thresholds T_f of attribute f
+// choosing as split the predicate whose removal leaves the conjunction shared
+// by the most aggregates of the batch (for a tree level: the candidate
+// condition, while the ancestors' conditions form the node).  Any choice gives
+// the same product, so the choice only affects speed.  With the sorted thresholds T_f of attribute f
 // and the bucket b(x) = #{t in T_f : t < x},
 //     x <= T_f[j]  <=>  b(x) <= j,
 // so every (node, f, j, m) aggregate is a prefix (or, for >, suffix) sum of
@@ -692,4 +692,11 @@ void tree_shape(const TreePlan* tp, int* out5) {
   out5[4] = T.shape.chunk;
 }
 
+}  // namespace lmf
+
+namespace lmf {
+void tree_counts(const TreePlan* tp, int32_t* nodes, int32_t* groups) {
+  *nodes = tp->impl->dev.n_nodes;
+  *groups = tp->impl->dev.n_groups;
+}
 }  // namespace lmf

@@ -50,5 +50,6 @@ bool tree_needs_tuning(const TreePlan* tp);
 cudaError_t tree_autotune(TreePlan* tp, const RootParams& rp, cudaStream_t s);
 // chosen histogram shape, for reporting: slices, split attributes and nodes per slice, CTAs per SM, chunk rows
 void tree_shape(const TreePlan* tp, int* out5);
+void tree_counts(const TreePlan* tp, int32_t* nodes, int32_t* groups);
 
 }  // namespace lmf

@@ -23,8 +23,10 @@ LMF_KEY, LMF_CONT, LMF_CAT = 0, 1, 2
 LMF_POW, LMF_LE, LMF_GT = 0, 1, 2
 LMF_PREC_PLAIN_FP32, LMF_PREC_SPLIT_BF16 = 0, 1
 LMF_BATCH_SINGLE, LMF_BATCH_GRAPH = 0, 1
+LMF_ROOT_DECLARED, LMF_ROOT_EXPLICIT, LMF_ROOT_HEURISTIC = 0, 1, 2
 LMF_MAX_GROUP_BY = 3
 LMF_STAGES = 5
+LMF_PLAN_FEATURES = 24
 STAGE_NAMES = ['input', 'views', 'root_scan', 'tree', 'finalize']
 
 _ROLE = {'key': LMF_KEY, 'cont': LMF_CONT, 'cat': LMF_CAT}
@@ -50,7 +52,8 @@ class lmf_agg_spec(ctypes.Structure):
 class lmf_plan_opts(ctypes.Structure):
     _fields_ = [('precision', ctypes.c_int32), ('batching', ctypes.c_int32),
                 ('tile_rows', ctypes.c_int32), ('ctas_per_sm', ctypes.c_int32),
-                ('root_mode', ctypes.c_int32), ('reserved', ctypes.c_int32 * 3)]
+                ('root_mode', ctypes.c_int32), ('root_rel', ctypes.c_int32),
+                ('no_merge', ctypes.c_int32), ('reserved', ctypes.c_int32)]
 
 
 class lmf_plan_stats(ctypes.Structure):
@@ -59,6 +62,11 @@ class lmf_plan_stats(ctypes.Structure):
                 ('n_grouped_aggs', ctypes.c_int32), ('n_filtered_aggs', ctypes.c_int32),
                 ('n_kernels_per_run', ctypes.c_int32), ('unique_keys', ctypes.c_int32),
                 ('root_grid', ctypes.c_int32), ('precision', ctypes.c_int32),
+                ('root_rel', ctypes.c_int32), ('merged', ctypes.c_int32),
+                ('tree_nodes', ctypes.c_int32), ('tree_groups', ctypes.c_int32),
+                ('tree_slices', ctypes.c_int32), ('tree_split_w', ctypes.c_int32),
+                ('tree_node_w', ctypes.c_int32), ('tree_ctas_per_sm', ctypes.c_int32),
+                ('tree_chunk', ctypes.c_int32),
                 ('root_rows', ctypes.c_int64), ('scratch_bytes', ctypes.c_int64)]
 
 
@@ -83,6 +91,20 @@ _SIGNATURES = {
     'lmf_result_sizes': (_I, [_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     'lmf_read_results': (_I, [_P, _I, _P, _P, _I, _P]),
     'lmf_read_result': (_I, [_P, _I, _I, _P]),
+    'lmf_plan_candidates': (_I, [_P, _I, ctypes.POINTER(lmf_plan_opts), ctypes.POINTER(lmf_plan_opts), _I,
+                                 ctypes.POINTER(_I)]),
+    'lmf_plan_features': (_I, [_P, _I, ctypes.POINTER(ctypes.c_float), _I]),
+    'lmf_plan_learned': (_I, [_P, _I, _P, ctypes.POINTER(lmf_plan_opts), ctypes.POINTER(lmf_plan_opts)]),
+    'lmf_mlp_create': (_I, [_I, _I, _I, ctypes.c_uint64, ctypes.POINTER(_P)]),
+    'lmf_mlp_destroy': (_I, [_P]),
+    'lmf_mlp_num_params': (_I, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    'lmf_mlp_get_params': (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
+    'lmf_mlp_set_params': (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
+    'lmf_mlp_set_norm': (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                              ctypes.c_float, ctypes.c_float]),
+    'lmf_mlp_forward': (_I, [_P, _P, _I, _P]),
+    'lmf_mlp_grad': (_I, [_P, _P, _P, _I, _P, ctypes.POINTER(ctypes.c_float)]),
+    'lmf_mlp_train_step': (_I, [_P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
     'lmf_status_string': (ctypes.c_char_p, [_I]),
     'lmf_error_message': (ctypes.c_char_p, [_P]),
 }
@@ -199,8 +221,9 @@ class Engine:
         return bid.value
 
     def plan(self, batch: int, precision: int = LMF_PREC_SPLIT_BF16, batching: int = LMF_BATCH_GRAPH,
-             tile_rows: int = 0, ctas_per_sm: int = 0):
-        o = lmf_plan_opts(precision, batching, tile_rows, ctas_per_sm, 0)
+             tile_rows: int = 0, ctas_per_sm: int = 0, root_mode: int = 0, root_rel: int = 0,
+             no_merge: int = 0):
+        o = lmf_plan_opts(precision, batching, tile_rows, ctas_per_sm, root_mode, root_rel, no_merge, 0)
         self._check(self.lib.lmf_plan(self.ctx, batch, ctypes.byref(o)), 'lmf_plan')
 
     def plan_info(self, batch: int) -> dict:
@@ -245,6 +268,33 @@ class Engine:
         self._check(self.lib.lmf_read_result(self.ctx, batch, agg, ctypes.c_void_p(dst)),
                     'lmf_read_result')
 
+    def plan_opts(self, batch: int, opts: 'lmf_plan_opts'):
+        self._check(self.lib.lmf_plan(self.ctx, batch, ctypes.byref(opts)), 'lmf_plan')
+
+    def plan_candidates(self, batch: int, base: Optional['lmf_plan_opts'] = None) -> List['lmf_plan_opts']:
+        b = base or lmf_plan_opts(LMF_PREC_SPLIT_BF16, LMF_BATCH_GRAPH, 0, 0, 0, 0, 0, 0)
+        n = ctypes.c_int()
+        self._check(self.lib.lmf_plan_candidates(self.ctx, batch, ctypes.byref(b), None, 0, ctypes.byref(n)),
+                    'lmf_plan_candidates')
+        arr = (lmf_plan_opts * max(1, n.value))()
+        self._check(self.lib.lmf_plan_candidates(self.ctx, batch, ctypes.byref(b), arr, n.value, ctypes.byref(n)),
+                    'lmf_plan_candidates')
+        return [arr[i] for i in range(n.value)]
+
+    def plan_features(self, batch: int) -> np.ndarray:
+        f = np.zeros(LMF_PLAN_FEATURES, np.float32)
+        self._check(self.lib.lmf_plan_features(self.ctx, batch, f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                               LMF_PLAN_FEATURES), 'lmf_plan_features')
+        return f
+
+    def plan_learned(self, batch: int, model: Optional['Mlp'], base: Optional['lmf_plan_opts'] = None
+                     ) -> 'lmf_plan_opts':
+        b = base or lmf_plan_opts(LMF_PREC_SPLIT_BF16, LMF_BATCH_GRAPH, 0, 0, 0, 0, 0, 0)
+        out = lmf_plan_opts()
+        self._check(self.lib.lmf_plan_learned(self.ctx, batch, model.h if model else None, ctypes.byref(b),
+                                              ctypes.byref(out)), 'lmf_plan_learned')
+        return out
+
     # -- convenience: all results as numpy arrays ------------------------------
     def results(self, batch: int, n_aggs: int) -> List[np.ndarray]:
         n_i64, n_f64 = self.result_sizes(batch)
@@ -255,6 +305,71 @@ class Engine:
         for n, dt, off in self.result_layout(batch, n_aggs):
             out.append((i64 if dt == LMF_I64 else f64)[off:off + n].copy())
         return out
+
+
+class Mlp:
+    """The planner's cost model (lmf_mlp): FP32 MLP with hand-written GPU kernels."""
+
+    def __init__(self, in_dim: int = 24, hidden: int = 128, seed: int = 0, device: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        st = self.lib.lmf_mlp_create(device, in_dim, hidden, seed, ctypes.byref(h))
+        if st != LMF_OK:
+            raise LmfError(st, 'lmf_mlp_create')
+        self.h = h
+        self.in_dim, self.hidden = in_dim, hidden
+        n = ctypes.c_int64()
+        self.lib.lmf_mlp_num_params(h, ctypes.byref(n))
+        self.n_params = n.value
+
+    def close(self):
+        if getattr(self, 'h', None):
+            self.lib.lmf_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st, what):
+        if st != LMF_OK:
+            raise LmfError(st, what)
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.n_params, np.float32)
+        self._ck(self.lib.lmf_mlp_get_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                             self.n_params), 'lmf_mlp_get_params')
+        return p
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, np.float32)
+        self._ck(self.lib.lmf_mlp_set_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                             self.n_params), 'lmf_mlp_set_params')
+
+    def set_norm(self, mean, std, y_mean: float, y_std: float):
+        m = np.ascontiguousarray(mean, np.float32)
+        s = np.ascontiguousarray(std, np.float32)
+        self._ck(self.lib.lmf_mlp_set_norm(self.h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                           s.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                           float(y_mean), float(y_std)), 'lmf_mlp_set_norm')
+
+    def forward(self, x_dev: int, batch: int, y_dev: int):
+        self._ck(self.lib.lmf_mlp_forward(self.h, ctypes.c_void_p(x_dev), batch, ctypes.c_void_p(y_dev)),
+                 'lmf_mlp_forward')
+
+    def grad(self, x_dev: int, y_dev: int, batch: int, grad_dev: int) -> float:
+        loss = ctypes.c_float()
+        self._ck(self.lib.lmf_mlp_grad(self.h, ctypes.c_void_p(x_dev), ctypes.c_void_p(y_dev), batch,
+                                       ctypes.c_void_p(grad_dev), ctypes.byref(loss)), 'lmf_mlp_grad')
+        return loss.value
+
+    def train_step(self, x_dev: int, y_dev: int, batch: int, lr: float) -> float:
+        loss = ctypes.c_float()
+        self._ck(self.lib.lmf_mlp_train_step(self.h, ctypes.c_void_p(x_dev), ctypes.c_void_p(y_dev), batch,
+                                             float(lr), ctypes.byref(loss)), 'lmf_mlp_train_step')
+        return loss.value
 
 
 def column_dtype(arr) -> int:
