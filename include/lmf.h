@@ -315,6 +315,33 @@ lmf_status lmf_mlp_train_step(lmf_mlp* m, const float* x_dev, const float* y_dev
 lmf_status lmf_plan_learned(lmf_ctx* ctx, int batch_id, lmf_mlp* model, const lmf_plan_opts* base,
                             lmf_plan_opts* chosen);
 
+/*
+ * The covar Gram of one relation, computed without allocating any device
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot call cudaMalloc -- code running under a memory pool or custom
+ * allocator that forbids outside allocations, code that must avoid the
+ * implicit synchronisation an allocation can cause, or a process whose device
+ * memory is already handed to another framework.
+ *
+ * dev_cols: host array of ncols device pointers, each to nrows FP32 values.
+ * dev_gram: device buffer of (ncols + 1)^2 doubles, written row-major with
+ *           G = sum_r z_r z_r^T, z_r = [1, x_1(r), ..., x_ncols(r)] (G[0][0] = nrows).
+ * cuda_stream: the stream to enqueue on (NULL: the legacy default stream).
+ * The same kernel as the plain root scan (FP32 products, ordered FP64
+ * combine) runs with its scratch -- per-CTA partial Grams and counts -- in a
+ * fixed array compiled into the library (about 2.5 MB: at most 304 CTAs of
+ * 32 x 32 doubles), which every GPU that loads the library keeps until the
+ * process exits.  Limit: ncols <= 31; larger sizes, negative sizes and null
+ * pointers return LMF_ERR_ARG; CUDA failures return LMF_ERR_CUDA.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the array, so calls that overlap on the GPU race; enqueue them
+ * on one stream or wait between them.  Asynchronous: the result is ready when
+ * the stream reaches it.
+ */
+lmf_status lmf_gram_noalloc(const float* const* dev_cols, int ncols, int64_t nrows, double* dev_gram,
+                            void* cuda_stream);
+
 /* Static text of a status code. */
 const char* lmf_status_string(lmf_status s);
 

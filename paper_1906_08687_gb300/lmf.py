@@ -105,6 +105,7 @@ _SIGNATURES = {
     'lmf_mlp_forward': (_I, [_P, _P, _I, _P]),
     'lmf_mlp_grad': (_I, [_P, _P, _P, _I, _P, ctypes.POINTER(ctypes.c_float)]),
     'lmf_mlp_train_step': (_I, [_P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
+    'lmf_gram_noalloc': (_I, [ctypes.POINTER(ctypes.c_void_p), _I, ctypes.c_int64, _P, _P]),
     'lmf_status_string': (ctypes.c_char_p, [_I]),
     'lmf_error_message': (ctypes.c_char_p, [_P]),
 }
