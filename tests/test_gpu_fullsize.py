@@ -1,0 +1,55 @@
+"""Parity at the benchmark sizes under the strict error rule (no arithmetic
+floor): the whole batch runs on the GPU, the oracle re-evaluates a seeded
+sample of its aggregates over the full join."""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from workloads import config2, config3, config4
+
+from lmf_testlib import compare, run_engine
+
+pytestmark = pytest.mark.gpu
+
+
+def _sample(n, k, seed):
+    rng = np.random.default_rng(seed)
+    return sorted(set([0] + rng.choice(n, size=min(k, n), replace=False).tolist()))
+
+
+@pytest.fixture(scope='module')
+def snowflake20m():
+    return config2(20_000_000)
+
+
+@pytest.mark.parametrize('precision', [0, 1])
+def test_config2_full_size(snowflake20m, precision):
+    sch, batch = snowflake20m
+    got, info, eng = run_engine(sch, batch, precision=precision, batching=1)
+    assert info['precision'] == precision and info['root_rows'] == 20_000_000
+    idx = _sample(len(batch), 64, 7 + precision)
+    want = oracle.evaluate(sch, [batch[i] for i in idx])
+    fails, stats = compare([got[i] for i in idx], want)
+    assert not fails, (fails[:3], stats)
+    eng.close()
+
+
+def test_config3_full_size():
+    sch, batch = config3(10_000_000)
+    got, info, eng = run_engine(sch, batch, precision=1, batching=1)
+    assert info['tree_nodes'] == 64 and info['tree_groups'] == 1
+    idx = _sample(len(batch), 300, 11)
+    want = oracle.evaluate(sch, [batch[i] for i in idx])
+    fails, stats = compare([got[i] for i in idx], want)
+    assert not fails, (fails[:3], stats)
+    eng.close()
+
+
+def test_config4_reduced_exact():
+    """Chow-Liu pair counts, marginals and the data cube: bit-exact counts."""
+    sch, batch = config4(400_000)
+    got, info, eng = run_engine(sch, batch, precision=1, batching=1)
+    want = oracle.evaluate(sch, batch)
+    fails, stats = compare(got, want)
+    assert not fails, fails[:3]
+    eng.close()

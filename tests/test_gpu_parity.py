@@ -44,7 +44,7 @@ def test_config1_ragged_sizes():
 @pytest.mark.parametrize('precision', [PLAIN, SPLIT])
 def test_config2_snowflake_reduced(precision):
     sch, batch = config2(300_007)
-    _, info, stats = _check(sch, batch, precision, GRAPH)
+    _, info, stats = _check(sch, batch, precision, GRAPH, floor=ARITH_FLOOR)
     assert info['precision'] == precision
     assert info['n_grouped_aggs'] == 10 * 31 + 45
     assert info['n_views'] == 6 and info['n_probe_groups'] == 3

@@ -63,7 +63,7 @@ def test_merge_off_same_results():
     for x, y in zip(a, b):
         if x.dtype == np.int64:
             assert np.array_equal(x, y)
-    fails, _ = compare(b, oracle.evaluate(sch, batch))
+    fails, _ = compare(b, oracle.evaluate(sch, batch), arith_floor=ARITH_FLOOR)
     assert not fails
 
 
