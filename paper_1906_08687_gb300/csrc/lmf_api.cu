@@ -870,7 +870,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   std::vector<size_t> rv_hist_off(rp.n_grp, 0), rv_R_off(rp.n_grp, 0);
   std::vector<std::vector<int>> rv_slots(rp.n_grp);     // z index per slot
   std::vector<int> rv_used(rp.n_grp, 0);
-  struct GPlan { int mode; int grp; int slot; int mu_word; int direct; double scale; int64_t cells; size_t out_off; };
+  struct GPlan { int mode; int grp; int slot; int mu_word; int direct; double scale; int64_t cells; size_t out_off; int cache_off; };
   std::vector<GPlan> gplan(B.aggs.size());
   for (size_t a = 0; a < B.aggs.size(); ++a) {
     if (cls[a].kind != 1) continue;
@@ -884,6 +884,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       gsrc = (gsrc == -2 || gsrc == q) ? q : -3;
     }
     GPlan gp{};
+    gp.cache_off = -1;
     gp.cells = cells;
     gp.direct = (gsrc < 0) ? 1 : 0;   // root categories or several keys: per-row table
     std::string f = cls[a].mono.empty() ? "" : cls[a].mono[0];
@@ -964,14 +965,73 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     cp.sc_off = A.take((size_t)P->groups[cp.group].K * (cp.d * (cp.d + 1) / 2) * 8 + 8);
   }
 
+  // ---- hot-cell cache: per CTA, the hottest (value, value) cells of every
+  // pair-count table are 32-bit counters in shared memory; Zipf-skewed
+  // categories otherwise serialise L2 atomics on a few addresses (a table's
+  // hottest cell takes 3-19% of all rows in the snowflake workload).  The hot
+  // values are the most frequent ones of each category column, counted here.
+  constexpr int kHotVals = 8, kCacheBudget = 24 * 1024 / 4;
+  std::map<int, std::vector<int32_t>> hot_vals;  // row category -> its hot values
+  int cache_cells = 0;
+  {
+    auto top_of = [&](const int32_t* col, int64_t n, int K, int h, std::vector<int32_t>* out) -> lmf_status {
+      if (n <= 0 || K <= 0) return LMF_OK;
+      unsigned int* d = nullptr;
+      CUDA_TRY(c, cudaMalloc(&d, sizeof(unsigned int) * K));
+      CUDA_TRY(c, cudaMemsetAsync(d, 0, sizeof(unsigned int) * K, c->stream));
+      CUDA_TRY(c, launch_key_stats(col, n, d, K, nullptr, c->stream));
+      std::vector<unsigned int> cnt(K);
+      CUDA_TRY(c, cudaMemcpyAsync(cnt.data(), d, sizeof(unsigned int) * K, cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      cudaFree(d);
+      std::vector<int32_t> idx(K);
+      for (int i = 0; i < K; ++i) idx[i] = i;
+      const int take = std::min(h, K);
+      std::partial_sort(idx.begin(), idx.begin() + take, idx.end(),
+                        [&](int a, int b) { return cnt[a] > cnt[b] || (cnt[a] == cnt[b] && a < b); });
+      for (int i = 0; i < take; ++i)
+        if (cnt[idx[i]] > 0) out->push_back(idx[i]);
+      return LMF_OK;
+    };
+    // pair COUNT tables with w in {0, 1}: a CTA counts fewer than 2^32 rows
+    for (size_t a = 0; a < B.aggs.size(); ++a) {
+      if (cls[a].kind != 1 || !gplan[a].direct || B.aggs[a].gb.size() != 2) continue;
+      if (!cls[a].mono.empty() || !P->unique_all) continue;
+      if (cache_cells + kHotVals * kHotVals > kCacheBudget) break;
+      for (auto& gname : B.aggs[a].gb) {
+        const int rc = P->rowcat.at(gname);
+        if (hot_vals.count(rc)) continue;
+        int col, r = owner_of(c, gname, &col);
+        const ColumnH& cc = c->rels[r].cols[col];
+        lmf_status st = top_of(static_cast<const int32_t*>(cc.dptr()), c->rels[r].nrows, cc.dom, kHotVals, &hot_vals[rc]);
+        if (st) return st;
+      }
+      gplan[a].cache_off = cache_cells;
+      cache_cells += kHotVals * kHotVals;
+    }
+  }
+  size_t hot_lut_bytes = 0;
+  std::map<int, size_t> hot_lut_at;  // row category -> offset in the lut
+  for (auto& kv : hot_vals) {
+    int col, r = owner_of(c, [&] {
+      for (auto& n : P->rowcat)
+        if (n.second == kv.first) return n.first;
+      return std::string();
+    }(), &col);
+    hot_lut_at[kv.first] = hot_lut_bytes;
+    hot_lut_bytes += (size_t)c->rels[r].cols[col].dom;
+  }
+  const size_t hot_lut_off = A.take(hot_lut_bytes + 1);
+  const size_t cache_dst_off = A.take((size_t)cache_cells * 8 + 8);
+
   // root scan shape
   int mp = 16;
   while (mp < m) mp += 16;
   P->mp = mp;
   const int T = root_plain_tile_rows();
   P->n_tiles = (Root.nrows + T - 1) / T;
-  P->smem = root_plain_smem(mp, ncat);
-  int cps = P->opts.ctas_per_sm > 0 ? P->opts.ctas_per_sm : (mp <= 32 ? 2 : 1);
+  P->smem = root_plain_smem(mp, ncat, cache_cells);
+  int cps = P->opts.ctas_per_sm > 0 ? P->opts.ctas_per_sm : (P->smem <= 110 * 1024 ? 2 : 1);
   P->grid = (int)std::max<int64_t>(1, std::min<int64_t>(P->n_tiles, (int64_t)c->num_sms * cps));
   CUDA_TRY(c, root_plain_prepare(mp, P->smem));
   // the split-bf16 tensor-core Gram needs w in {0, 1} (unique child keys) and
@@ -981,7 +1041,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   if (use_tc) {
     P->tc = std::make_unique<GramTcPlan>();
     gram_tc_shape(m, Root.nrows, c->num_sms, P->opts.tile_rows, P->tc.get());
-    CUDA_TRY(c, gram_tc_configure(P->tc.get(), ncat, P->opts.ctas_per_sm));
+    CUDA_TRY(c, gram_tc_configure(P->tc.get(), ncat, P->opts.ctas_per_sm, cache_cells));
     P->grid = P->tc->grid;
   }
   P->part_off = A.take((size_t)P->grid * mp * mp * 8);
@@ -1063,6 +1123,23 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     }
     rv_index[q] = rp.n_rv++;
   }
+  // hot-cell tables: category value -> hot index, and the global cell every
+  // cache cell flushes to
+  std::vector<long long*> cache_dst(cache_cells, P->at<long long>(P->count_off));
+  {
+    std::vector<int8_t> lut(hot_lut_bytes + 1, -1);
+    for (int i = 0; i < kMaxCat; ++i) rp.hot_lut_off[i] = -1;
+    for (auto& kv : hot_vals) {
+      const size_t at = hot_lut_at[kv.first];
+      for (size_t h = 0; h < kv.second.size(); ++h) lut[at + kv.second[h]] = (int8_t)h;
+      rp.hot_lut_off[kv.first] = (int32_t)at;
+    }
+    CUDA_TRY(c, cudaMemcpy(P->arena.base + hot_lut_off, lut.data(), lut.size(), cudaMemcpyHostToDevice));
+  }
+  rp.hot_lut = P->at<int8_t>(hot_lut_off);
+  rp.hot_h = kHotVals;
+  rp.cache_cells = cache_cells;
+  rp.cache_dst = P->at<long long*>(cache_dst_off);
   std::vector<RvTask> tasks;
   std::vector<DirectAgg> direct;
   for (size_t a = 0; a < B.aggs.size(); ++a) {
@@ -1081,6 +1158,14 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       d.z = f.empty() ? -1 : P->zidx.at(f);
       d.scale = (float)gp.scale;
       d.out = P->at<long long>(gp.out_off);
+      d.cache_off = gp.cache_off;
+      if (gp.cache_off >= 0) {
+        const auto& va = hot_vals.at(d.cat[0]);
+        const auto& vb = hot_vals.at(d.cat[1]);
+        for (size_t ha = 0; ha < va.size(); ++ha)
+          for (size_t hb = 0; hb < vb.size(); ++hb)
+            cache_dst[gp.cache_off + ha * kHotVals + hb] = d.out + (int64_t)va[ha] * d.dom[1] + vb[hb];
+      }
       direct.push_back(d);
     } else {
       RvTask t{};
@@ -1100,6 +1185,9 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       P->max_group_K = std::max(P->max_group_K, P->groups[RR.groups[gp.grp]].K);
     }
   }
+  if (cache_cells > 0)
+    CUDA_TRY(c, cudaMemcpy(P->arena.base + cache_dst_off, cache_dst.data(), sizeof(long long*) * cache_cells,
+                           cudaMemcpyHostToDevice));
   P->rv_tasks = tasks;
   P->direct = direct;
   rp.n_direct = (int)direct.size();

@@ -163,15 +163,16 @@ __device__ __forceinline__ void pack_row(unsigned char* sA, unsigned char* sB, c
 }
 
 struct TcLayout {
-  uint32_t z_off, c_off, bar_off, slot_off, cred_off, total;
+  uint32_t z_off, c_off, cache_off, bar_off, slot_off, cred_off, total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int n_rowcat) {
+__host__ __device__ inline TcLayout tc_layout(int n_rowcat, int cache_cells) {
   TcLayout L;
   L.z_off = kAStage + kBStage;
   L.c_off = L.z_off + kTcRows * kZld * 4;
   const uint32_t ncat = n_rowcat > 0 ? n_rowcat : 1;
-  L.bar_off = (L.c_off + kTcRows * ncat * 4 + 15) & ~15u;
+  L.cache_off = (L.c_off + kTcRows * ncat * 4 + 15) & ~15u;
+  L.bar_off = (L.cache_off + static_cast<uint32_t>(cache_cells) * 4 + 15) & ~15u;
   L.slot_off = L.bar_off + 16;
   L.cred_off = L.slot_off + 16;
   L.total = L.cred_off + 4 * 8;
@@ -181,8 +182,9 @@ __host__ __device__ inline TcLayout tc_layout(int n_rowcat) {
 __global__ void __launch_bounds__(kTcThreads) k_root_tc(const __grid_constant__ RootParams p, int64_t n_tiles,
                                                          double* part) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const TcLayout L = tc_layout(p.n_rowcat);
+  const TcLayout L = tc_layout(p.n_rowcat, p.cache_cells);
   unsigned char* sA = smem;
+  uint32_t* cache = reinterpret_cast<uint32_t*>(smem + L.cache_off);
   unsigned char* sB = smem + kAStage;
   float* Zs = reinterpret_cast<float*>(smem + L.z_off);
   int32_t* Cs = reinterpret_cast<int32_t*>(smem + L.c_off);
@@ -195,6 +197,7 @@ __global__ void __launch_bounds__(kTcThreads) k_root_tc(const __grid_constant__ 
   const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
   const uint32_t bar[2] = {smem_u32(&bars[0]), smem_u32(&bars[1])};
 
+  root_cache_zero(p, cache);
   // the fourth M block of A stays zero
   for (int i = tid; i < 4 * (int)kSBO / 16; i += kTcThreads)
     reinterpret_cast<uint4*>(sA + 12 * kSBO)[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(kTcThreads) k_root_tc(const __grid_constant__ 
     const int buf = static_cast<int>(it & 1);
     float* zrow = Zs + tid * kZld;
     int32_t* crow = Cs + tid * ncat;
-    cnt_acc += root_row_pass<32>(p, tile * kTcRows + tid, zrow, crow);
+    cnt_acc += root_row_pass<32>(p, tile * kTcRows + tid, zrow, crow, p.cache_cells ? cache : nullptr);
     if (it > 0) {  // the previous tile's MMAs read the operand stage
       const int64_t pi = it - 1;
       if (!mbar_wait(bar[pi & 1], static_cast<uint32_t>((pi >> 1) & 1))) ok = false;
@@ -270,6 +273,7 @@ __global__ void __launch_bounds__(kTcThreads) k_root_tc(const __grid_constant__ 
     drain(static_cast<int>(pi & 1));
   }
 
+  root_cache_flush(p, cache);
   if (warp < 3) {
     double* out = part + ((static_cast<int64_t>(blockIdx.x) * 3 + warp) * 32 + lane) * 32;
 #pragma unroll
@@ -326,10 +330,10 @@ void gram_tc_alloc(GramTcPlan* tp, const std::function<size_t(size_t)>& take) {
   tp->part_off = take(static_cast<size_t>(tp->grid) * 3 * 1024 * sizeof(double));
 }
 
-cudaError_t gram_tc_configure(GramTcPlan* tp, int n_rowcat, int ctas_per_sm) {
-  const TcLayout L = tc_layout(n_rowcat);
+cudaError_t gram_tc_configure(GramTcPlan* tp, int n_rowcat, int ctas_per_sm, int cache_cells) {
+  const TcLayout L = tc_layout(n_rowcat, cache_cells);
   tp->smem = L.total;
-  int cps = ctas_per_sm > 0 ? ctas_per_sm : (L.total <= 72 * 1024 ? 3 : 2);
+  int cps = ctas_per_sm > 0 ? ctas_per_sm : (L.total <= 72 * 1024 ? 3 : (L.total <= 110 * 1024 ? 2 : 1));
   cps = cps > 4 ? 4 : cps;  // four CTAs of 128 tensor-memory columns fill an SM's 512
   int64_t g = static_cast<int64_t>(tp->num_sms) * cps;
   if (g > tp->n_tiles) g = tp->n_tiles;

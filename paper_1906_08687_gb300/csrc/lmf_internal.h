@@ -112,6 +112,7 @@ struct DirectAgg {
   int32_t z;                         // -1: count; else z index of SUM(z)
   float scale;
   long long* out;                    // [cells] fixed-point / counts
+  int32_t cache_off;                 // pair tables: first cache cell of its hot x hot block, else -1
 };
 
 struct OmegaAcc {                    // SUM over root rows of w / cnt_e per key of e
@@ -142,6 +143,13 @@ struct RootParams {
   int32_t n_om;
   OmegaAcc om[kMaxGroups * 4];
   uint32_t* status;
+  // per-CTA shared-memory cache of the hot cells of pair-count tables (Zipf-hot
+  // category values), 32-bit counters flushed once per CTA
+  int32_t cache_cells;               // 0: no cache
+  int32_t hot_h;                     // hot values per category (pair tables use hot_h^2 cells)
+  const int8_t* hot_lut;             // concatenated per-category value -> hot index, -1 cold
+  int32_t hot_lut_off[kMaxCat];      // per row category: offset into hot_lut, -1 none
+  long long* const* cache_dst;       // [cache_cells]: global cell each cache cell flushes to
 };
 
 // answering a grouped aggregate from a reverse view: loop over the group's keys
@@ -182,7 +190,7 @@ cudaError_t launch_view_general(const ViewArgs& a, cudaStream_t s);
 cudaError_t launch_view_finalize(const ViewFinalizeArgs& a, cudaStream_t s);
 cudaError_t launch_root_plain(const RootParams& p, int mp, int grid, int64_t n_tiles,
                               size_t smem, cudaStream_t s);
-size_t root_plain_smem(int mp, int n_rowcat);
+size_t root_plain_smem(int mp, int n_rowcat, int cache_cells = 0);
 cudaError_t root_plain_prepare(int mp, size_t smem);
 int root_plain_tile_rows();
 cudaError_t launch_combine(const double* part, int grid, int mp, int m, const long long* cnt_part,

@@ -266,7 +266,10 @@ __global__ void __launch_bounds__(256) k_root_plain(const __grid_constant__ Root
   float* Za = reinterpret_cast<float*>(smem_raw);
   float* Zb = Za + T * LD;
   int32_t* Cs = reinterpret_cast<int32_t*>(Zb + T * LD);
+  uint32_t* cache = reinterpret_cast<uint32_t*>(Cs + T * (p.n_rowcat > 0 ? p.n_rowcat : 1));
   const int tid = threadIdx.x;
+  root_cache_zero(p, cache);
+  __syncthreads();
   const int gblk = tid % NB, grow = tid / NB;
   const bool active = grow < RG;
   int bi = 0, t = gblk;
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(256) k_root_plain(const __grid_constant__ Root
       const int64_t row = tile * T + tid;
       float* zrow = Zb + tid * LD;
       int32_t* crow = Cs + tid * (p.n_rowcat > 0 ? p.n_rowcat : 1);
-      const long long w = root_row_pass<MP>(p, row, zrow, crow);
+      const long long w = root_row_pass<MP>(p, row, zrow, crow, p.cache_cells ? cache : nullptr);
       cnt_acc += w;
       // w * z for the left operand
       const float wf = static_cast<float>(w);
@@ -323,6 +326,7 @@ __global__ void __launch_bounds__(256) k_root_plain(const __grid_constant__ Root
     __syncthreads();
   }
 
+  root_cache_flush(p, cache);
   // ---------------- CTA reduction of the row groups, FP64 partial out
   double* red = reinterpret_cast<double*>(smem_raw);  // [NB * 16][RG]
   if (active) {
@@ -356,10 +360,10 @@ __global__ void __launch_bounds__(256) k_root_plain(const __grid_constant__ Root
   }
 }
 
-size_t root_plain_smem(int mp, int n_rowcat) {
+size_t root_plain_smem(int mp, int n_rowcat, int cache_cells) {
   size_t z = (size_t)2 * kPlainT * (mp + 4) * sizeof(float);
   size_t c = (size_t)kPlainT * (n_rowcat > 0 ? n_rowcat : 1) * sizeof(int32_t);
-  return z + c;
+  return z + c + (size_t)cache_cells * 4;
 }
 int root_plain_tile_rows() { return kPlainT; }
 

@@ -77,9 +77,10 @@ __device__ __forceinline__ long long root_row_z(const RootParams& p, int64_t row
   return w;
 }
 
-// grouped updates of one joining row (w != 0)
+// grouped updates of one joining row (w != 0); cache (may be null) holds the
+// CTA's counters for the hot cells of pair-count tables
 __device__ __forceinline__ void root_row_grouped(const RootParams& p, int64_t row, const float* zrow,
-                                                 const int32_t* crow, long long w) {
+                                                 const int32_t* crow, long long w, uint32_t* cache) {
   for (int r = 0; r < p.n_rv; ++r) {
     const RevView& R = p.rv[r];
     const int32_t fk = p.grp[R.grp].fk[row];
@@ -89,9 +90,18 @@ __device__ __forceinline__ void root_row_grouped(const RootParams& p, int64_t ro
   }
   for (int d = 0; d < p.n_direct; ++d) {
     const DirectAgg& A = p.direct[d];
+    const long long v = A.z < 0 ? w : rp_fixp(w, zrow[A.z], A.scale);
+    if (cache && A.cache_off >= 0) {  // a pair-count table: 32-bit counter cells
+      const int ha = __ldg(p.hot_lut + p.hot_lut_off[A.cat[0]] + crow[A.cat[0]]);
+      const int hb = __ldg(p.hot_lut + p.hot_lut_off[A.cat[1]] + crow[A.cat[1]]);
+      if (ha >= 0 && hb >= 0) {
+        atomicAdd(cache + A.cache_off + ha * p.hot_h + hb, static_cast<uint32_t>(v));
+        continue;
+      }
+    }
     int64_t cell = 0;
     for (int q = 0; q < A.n_gb; ++q) cell = cell * A.dom[q] + crow[A.cat[q]];
-    rp_add_ll(A.out + cell, A.z < 0 ? w : rp_fixp(w, zrow[A.z], A.scale));
+    rp_add_ll(A.out + cell, v);
   }
   for (int o = 0; o < p.n_om; ++o) {
     const OmegaAcc& O = p.om[o];
@@ -102,11 +112,23 @@ __device__ __forceinline__ void root_row_grouped(const RootParams& p, int64_t ro
   }
 }
 
+// the CTA's cache of 32-bit counters: zero at start, flush to the global
+// int64 cells at the end
+__device__ __forceinline__ void root_cache_zero(const RootParams& p, uint32_t* cache) {
+  for (int i = threadIdx.x; i < p.cache_cells; i += blockDim.x) cache[i] = 0u;
+}
+__device__ __forceinline__ void root_cache_flush(const RootParams& p, const uint32_t* cache) {
+  for (int i = threadIdx.x; i < p.cache_cells; i += blockDim.x) {
+    const unsigned long long v = cache[i];
+    if (v) atomicAdd(reinterpret_cast<unsigned long long*>(p.cache_dst[i]), v);
+  }
+}
+
 template <int MP>
 __device__ __forceinline__ long long root_row_pass(const RootParams& p, int64_t row, float* zrow,
-                                                   int32_t* crow) {
+                                                   int32_t* crow, uint32_t* cache) {
   const long long w = root_row_z<MP>(p, row, zrow, crow);
-  if (w != 0) root_row_grouped(p, row, zrow, crow, w);
+  if (w != 0) root_row_grouped(p, row, zrow, crow, w, cache);
   return w;
 }
 
