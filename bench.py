@@ -36,7 +36,9 @@ METRIC = 'G joined-tuple-aggregates/s, HBM % of peak; speedup vs plain at ≤1e-
 UNIT = 'G joined-tuple-aggregates/s'
 PROFILE_SUMMARY = os.path.join(ROOT, 'profiles', 'root_scan_snowflake20M.md')
 KERNEL_SOURCES = ['paper_1906_08687_gb300/csrc/lmf_kernels.cu',
-                  'paper_1906_08687_gb300/csrc/lmf_gram_tc.cu']
+                  'paper_1906_08687_gb300/csrc/lmf_gram_tc.cu',
+                  'paper_1906_08687_gb300/csrc/lmf_rowpass.cuh',
+                  'paper_1906_08687_gb300/csrc/lmf_internal.h']
 
 
 def parse():
@@ -47,6 +49,9 @@ def parse():
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--n-fact', type=int, default=20_000_000)
     ap.add_argument('--precision', default='split', choices=['split', 'plain'])
+    ap.add_argument('--fact-order', default='sorted', choices=['sorted', 'random'],
+                    help='fact rows sorted by their join attributes (the input order of the '
+                         "paper's experiments) or in generation order")
     ap.add_argument('--cpu-sample-rows', type=int, default=10_000_000)
     ap.add_argument('--ref-sample-rows', type=int, default=200_000)
     ap.add_argument('--check-aggs', type=int, default=48,
@@ -152,6 +157,10 @@ def profiled_traffic(precision: str):
     return float(m.group(1))
 
 
+FACT_ORDER_SORTED = ('sorted by the join attributes, fewest distinct values first (k3, k2, k1): '
+                     'the scan order of Sec. 3.5, as the paper\'s experiments load every relation')
+
+
 # ----------------------------------------------------------------------------
 def run_reference(args):
     """The oracle on this host's cores, one bounded sample of the workload per step."""
@@ -161,7 +170,7 @@ def run_reference(args):
     from oracle import oracle
     from workloads import config2
     oracle.build()
-    sch, batch = config2(args.n_fact)
+    sch, batch = config2(args.n_fact, fact_order=args.fact_order)
     S = min(args.ref_sample_rows, args.n_fact)
     nt = oracle.max_threads()
     times = []
@@ -181,7 +190,7 @@ def run_reference(args):
         'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': t * 1e3, 'higher_is_better': True,
         'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
         'config': {'workload': f'snowflake-{args.n_fact}', 'n_aggregates': len(batch),
-                   'sample_rows_per_step': S},
+                   'fact_order': args.fact_order, 'sample_rows_per_step': S},
         'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': nt, 'kind': 'oracle', 'sample': sample},
         'e2e': {'value': value, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
     }
@@ -209,7 +218,7 @@ def main():
     from workloads import config2, SEED_BASE
     from lmf_testlib import compare, to_device, to_pinned
 
-    sch, batch = config2(args.n_fact, seed=SEED_BASE + 2 + 1000 * rank)
+    sch, batch = config2(args.n_fact, seed=SEED_BASE + 2 + 1000 * rank, fact_order=args.fact_order)
     n_agg = len(batch)
     dev = to_device(sch, f'cuda:{local}')
     stream = torch.cuda.Stream()
@@ -313,6 +322,8 @@ def main():
         'config': {'workload': f'snowflake-{args.n_fact} (3 FKs, 8 fact + 22 dimension features, '
                                f'10 categoricals; covar + grouped + pair counts)',
                    'n_aggregates': n_agg, 'join_rows': join_rows, 'precision': info['precision'],
+                   'fact_order': (FACT_ORDER_SORTED if args.fact_order == 'sorted'
+                                  else 'generation order (i.i.d. rows)'),
                    'batching': 'cuda-graph', 'kernels_per_step': info['n_kernels_per_run'],
                    'l2': f'inputs larger than L2 ({fact_bytes / 1e6:.0f} MB fact table per step)',
                    'parallelism': f'replicas x{ws}'},

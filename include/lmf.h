@@ -137,6 +137,9 @@ typedef struct {
   int32_t tree_chunk;         /* ... rows per work item */
   int64_t root_rows;          /* rows of the root relation */
   int64_t scratch_bytes;      /* device bytes owned by the plan */
+  int32_t resident_group;     /* probe group whose key is held per CTA (a root sorted on
+                                 that foreign key), -1: none */
+  int32_t resident_cells;     /* shared-memory counters of the resident-key tables */
 } lmf_plan_stats;
 
 /*

@@ -870,7 +870,10 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   std::vector<size_t> rv_hist_off(rp.n_grp, 0), rv_R_off(rp.n_grp, 0);
   std::vector<std::vector<int>> rv_slots(rp.n_grp);     // z index per slot
   std::vector<int> rv_used(rp.n_grp, 0);
-  struct GPlan { int mode; int grp; int slot; int mu_word; int direct; double scale; int64_t cells; size_t out_off; int cache_off; };
+  struct GPlan {
+    int mode; int grp; int slot; int mu_word; int direct; double scale; int64_t cells; size_t out_off; int cache_off;
+    int res_off, res_q, res_word, res_n;
+  };
   std::vector<GPlan> gplan(B.aggs.size());
   for (size_t a = 0; a < B.aggs.size(); ++a) {
     if (cls[a].kind != 1) continue;
@@ -885,6 +888,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     }
     GPlan gp{};
     gp.cache_off = -1;
+    gp.res_off = -1;
     gp.cells = cells;
     gp.direct = (gsrc < 0) ? 1 : 0;   // root categories or several keys: per-row table
     std::string f = cls[a].mono.empty() ? "" : cls[a].mono[0];
@@ -965,6 +969,65 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     cp.sc_off = A.take((size_t)P->groups[cp.group].K * (cp.d * (cp.d + 1) / 2) * 8 + 8);
   }
 
+  // ---- resident key: the root's foreign key with the fewest changes between
+  // adjacent rows, if its runs average at least kResRun rows (a root sorted on
+  // its join attributes, Sec. 3.5), carries the COUNT tables that take exactly
+  // one category from its group; their counters for the current key live in
+  // shared memory (kResBudget of them in all)
+  constexpr int64_t kResRun = 1024;
+  constexpr int kResBudget = 24 * 1024 / 4, kResTableMax = 4096;
+  int res_grp = -1, res_cells = 0;
+  // changes between adjacent root rows of every probe group's foreign key;
+  // a key whose runs average 4 rows or more gets its updates summed per run
+  // inside a warp
+  std::vector<unsigned long long> changes(rp.n_grp, 0);
+  std::vector<int> has_runs(rp.n_grp, 0);
+  if (rp.n_grp > 0 && Root.nrows > 1) {
+    unsigned long long* d = nullptr;
+    CUDA_TRY(c, cudaMalloc(&d, sizeof(unsigned long long) * rp.n_grp));
+    CUDA_TRY(c, cudaMemsetAsync(d, 0, sizeof(unsigned long long) * rp.n_grp, c->stream));
+    for (int q = 0; q < rp.n_grp; ++q) {
+      GroupH& g = P->groups[RR.groups[q]];
+      const RelationH& O = c->rels[g.owner];
+      CUDA_TRY(c, launch_key_changes(static_cast<const int32_t*>(O.cols[O.find(g.fk)].dptr()), O.nrows, d + q,
+                                     c->stream));
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(changes.data(), d, sizeof(unsigned long long) * rp.n_grp, cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    cudaFree(d);
+    for (int q = 0; q < rp.n_grp; ++q) {
+      has_runs[q] = (int64_t)(changes[q] + 1) * 4 <= Root.nrows;
+      if (P->unique_all && Root.nrows >= 2 * kResRun && (int64_t)(changes[q] + 1) * kResRun <= Root.nrows &&
+          (res_grp < 0 || changes[q] < changes[res_grp]))
+        res_grp = q;
+    }
+  }
+  if (res_grp >= 0) {
+    for (size_t a = 0; a < B.aggs.size(); ++a) {
+      if (cls[a].kind != 1 || !gplan[a].direct || !cls[a].mono.empty()) continue;
+      const AggH& ag = B.aggs[a];
+      int q_res = -1, n_in = 0;
+      int64_t n = 1;
+      for (size_t q = 0; q < ag.gb.size(); ++q) {
+        if (P->catword.at(ag.gb[q]).first == res_grp) {
+          q_res = (int)q;
+          ++n_in;
+        } else {
+          int col, r = owner_of(c, ag.gb[q], &col);
+          n *= c->rels[r].cols[col].dom;
+        }
+      }
+      if (n_in != 1 || n > kResTableMax || res_cells + n > kResBudget) continue;
+      gplan[a].res_off = res_cells;
+      gplan[a].res_q = q_res;
+      gplan[a].res_word = P->catword.at(ag.gb[q_res]).second;
+      gplan[a].res_n = (int)n;
+      res_cells += (int)n;
+    }
+    if (res_cells == 0) res_grp = -1;
+  }
+
   // ---- hot-cell cache: per CTA, the hottest (value, value) cells of every
   // pair-count table are 32-bit counters in shared memory; Zipf-skewed
   // categories otherwise serialise L2 atomics on a few addresses (a table's
@@ -996,7 +1059,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     // pair COUNT tables with w in {0, 1}: a CTA counts fewer than 2^32 rows
     for (size_t a = 0; a < B.aggs.size(); ++a) {
       if (cls[a].kind != 1 || !gplan[a].direct || B.aggs[a].gb.size() != 2) continue;
-      if (!cls[a].mono.empty() || !P->unique_all) continue;
+      if (!cls[a].mono.empty() || !P->unique_all || gplan[a].res_off >= 0) continue;
       if (cache_cells + kHotVals * kHotVals > kCacheBudget) break;
       for (auto& gname : B.aggs[a].gb) {
         const int rc = P->rowcat.at(gname);
@@ -1030,7 +1093,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   P->mp = mp;
   const int T = root_plain_tile_rows();
   P->n_tiles = (Root.nrows + T - 1) / T;
-  P->smem = root_plain_smem(mp, ncat, cache_cells);
+  P->smem = root_plain_smem(mp, ncat, cache_cells, res_cells);
   int cps = P->opts.ctas_per_sm > 0 ? P->opts.ctas_per_sm : (P->smem <= 110 * 1024 ? 2 : 1);
   P->grid = (int)std::max<int64_t>(1, std::min<int64_t>(P->n_tiles, (int64_t)c->num_sms * cps));
   CUDA_TRY(c, root_plain_prepare(mp, P->smem));
@@ -1041,7 +1104,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   if (use_tc) {
     P->tc = std::make_unique<GramTcPlan>();
     gram_tc_shape(m, Root.nrows, c->num_sms, P->opts.tile_rows, P->tc.get());
-    CUDA_TRY(c, gram_tc_configure(P->tc.get(), ncat, P->opts.ctas_per_sm, cache_cells));
+    CUDA_TRY(c, gram_tc_configure(P->tc.get(), ncat, P->opts.ctas_per_sm, cache_cells, res_cells));
     P->grid = P->tc->grid;
   }
   P->part_off = A.take((size_t)P->grid * mp * mp * 8);
@@ -1113,6 +1176,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     R.hist = P->at<unsigned long long>(rv_hist_off[q]);
     R.R = P->at<long long>(rv_R_off[q]);
     R.grp = q;
+    R.runs = has_runs[q];
     R.n_slot = (int)rv_slots[q].size();
     for (int s = 0; s < R.n_slot; ++s) {
       R.slot_z[s] = (int16_t)rv_slots[q][s];
@@ -1139,6 +1203,9 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   rp.hot_lut = P->at<int8_t>(hot_lut_off);
   rp.hot_h = kHotVals;
   rp.cache_cells = cache_cells;
+  rp.res_grp = res_grp < 0 ? 0 : res_grp;
+  rp.res_cells = res_cells;
+  rp.unit_w = P->unique_all ? 1 : 0;
   rp.cache_dst = P->at<long long*>(cache_dst_off);
   std::vector<RvTask> tasks;
   std::vector<DirectAgg> direct;
@@ -1150,15 +1217,22 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     if (gp.direct) {
       DirectAgg d{};
       d.n_gb = (int)ag.gb.size();
+      d.runs = 1;
       for (int q = 0; q < d.n_gb; ++q) {
         int col, r = owner_of(c, ag.gb[q], &col);
         d.cat[q] = P->rowcat.at(ag.gb[q]);
         d.dom[q] = c->rels[r].cols[col].dom;
+        const int g = P->catword.at(ag.gb[q]).first;  // -1: a root category
+        if (g < 0 || !has_runs[g]) d.runs = 0;
       }
       d.z = f.empty() ? -1 : P->zidx.at(f);
       d.scale = (float)gp.scale;
       d.out = P->at<long long>(gp.out_off);
       d.cache_off = gp.cache_off;
+      d.res_off = gp.res_off;
+      d.res_q = gp.res_q;
+      d.res_word = gp.res_word;
+      d.res_n = gp.res_n;
       if (gp.cache_off >= 0) {
         const auto& va = hot_vals.at(d.cat[0]);
         const auto& vb = hot_vals.at(d.cat[1]);
@@ -1192,6 +1266,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   P->direct = direct;
   rp.n_direct = (int)direct.size();
   rp.direct = P->at<DirectAgg>(P->direct_off);
+  for (int d = 0; d < rp.n_direct && d < kDirInline; ++d) rp.dir[d] = direct[d];
   rp.n_om = 0;
   std::vector<CorrTask> corr;
   for (auto& o : omega) {
@@ -1469,6 +1544,8 @@ lmf_status lmf_plan_info(lmf_ctx* c, int batch_id, lmf_plan_stats* info) {
   }
   info->root_rows = P->rootp.N;
   info->scratch_bytes = (int64_t)P->arena.size;
+  info->resident_group = P->rootp.res_cells > 0 ? P->rootp.res_grp : -1;
+  info->resident_cells = P->rootp.res_cells;
   return LMF_OK;
 }
 

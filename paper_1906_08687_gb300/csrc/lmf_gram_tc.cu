@@ -166,13 +166,13 @@ struct TcLayout {
   uint32_t z_off, c_off, cache_off, bar_off, slot_off, cred_off, total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int n_rowcat, int cache_cells) {
+__host__ __device__ inline TcLayout tc_layout(int n_rowcat, int cache_cells, int res_cells) {
   TcLayout L;
   L.z_off = kAStage + kBStage;
   L.c_off = L.z_off + kTcRows * kZld * 4;
   const uint32_t ncat = n_rowcat > 0 ? n_rowcat : 1;
   L.cache_off = (L.c_off + kTcRows * ncat * 4 + 15) & ~15u;
-  L.bar_off = (L.cache_off + static_cast<uint32_t>(cache_cells) * 4 + 15) & ~15u;
+  L.bar_off = (L.cache_off + static_cast<uint32_t>(cache_cells + res_cells) * 4 + 15) & ~15u;
   L.slot_off = L.bar_off + 16;
   L.cred_off = L.slot_off + 16;
   L.total = L.cred_off + 4 * 8;
@@ -182,9 +182,11 @@ __host__ __device__ inline TcLayout tc_layout(int n_rowcat, int cache_cells) {
 __global__ void __launch_bounds__(kTcThreads) k_root_tc(const __grid_constant__ RootParams p, int64_t n_tiles,
                                                          double* part) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const TcLayout L = tc_layout(p.n_rowcat, p.cache_cells);
+  const TcLayout L = tc_layout(p.n_rowcat, p.cache_cells, p.res_cells);
   unsigned char* sA = smem;
   uint32_t* cache = reinterpret_cast<uint32_t*>(smem + L.cache_off);
+  uint32_t* res_hist = cache + p.cache_cells;
+  long long res_key = -1;
   unsigned char* sB = smem + kAStage;
   float* Zs = reinterpret_cast<float*>(smem + L.z_off);
   int32_t* Cs = reinterpret_cast<int32_t*>(smem + L.c_off);
@@ -240,11 +242,15 @@ __global__ void __launch_bounds__(kTcThreads) k_root_tc(const __grid_constant__ 
   };
 
   int64_t it = 0;
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+  // one contiguous range of tiles per CTA: on a sorted root a CTA meets few keys
+  const int64_t t_end = (blockIdx.x + 1) * n_tiles / gridDim.x;
+  for (int64_t tile = blockIdx.x * n_tiles / gridDim.x; tile < t_end; ++tile, ++it) {
     const int buf = static_cast<int>(it & 1);
     float* zrow = Zs + tid * kZld;
     int32_t* crow = Cs + tid * ncat;
-    cnt_acc += root_row_pass<32>(p, tile * kTcRows + tid, zrow, crow, p.cache_cells ? cache : nullptr);
+    if (p.res_cells > 0) root_res_advance(p, tile * kTcRows, res_hist, res_key);
+    cnt_acc += root_row_pass<32>(p, tile * kTcRows + tid, zrow, kZld, crow, p.cache_cells ? cache : nullptr,
+                                 res_hist, res_key);
     if (it > 0) {  // the previous tile's MMAs read the operand stage
       const int64_t pi = it - 1;
       if (!mbar_wait(bar[pi & 1], static_cast<uint32_t>((pi >> 1) & 1))) ok = false;
@@ -273,6 +279,8 @@ __global__ void __launch_bounds__(kTcThreads) k_root_tc(const __grid_constant__ 
     drain(static_cast<int>(pi & 1));
   }
 
+  __syncthreads();
+  if (p.res_cells > 0) root_res_flush(p, res_hist, res_key);
   root_cache_flush(p, cache);
   if (warp < 3) {
     double* out = part + ((static_cast<int64_t>(blockIdx.x) * 3 + warp) * 32 + lane) * 32;
@@ -330,8 +338,8 @@ void gram_tc_alloc(GramTcPlan* tp, const std::function<size_t(size_t)>& take) {
   tp->part_off = take(static_cast<size_t>(tp->grid) * 3 * 1024 * sizeof(double));
 }
 
-cudaError_t gram_tc_configure(GramTcPlan* tp, int n_rowcat, int ctas_per_sm, int cache_cells) {
-  const TcLayout L = tc_layout(n_rowcat, cache_cells);
+cudaError_t gram_tc_configure(GramTcPlan* tp, int n_rowcat, int ctas_per_sm, int cache_cells, int res_cells) {
+  const TcLayout L = tc_layout(n_rowcat, cache_cells, res_cells);
   tp->smem = L.total;
   int cps = ctas_per_sm > 0 ? ctas_per_sm : (L.total <= 72 * 1024 ? 3 : (L.total <= 110 * 1024 ? 2 : 1));
   cps = cps > 4 ? 4 : cps;  // four CTAs of 128 tensor-memory columns fill an SM's 512

@@ -23,7 +23,7 @@ struct GramTcPlan {
 bool gram_tc_supported(int m);
 void gram_tc_shape(int m, int64_t N, int num_sms, int tile_rows, GramTcPlan* tp);
 // shared memory / grid for a row-category vector of n_rowcat entries
-cudaError_t gram_tc_configure(GramTcPlan* tp, int n_rowcat, int ctas_per_sm, int cache_cells);
+cudaError_t gram_tc_configure(GramTcPlan* tp, int n_rowcat, int ctas_per_sm, int cache_cells, int res_cells);
 void gram_tc_alloc(GramTcPlan* tp, const std::function<size_t(size_t)>& take);
 void gram_tc_finish(GramTcPlan* tp, RootParams& rp, char* base);
 cudaError_t gram_tc_launch(GramTcPlan* tp, const RootParams& rp, cudaStream_t s);

@@ -17,6 +17,7 @@ constexpr int kMaxZ = 64;            // length of z = [1, root features, view me
 constexpr int kMaxOwn = 48;          // own continuous columns of one relation
 constexpr int kMaxCat = 32;          // categorical words of one record / root row
 constexpr int kMaxQ = kMaxZ * (kMaxZ + 1) / 2;
+constexpr int kDirInline = 96;        // per-row tables whose descriptors ride in the kernel parameters
 
 // device status bits (OR-ed by kernels, read by lmf_sync)
 constexpr uint32_t kStatusCatRange = 1u;      // category outside [0, domain)
@@ -98,6 +99,7 @@ struct RevView {
   unsigned long long* hist;          // [K]
   long long* R;                      // [K][n_slot]
   int32_t grp;                       // root probe group
+  int32_t runs;                      // 1: its key comes in runs of equal values (sum them per warp)
   int32_t n_slot;
   int16_t slot_z[kMaxZ];             // z index of each slot
   float slot_scale[kMaxZ];           // fixed-point scale per slot (power of 2)
@@ -113,6 +115,14 @@ struct DirectAgg {
   float scale;
   long long* out;                    // [cells] fixed-point / counts
   int32_t cache_off;                 // pair tables: first cache cell of its hot x hot block, else -1
+  // resident-key form (COUNT tables with one category from the resident probe
+  // group): the CTA counts the rows of the current resident key in shared
+  // memory over the other categories' cells
+  int32_t res_off;                   // first shared counter, -1: not resident
+  int32_t res_q;                     // group-by position of the resident group's category
+  int32_t res_word;                  // that category's word in the resident group's record
+  int32_t res_n;                     // counters: product of the other positions' domains
+  int32_t runs;                      // 1: its cells come in runs of equal values (sum them per warp)
 };
 
 struct OmegaAcc {                    // SUM over root rows of w / cnt_e per key of e
@@ -139,7 +149,8 @@ struct RootParams {
   int32_t n_rv;
   RevView rv[kMaxGroups];
   int32_t n_direct;
-  const DirectAgg* direct;           // device array
+  DirectAgg dir[kDirInline];         // the first kDirInline per-row tables (constant bank)
+  const DirectAgg* direct;           // device array of all n_direct (read for d >= kDirInline)
   int32_t n_om;
   OmegaAcc om[kMaxGroups * 4];
   uint32_t* status;
@@ -150,6 +161,13 @@ struct RootParams {
   const int8_t* hot_lut;             // concatenated per-category value -> hot index, -1 cold
   int32_t hot_lut_off[kMaxCat];      // per row category: offset into hot_lut, -1 none
   long long* const* cache_dst;       // [cache_cells]: global cell each cache cell flushes to
+  // resident key: when the root is sorted on the foreign key of probe group
+  // res_grp (long runs of one key, the trie order of the scan in Sec. 3.5),
+  // every CTA scans one contiguous range of tiles and keeps the resident-form
+  // tables of the current key in res_cells shared 32-bit counters; 0: off
+  int32_t res_grp;
+  int32_t res_cells;
+  int32_t unit_w;                    // 1: every w is 0 or 1 (unique child keys)
 };
 
 // answering a grouped aggregate from a reverse view: loop over the group's keys
@@ -190,7 +208,7 @@ cudaError_t launch_view_general(const ViewArgs& a, cudaStream_t s);
 cudaError_t launch_view_finalize(const ViewFinalizeArgs& a, cudaStream_t s);
 cudaError_t launch_root_plain(const RootParams& p, int mp, int grid, int64_t n_tiles,
                               size_t smem, cudaStream_t s);
-size_t root_plain_smem(int mp, int n_rowcat, int cache_cells = 0);
+size_t root_plain_smem(int mp, int n_rowcat, int cache_cells = 0, int res_cells = 0);
 cudaError_t root_plain_prepare(int mp, size_t smem);
 int root_plain_tile_rows();
 cudaError_t launch_combine(const double* part, int grid, int mp, int m, const long long* cnt_part,
@@ -204,5 +222,7 @@ cudaError_t launch_out_map(const OutMap* maps, int n_maps, int64_t max_cells, co
 cudaError_t launch_colmaxabs(const Col* cols, int n, int64_t nrows, double* out, cudaStream_t s);
 cudaError_t launch_key_stats(const int32_t* key, int64_t n, unsigned int* hist, int K,
                              int* minmax, cudaStream_t s);
+// *out += number of adjacent unequal pairs of key[0, n) (*out zeroed by the caller)
+cudaError_t launch_key_changes(const int32_t* key, int64_t n, unsigned long long* out, cudaStream_t s);
 
 }  // namespace lmf

@@ -83,6 +83,25 @@ cudaError_t launch_key_stats(const int32_t* key, int64_t n, unsigned int* hist, 
   return cudaGetLastError();
 }
 
+// number of i in [1, n) with key[i] != key[i - 1]: one less than the runs of
+// equal keys
+__global__ void k_key_changes(const int32_t* key, int64_t n, unsigned long long* out) {
+  unsigned long long c = 0;
+  for (int64_t i = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    c += key[i] != key[i - 1];
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+cudaError_t launch_key_changes(const int32_t* key, int64_t n, unsigned long long* out, cudaStream_t s) {
+  if (n <= 1) return cudaSuccess;
+  int64_t gb = (n + 255) / 256;
+  int grid = (int)(gb < 2048 ? gb : 2048);
+  k_key_changes<<<grid, 256, 0, s>>>(key, n, out);
+  return cudaGetLastError();
+}
+
 __global__ void k_colmaxabs(const Col c, int64_t n, unsigned long long* out) {
   double m = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -267,6 +286,8 @@ __global__ void __launch_bounds__(256) k_root_plain(const __grid_constant__ Root
   float* Zb = Za + T * LD;
   int32_t* Cs = reinterpret_cast<int32_t*>(Zb + T * LD);
   uint32_t* cache = reinterpret_cast<uint32_t*>(Cs + T * (p.n_rowcat > 0 ? p.n_rowcat : 1));
+  uint32_t* res_hist = cache + p.cache_cells;
+  long long res_key = -1;
   const int tid = threadIdx.x;
   root_cache_zero(p, cache);
   __syncthreads();
@@ -283,13 +304,17 @@ __global__ void __launch_bounds__(256) k_root_plain(const __grid_constant__ Root
   for (int q = 0; q < 16; ++q) hi[q] = lo[q] = 0.f;
   long long cnt_acc = 0;
 
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  // one contiguous range of tiles per CTA: on a sorted root a CTA meets few keys
+  const int64_t t_end = (blockIdx.x + 1) * n_tiles / gridDim.x;
+  for (int64_t tile = blockIdx.x * n_tiles / gridDim.x; tile < t_end; ++tile) {
+    if (p.res_cells > 0) root_res_advance(p, tile * T, res_hist, res_key);
     // ---------------- phase 1: one row per thread
     {
       const int64_t row = tile * T + tid;
       float* zrow = Zb + tid * LD;
       int32_t* crow = Cs + tid * (p.n_rowcat > 0 ? p.n_rowcat : 1);
-      const long long w = root_row_pass<MP>(p, row, zrow, crow, p.cache_cells ? cache : nullptr);
+      const long long w =
+          root_row_pass<MP>(p, row, zrow, LD, crow, p.cache_cells ? cache : nullptr, res_hist, res_key);
       cnt_acc += w;
       // w * z for the left operand
       const float wf = static_cast<float>(w);
@@ -326,6 +351,7 @@ __global__ void __launch_bounds__(256) k_root_plain(const __grid_constant__ Root
     __syncthreads();
   }
 
+  if (p.res_cells > 0) root_res_flush(p, res_hist, res_key);
   root_cache_flush(p, cache);
   // ---------------- CTA reduction of the row groups, FP64 partial out
   double* red = reinterpret_cast<double*>(smem_raw);  // [NB * 16][RG]
@@ -360,10 +386,10 @@ __global__ void __launch_bounds__(256) k_root_plain(const __grid_constant__ Root
   }
 }
 
-size_t root_plain_smem(int mp, int n_rowcat, int cache_cells) {
+size_t root_plain_smem(int mp, int n_rowcat, int cache_cells, int res_cells) {
   size_t z = (size_t)2 * kPlainT * (mp + 4) * sizeof(float);
   size_t c = (size_t)kPlainT * (n_rowcat > 0 ? n_rowcat : 1) * sizeof(int32_t);
-  return z + c + (size_t)cache_cells * 4;
+  return z + c + (size_t)(cache_cells + res_cells) * 4;
 }
 int root_plain_tile_rows() { return kPlainT; }
 

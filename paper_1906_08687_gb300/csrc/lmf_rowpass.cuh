@@ -14,8 +14,17 @@ __device__ __forceinline__ float rp_load_f(const Col& c, int64_t i) {
   return c.dtype == 2 ? static_cast<float>(static_cast<const double*>(c.p)[i])
                       : static_cast<const float*>(c.p)[i];
 }
+// Reductions whose old value nobody reads: `red` carries no return value, so
+// the issuing warp never waits for the memory system to answer.
+__device__ __forceinline__ void rp_red_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 __device__ __forceinline__ void rp_add_ll(long long* p, long long v) {
-  atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+  rp_red_u64(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+}
+__device__ __forceinline__ void rp_red_shared_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))), "r"(v)
+               : "memory");
 }
 // exact fixed-point image of w * x (x * scale is a power-of-two scaling)
 __device__ __forceinline__ long long rp_fixp(long long w, float x, float scale) {
@@ -77,58 +86,258 @@ __device__ __forceinline__ long long root_row_z(const RootParams& p, int64_t row
   return w;
 }
 
-// grouped updates of one joining row (w != 0); cache (may be null) holds the
-// CTA's counters for the hot cells of pair-count tables
-__device__ __forceinline__ void root_row_grouped(const RootParams& p, int64_t row, const float* zrow,
-                                                 const int32_t* crow, long long w, uint32_t* cache) {
-  for (int r = 0; r < p.n_rv; ++r) {
-    const RevView& R = p.rv[r];
-    const int32_t fk = p.grp[R.grp].fk[row];
-    atomicAdd(R.hist + fk, static_cast<unsigned long long>(w));
-    long long* dst = R.R + (int64_t)fk * R.n_slot;
-    for (int s = 0; s < R.n_slot; ++s) rp_add_ll(dst + s, rp_fixp(w, zrow[R.slot_z[s]], R.slot_scale[s]));
+// Runs of equal update targets among the 32 consecutive rows of a warp.  On a
+// fact relation sorted by its join attributes (the scan order of Sec. 3.5) the
+// rows of one key are contiguous, so a run's updates are summed with shuffles
+// and only its first lane issues the atomics.  Integer sums are exact in any
+// order, so this changes the number of atomics, never a result.
+constexpr unsigned kFullWarp = 0xffffffffu;
+constexpr int kRunMaxHeads = 24;  // fewer runs than this in a warp: sum them first
+
+struct WarpRuns {
+  bool head;       // first lane of its run
+  bool sum;        // warp-uniform: the runs are summed before the atomics
+  int end;         // one past the last lane of this lane's run
+  unsigned heads;  // lanes that start a run
+};
+
+__device__ __forceinline__ WarpRuns warp_runs(long long key) {
+  const int lane = threadIdx.x & 31;
+  const long long prev = __shfl_up_sync(kFullWarp, key, 1);
+  WarpRuns r;
+  r.head = lane == 0 || key != prev;
+  const unsigned hm = __ballot_sync(kFullWarp, r.head);
+  r.heads = hm;
+  r.sum = __popc(hm) <= kRunMaxHeads;
+  const unsigned above = hm & ~((2u << lane) - 1u);
+  r.end = above ? __ffs(above) - 1 : 32;
+  return r;
+}
+
+// total of v over lanes [lane, end) of the run (complete in the run's head)
+__device__ __forceinline__ long long warp_run_sum(const WarpRuns& r, long long v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long o = __shfl_down_sync(kFullWarp, v, d);
+    if (lane + d < r.end) v += o;
   }
+  return v;
+}
+
+__device__ __forceinline__ void rp_direct_add(const RootParams& p, const DirectAgg& A, int64_t cell,
+                                              const int32_t* crow, long long v, uint32_t* cache) {
+  if (cache && A.cache_off >= 0) {  // a pair-count table: 32-bit counter cells
+    const int ha = __ldg(p.hot_lut + p.hot_lut_off[A.cat[0]] + crow[A.cat[0]]);
+    const int hb = __ldg(p.hot_lut + p.hot_lut_off[A.cat[1]] + crow[A.cat[1]]);
+    if (ha >= 0 && hb >= 0) {
+      rp_red_shared_u32(cache + A.cache_off + ha * p.hot_h + hb, static_cast<uint32_t>(v));
+      return;
+    }
+  }
+  rp_add_ll(A.out + cell, v);
+}
+
+// ---- resident key ----------------------------------------------------------
+// A root sorted on its join attributes (Sec. 3.5: the scan sees the relation as
+// a trie, first attribute outermost) holds one value of its first attribute
+// over long runs.  A COUNT table with one category from that attribute's probe
+// group then gets, for the whole run, one fixed value at that position: the CTA
+// counts the run's rows in shared memory over the other positions' cells (the
+// table's row for the current key) and adds them to the table when the key
+// changes.  Counters are 32-bit: a CTA holds a key for fewer than 2^32 rows.
+
+// a row's counter within a resident table: the other positions, last fastest
+__device__ __forceinline__ int res_index(const DirectAgg& A, const int32_t* crow) {
+  int idx = 0;
+  for (int q = 0; q < A.n_gb; ++q)
+    if (q != A.res_q) idx = idx * A.dom[q] + crow[A.cat[q]];
+  return idx;
+}
+
+// adds the counters of resident key k to their tables and clears them; every
+// thread of the CTA calls this
+__device__ __forceinline__ void root_res_flush(const RootParams& p, uint32_t* hist, long long k) {
+  if (k < 0) return;  // no row counted under "no key"
+  const GroupDesc& G = p.grp[p.res_grp];
   for (int d = 0; d < p.n_direct; ++d) {
-    const DirectAgg& A = p.direct[d];
-    const long long v = A.z < 0 ? w : rp_fixp(w, zrow[A.z], A.scale);
-    if (cache && A.cache_off >= 0) {  // a pair-count table: 32-bit counter cells
-      const int ha = __ldg(p.hot_lut + p.hot_lut_off[A.cat[0]] + crow[A.cat[0]]);
-      const int hb = __ldg(p.hot_lut + p.hot_lut_off[A.cat[1]] + crow[A.cat[1]]);
-      if (ha >= 0 && hb >= 0) {
-        atomicAdd(cache + A.cache_off + ha * p.hot_h + hb, static_cast<uint32_t>(v));
-        continue;
+    const DirectAgg& A = d < kDirInline ? p.dir[d] : p.direct[d];
+    if (A.res_off < 0) continue;
+    const int32_t a = static_cast<int32_t>(G.rec[k * G.stride + A.res_word]);
+    for (int i = threadIdx.x; i < A.res_n; i += blockDim.x) {
+      const uint32_t v = hist[A.res_off + i];
+      if (v == 0u) continue;
+      hist[A.res_off + i] = 0u;
+      int rem = i;
+      int64_t cell = 0, mult = 1;
+      for (int q = A.n_gb - 1; q >= 0; --q) {
+        int val = a;
+        if (q != A.res_q) {
+          val = rem % A.dom[q];
+          rem /= A.dom[q];
+        }
+        cell += static_cast<int64_t>(val) * mult;
+        mult *= A.dom[q];
+      }
+      rp_red_u64(reinterpret_cast<unsigned long long*>(A.out + cell), v);
+    }
+  }
+}
+
+// at the start of a tile: make the key of the tile's first row resident,
+// flushing the previous one; every thread of the CTA calls this and holds the
+// same key
+__device__ __forceinline__ void root_res_advance(const RootParams& p, int64_t row0, uint32_t* hist,
+                                                 long long& key) {
+  long long nk = -1;
+  if (row0 < p.N) {
+    const GroupDesc& G = p.grp[p.res_grp];
+    const int32_t f = G.fk[row0];
+    nk = (f >= 0 && f < G.K) ? f : -1;
+  }
+  if (nk == key) return;
+  __syncthreads();  // the counts of earlier tiles are in
+  root_res_flush(p, hist, key);
+  __syncthreads();  // cleared before the next tile counts
+  key = nk;
+}
+
+// one per-row table for the warp's rows (every lane calls this; fres is the
+// row's resident-group key, -2 when no key is resident or the row is dead)
+__device__ __forceinline__ void root_direct_one(const RootParams& p, const DirectAgg& A, int64_t row,
+                                                const float* zrow, const int32_t* crow, long long w,
+                                                uint32_t* cache, uint32_t* res_hist, long long res_key,
+                                                long long fres) {
+  const bool live = w != 0;
+  if (A.res_off >= 0 && res_key >= 0) {  // resident form (warp-uniform branch)
+    if (!live) return;
+    if (fres == res_key) {
+      rp_red_shared_u32(res_hist + A.res_off + res_index(A, crow), static_cast<uint32_t>(w));
+    } else {
+      int64_t cell = 0;
+      for (int k = 0; k < A.n_gb; ++k) cell = cell * A.dom[k] + crow[A.cat[k]];
+      rp_direct_add(p, A, cell, crow, w, cache);
+    }
+    return;
+  }
+  int64_t cell = -1;
+  if (live) {
+    cell = 0;
+    for (int k = 0; k < A.n_gb; ++k) cell = cell * A.dom[k] + crow[A.cat[k]];
+  }
+  const long long v = live ? (A.z < 0 ? w : rp_fixp(w, zrow[A.z], A.scale)) : 0ll;
+  if (!A.runs) {
+    if (live) rp_direct_add(p, A, cell, crow, v, cache);
+    return;
+  }
+  const WarpRuns q = warp_runs(cell);  // warp-uniform: A.runs is
+  if (!q.sum) {
+    if (live) rp_direct_add(p, A, cell, crow, v, cache);
+    return;
+  }
+  const long long t = warp_run_sum(q, v);
+  if (q.head && live) rp_direct_add(p, A, cell, crow, t, cache);
+}
+
+// Reverse view R for the warp's 32 rows, slot-parallel: lane s sums slot s
+// over the rows of each run of equal keys and issues one reduction per run, so
+// one instruction updates a key's consecutive slots.  zw: the warp's z rows,
+// ldz floats apart (zero for dead rows); fk: this lane's key, -1 when dead.
+__device__ __forceinline__ void root_rv_slots(const RootParams& p, const RevView& R, long long fk, long long w,
+                                              const float* zw, int ldz) {
+  const int lane = threadIdx.x & 31;
+  const WarpRuns q = warp_runs(fk);
+  // the key's join count: one reduction from the head of every run
+  if (p.unit_w) {
+    const unsigned live = __ballot_sync(kFullWarp, w != 0);
+    if (q.head && fk >= 0) {
+      const unsigned run = (q.end == 32 ? 0xffffffffu : ((1u << q.end) - 1u)) & ~((1u << lane) - 1u);
+      rp_red_u64(R.hist + fk, static_cast<unsigned long long>(__popc(live & run)));
+    }
+  } else {
+    const long long h = warp_run_sum(q, w);
+    if (q.head && fk >= 0 && h != 0) rp_red_u64(R.hist + fk, static_cast<unsigned long long>(h));
+  }
+  if (R.n_slot == 0) return;
+  for (int s0 = 0; s0 < R.n_slot; s0 += 32) {
+    const int s = s0 + lane;
+    const bool slot = s < R.n_slot;
+    const int zi = slot ? R.slot_z[s] : 0;
+    const float sc = slot ? R.slot_scale[s] : 0.f;
+    long long acc = 0;
+#pragma unroll 4
+    for (int j = 0; j < 32; ++j) {
+      if (p.unit_w) {  // w is 0 or 1 and z is zero for dead rows
+        acc += __float2ll_rn(zw[j * ldz + zi] * sc);
+      } else {
+        acc += rp_fixp(__shfl_sync(kFullWarp, w, j), zw[j * ldz + zi], sc);
+      }
+      if (j == 31 || ((q.heads >> (j + 1)) & 1u)) {  // row j ends a run (warp-uniform)
+        const long long kj = __shfl_sync(kFullWarp, fk, j);
+        if (slot && kj >= 0 && acc != 0) rp_add_ll(R.R + kj * R.n_slot + s, acc);
+        acc = 0;
       }
     }
-    int64_t cell = 0;
-    for (int q = 0; q < A.n_gb; ++q) cell = cell * A.dom[q] + crow[A.cat[q]];
-    rp_add_ll(A.out + cell, v);
   }
+}
+
+// Grouped updates of the warp's 32 rows; every lane of the warp calls this,
+// w == 0 marks a row that does not join (or lies past the relation's end).
+// cache (may be null) holds the CTA's counters for the hot cells of
+// pair-count tables, res_hist those of the resident key res_key (-1: none).
+__device__ __forceinline__ void root_row_grouped(const RootParams& p, int64_t row, const float* zrow, int ldz,
+                                                 const int32_t* crow, long long w, uint32_t* cache,
+                                                 uint32_t* res_hist, long long res_key) {
+  const bool live = w != 0;
+  const long long fres = (live && res_key >= 0) ? static_cast<long long>(p.grp[p.res_grp].fk[row]) : -2ll;
+  for (int r = 0; r < p.n_rv; ++r) {
+    const RevView& R = p.rv[r];
+    const long long fk = live ? static_cast<long long>(p.grp[R.grp].fk[row]) : -1ll;
+    if (R.runs) {  // keys in runs: slot-parallel sums per run (warp-uniform branch)
+      root_rv_slots(p, R, fk, w, zrow - (threadIdx.x & 31) * ldz, ldz);
+      continue;
+    }
+    if (live) {
+      long long* dst = R.R + fk * R.n_slot;
+      rp_red_u64(R.hist + fk, static_cast<unsigned long long>(w));
+      for (int s = 0; s < R.n_slot; ++s) rp_add_ll(dst + s, rp_fixp(w, zrow[R.slot_z[s]], R.slot_scale[s]));
+    }
+  }
+  const int n_inline = p.n_direct < kDirInline ? p.n_direct : kDirInline;
+  for (int d = 0; d < n_inline; ++d) root_direct_one(p, p.dir[d], row, zrow, crow, w, cache, res_hist, res_key, fres);
+  for (int d = kDirInline; d < p.n_direct; ++d)
+    root_direct_one(p, p.direct[d], row, zrow, crow, w, cache, res_hist, res_key, fres);
+  if (!live) return;
   for (int o = 0; o < p.n_om; ++o) {
     const OmegaAcc& O = p.om[o];
     const GroupDesc& G = p.grp[O.grp];
     const int32_t fk = G.fk[row];
     const long long ce = static_cast<long long>(G.rec[(int64_t)fk * G.stride + O.cnt_word]);
-    atomicAdd(O.omega + fk, static_cast<unsigned long long>(w / ce));
+    rp_red_u64(O.omega + fk, static_cast<unsigned long long>(w / ce));
   }
 }
 
-// the CTA's cache of 32-bit counters: zero at start, flush to the global
-// int64 cells at the end
+// the CTA's cache of 32-bit counters (hot cells, then the resident-key
+// counters): zero at start, flush to the global int64 cells at the end
 __device__ __forceinline__ void root_cache_zero(const RootParams& p, uint32_t* cache) {
-  for (int i = threadIdx.x; i < p.cache_cells; i += blockDim.x) cache[i] = 0u;
+  const int n = p.cache_cells + p.res_cells;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) cache[i] = 0u;
 }
 __device__ __forceinline__ void root_cache_flush(const RootParams& p, const uint32_t* cache) {
   for (int i = threadIdx.x; i < p.cache_cells; i += blockDim.x) {
     const unsigned long long v = cache[i];
-    if (v) atomicAdd(reinterpret_cast<unsigned long long*>(p.cache_dst[i]), v);
+    if (v) rp_red_u64(reinterpret_cast<unsigned long long*>(p.cache_dst[i]), v);
   }
 }
 
+// every lane of the warp calls this (root_row_grouped is warp-cooperative)
 template <int MP>
-__device__ __forceinline__ long long root_row_pass(const RootParams& p, int64_t row, float* zrow,
-                                                   int32_t* crow, uint32_t* cache) {
+__device__ __forceinline__ long long root_row_pass(const RootParams& p, int64_t row, float* zrow, int ldz,
+                                                   int32_t* crow, uint32_t* cache, uint32_t* res_hist,
+                                                   long long res_key) {
   const long long w = root_row_z<MP>(p, row, zrow, crow);
-  if (w != 0) root_row_grouped(p, row, zrow, crow, w, cache);
+  __syncwarp();  // the warp's z rows are in shared memory for the slot-parallel sums
+  root_row_grouped(p, row, zrow, ldz, crow, w, cache, res_hist, res_key);
   return w;
 }
 

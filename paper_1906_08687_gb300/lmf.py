@@ -67,7 +67,8 @@ class lmf_plan_stats(ctypes.Structure):
                 ('tree_slices', ctypes.c_int32), ('tree_split_w', ctypes.c_int32),
                 ('tree_node_w', ctypes.c_int32), ('tree_ctas_per_sm', ctypes.c_int32),
                 ('tree_chunk', ctypes.c_int32),
-                ('root_rows', ctypes.c_int64), ('scratch_bytes', ctypes.c_int64)]
+                ('root_rows', ctypes.c_int64), ('scratch_bytes', ctypes.c_int64),
+                ('resident_group', ctypes.c_int32), ('resident_cells', ctypes.c_int32)]
 
 
 # every symbol include/lmf.h declares, with its ctypes signature

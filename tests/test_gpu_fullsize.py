@@ -17,14 +17,9 @@ def _sample(n, k, seed):
     return sorted(set([0] + rng.choice(n, size=min(k, n), replace=False).tolist()))
 
 
-@pytest.fixture(scope='module')
-def snowflake20m():
-    return config2(20_000_000)
-
-
-@pytest.mark.parametrize('precision', [0, 1])
-def test_config2_full_size(snowflake20m, precision):
-    sch, batch = snowflake20m
+@pytest.mark.parametrize('precision,order', [(0, 'sorted'), (1, 'sorted'), (1, 'random')])
+def test_config2_full_size(precision, order):
+    sch, batch = config2(20_000_000, fact_order=order)
     got, info, eng = run_engine(sch, batch, precision=precision, batching=1)
     assert info['precision'] == precision and info['root_rows'] == 20_000_000
     idx = _sample(len(batch), 64, 7 + precision)
@@ -45,9 +40,10 @@ def test_config3_full_size():
     eng.close()
 
 
-def test_config4_reduced_exact():
+@pytest.mark.parametrize('order', ['sorted', 'random'])
+def test_config4_reduced_exact(order):
     """Chow-Liu pair counts, marginals and the data cube: bit-exact counts."""
-    sch, batch = config4(400_000)
+    sch, batch = config4(400_000, fact_order=order)
     got, info, eng = run_engine(sch, batch, precision=1, batching=1)
     want = oracle.evaluate(sch, batch)
     fails, stats = compare(got, want)

@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 from oracle import oracle
-from workloads import Agg, config1, config2, covar_batch, grouped_batch, tiny_schema
+from workloads import (Agg, Column, Relation, Schema, config1, config2, covar_batch, grouped_batch,
+                       pair_count_batch, sort_by_join_attributes, tiny_schema)
 
 from lmf_testlib import ARITH_FLOOR, compare, run_engine
 
@@ -42,8 +43,9 @@ def test_config1_ragged_sizes():
 
 
 @pytest.mark.parametrize('precision', [PLAIN, SPLIT])
-def test_config2_snowflake_reduced(precision):
-    sch, batch = config2(300_007)
+@pytest.mark.parametrize('order', ['sorted', 'random'])
+def test_config2_snowflake_reduced(precision, order):
+    sch, batch = config2(300_007, fact_order=order)
     _, info, stats = _check(sch, batch, precision, GRAPH, floor=ARITH_FLOOR)
     assert info['precision'] == precision
     assert info['n_grouped_aggs'] == 10 * 31 + 45
@@ -87,3 +89,79 @@ def test_unsupported_shapes_fail_cleanly():
     with pytest.raises(LmfError) as e:
         run_engine(sch, bad)
     assert e.value.status == -10
+
+
+def _runs_schema(n, seed, order, run_hi=91):
+    """A star whose fact keys come in runs of 1..run_hi-1 equal values (with
+    dangling keys inside and between runs), so warps see one run, many runs,
+    runs that cross warp and tile edges, and a ragged tail; sorted on the join
+    attributes, or shuffled."""
+    rng = np.random.default_rng(seed)
+    k1 = np.repeat(rng.integers(0, 41, size=n), rng.integers(1, run_hi, size=n))[:n].astype(np.int32)
+    k2 = np.repeat(rng.integers(0, 8, size=n), rng.integers(1, 6, size=n))[:n].astype(np.int32)
+    F = Relation('F', [Column('k1', 'key', k1), Column('k2', 'key', k2),
+                       Column('x0', 'cont', rng.standard_normal(n).astype(np.float32)),
+                       Column('x1', 'cont', (rng.integers(-4, 5, n) + 0.25).astype(np.float32)),
+                       Column('fc', 'cat', rng.integers(0, 3, n).astype(np.int32), 3)])
+    if order == 'sorted':
+        F = sort_by_join_attributes(F, ['k1', 'k2'])
+    else:  # the same rows shuffled: no runs left
+        perm = np.random.default_rng(seed + 1).permutation(n)
+        F = Relation('F', [Column(c.name, c.role, c.data[perm], c.cat_domain) for c in F.columns])
+    D1 = Relation('D1', [Column('k1', 'key', np.arange(40, dtype=np.int32)),   # key 40 dangles
+                         Column('d1_x', 'cont', rng.standard_normal(40).astype(np.float32)),
+                         Column('d1_c', 'cat', rng.integers(0, 5, 40).astype(np.int32), 5)])
+    D2 = Relation('D2', [Column('k2', 'key', np.arange(8, dtype=np.int32)),
+                         Column('d2_c', 'cat', rng.integers(0, 4, 8).astype(np.int32), 4)])
+    sch = Schema([F, D1, D2], [('F', 'D1', 'k1'), ('F', 'D2', 'k2')], 'F')
+    feats, cats = ['x0', 'x1', 'd1_x'], ['fc', 'd1_c', 'd2_c']
+    return sch, covar_batch(feats) + grouped_batch(cats, feats) + pair_count_batch(cats)
+
+
+@pytest.mark.parametrize('n', [1, 31, 33, 4099, 70_001])
+def test_runs_of_equal_keys(n):
+    """Runs of equal keys are summed inside a warp before the atomics: parity
+    with the oracle, and grouped outputs (exact integer / fixed-point sums) are
+    bit-identical whatever the row order."""
+    sch_s, batch = _runs_schema(n, 17 + n, 'sorted')
+    sch_r, _ = _runs_schema(n, 17 + n, 'random')
+    got_s, info, _ = _check(sch_s, batch, SPLIT, GRAPH, floor=ARITH_FLOOR)
+    got_r, _, _ = _check(sch_r, batch, PLAIN, SINGLE, floor=ARITH_FLOOR)
+    grouped = [i for i, a in enumerate(batch) if a.group_by]
+    assert info['n_grouped_aggs'] == len(grouped)
+    for i in grouped:
+        assert np.array_equal(got_s[i], got_r[i]), batch[i]
+
+
+@pytest.mark.parametrize('n', [5000, 70_001, 300_001])
+@pytest.mark.parametrize('precision', [PLAIN, SPLIT])
+def test_resident_key(n, precision):
+    """Runs of 300..4000 rows of one foreign key: the key is held per CTA and
+    the pair tables with one of its categories count in shared memory.  Parity
+    with the oracle; bit-identical grouped outputs against the same rows in
+    random order (where no key is resident)."""
+    sch_s, batch = _runs_schema(n, 29 + n, 'sorted', run_hi=4001)
+    sch_r, _ = _runs_schema(n, 29 + n, 'random', run_hi=4001)
+    got_s, info_s, _ = _check(sch_s, batch, precision, GRAPH, floor=ARITH_FLOOR)
+    got_r, info_r, _ = _check(sch_r, batch, precision, SINGLE, floor=ARITH_FLOOR)
+    assert info_s['resident_group'] >= 0 and info_s['resident_cells'] > 0
+    assert info_r['resident_group'] == -1
+    for i, a in enumerate(batch):
+        if a.group_by:
+            assert np.array_equal(got_s[i], got_r[i]), batch[i]
+
+
+def test_config2_resident_key_engaged():
+    """The sorted snowflake holds its first sort attribute (k3, 1000 keys) per
+    CTA once its runs are long enough; pair counts stay exact."""
+    sch, batch = config2(2_000_000, fact_order='sorted')
+    got, info, eng = run_engine(sch, batch, precision=SPLIT, batching=GRAPH)
+    assert info['resident_group'] >= 0 and info['resident_cells'] > 0
+    eng.close()
+    pick = [i for i, a in enumerate(batch) if len(a.group_by) == 2] + [0, 1, 500, 700]
+    fails, stats = compare([got[i] for i in pick], oracle.evaluate(sch, [batch[i] for i in pick]))
+    assert not fails, (fails[:3], stats)
+    sch, batch = config2(2_000_000, fact_order='random')
+    got, info, eng = run_engine(sch, batch, precision=SPLIT, batching=GRAPH)
+    assert info['resident_group'] == -1 and info['resident_cells'] == 0
+    eng.close()

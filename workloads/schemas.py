@@ -93,6 +93,21 @@ def _rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.Philox(seed))
 
 
+def sort_by_join_attributes(rel: Relation, keys: Sequence[str]) -> Relation:
+    """The relation with its rows in the scan order of Sec. 3.5: sorted on its
+    join attributes, the attribute with the fewest distinct values first (ties
+    keep the given order).  The paper's experiments get every relation sorted
+    by its join attributes (App. B).  Same rows, so every aggregate keeps its
+    value; only the row order changes."""
+    if rel.nrows == 0 or not keys:
+        return rel
+    ndist = [len(np.unique(rel.col(k).data)) for k in keys]
+    order = [k for _, _, k in sorted(zip(ndist, range(len(keys)), keys))]
+    perm = np.lexsort([rel.col(k).data for k in reversed(order)])
+    return Relation(rel.name, [dataclasses.replace(c, data=np.ascontiguousarray(c.data[perm]))
+                               for c in rel.columns])
+
+
 def zipf_keys(rng: np.random.Generator, n: int, k: int, s: float) -> np.ndarray:
     """n draws over key ids 0..k-1 with P(rank i) ~ i^-s (i = 1..k); ranks are
     mapped to key ids by a seeded random permutation.  s = 0 is uniform."""
@@ -177,13 +192,22 @@ def cube_batch(dims: Sequence[str]) -> List[Agg]:
 # ----------------------------------------------------------------------------
 # config 1: star schema, 66 aggregates
 # ----------------------------------------------------------------------------
-def config1(n_fact: int = 200_000, seed: Optional[int] = None) -> Tuple[Schema, List[Agg]]:
+def _check_order(fact_order: str) -> None:
+    if fact_order not in ('sorted', 'random'):
+        raise ValueError(f"fact_order must be 'sorted' or 'random', not {fact_order!r}")
+
+
+def config1(n_fact: int = 200_000, seed: Optional[int] = None,
+            fact_order: str = 'sorted') -> Tuple[Schema, List[Agg]]:
+    _check_order(fact_order)
     rng = _rng(SEED_BASE + 1 if seed is None else seed)
     ks, kt = 1000, 500
     R = Relation('R', [
         Column('k1', 'key', zipf_keys(rng, n_fact, ks, 0.0)),
         Column('k2', 'key', zipf_keys(rng, n_fact, kt, 0.0)),
     ] + [Column(f'r{i}', 'cont', rng.standard_normal(n_fact)) for i in range(3)])
+    if fact_order == 'sorted':
+        R = sort_by_join_attributes(R, ['k1', 'k2'])
     S = Relation('S', [Column('k1', 'key', np.arange(ks, dtype=np.int32))] +
                  [Column(f's{i}', 'cont', rng.standard_normal(ks)) for i in range(4)])
     T = Relation('T', [Column('k2', 'key', np.arange(kt, dtype=np.int32))] +
@@ -209,7 +233,8 @@ _SNOW = [  # relation, key, K, parent, fk-on-parent
 
 
 def _snowflake(rng, n_fact, n_fact_feat, dim_feat, dim_cat, fk_s, cat_s, cat_lo,
-               cat_hi, label=False, feat_dtype=np.float32):
+               cat_hi, label=False, feat_dtype=np.float32, fact_order='sorted'):
+    _check_order(fact_order)
     feats: List[str] = []
     cats: List[str] = []
     gidx = 0
@@ -224,6 +249,8 @@ def _snowflake(rng, n_fact, n_fact_feat, dim_feat, dim_cat, fk_s, cat_s, cat_lo,
     if label:
         fact_cols.append(Column('y', 'cont', _feature(rng, n_fact, 0, feat_dtype)))
     rels = {'F': Relation('F', fact_cols)}
+    if fact_order == 'sorted':
+        rels['F'] = sort_by_join_attributes(rels['F'], [c.name for c in fact_cols if c.role == 'key'])
     edges = []
     for rel, key, K, parent in _SNOW:
         cols = [Column(key, 'key', np.arange(K, dtype=np.int32))]
@@ -245,13 +272,14 @@ def _snowflake(rng, n_fact, n_fact_feat, dim_feat, dim_cat, fk_s, cat_s, cat_lo,
     return Schema([rels[r] for r in order], edges, 'F'), feats, cats
 
 
-def config2(n_fact: int = 20_000_000, seed: Optional[int] = None) -> Tuple[Schema, List[Agg]]:
+def config2(n_fact: int = 20_000_000, seed: Optional[int] = None,
+            fact_order: str = 'sorted') -> Tuple[Schema, List[Agg]]:
     rng = _rng(SEED_BASE + 2 if seed is None else seed)
     sch, feats, cats = _snowflake(
         rng, n_fact, 8,
         dim_feat={'D1': 6, 'Sub1': 4, 'Sub2': 2, 'D2': 5, 'D3': 3, 'D4': 2},
         dim_cat={'D1': 2, 'Sub1': 1, 'Sub2': 1, 'D2': 3, 'D3': 2, 'D4': 1},
-        fk_s=0.8, cat_s=1.1, cat_lo=5, cat_hi=1000)
+        fk_s=0.8, cat_s=1.1, cat_lo=5, cat_hi=1000, fact_order=fact_order)
     sch.meta.update(name=f'snowflake-{n_fact}', features=feats, cats=cats)
     batch = covar_batch(feats) + grouped_batch(cats, feats) + pair_count_batch(cats)
     return sch, batch
@@ -276,12 +304,13 @@ def _joined_sample(sch: Schema, attr: str, rows: np.ndarray) -> np.ndarray:
 
 
 def config3(n_fact: int = 10_000_000, seed: Optional[int] = None, n_nodes_depth: int = 6,
-            n_thresholds: int = 32, sample_rows: int = 1_000_000) -> Tuple[Schema, List[Agg]]:
+            n_thresholds: int = 32, sample_rows: int = 1_000_000,
+            fact_order: str = 'sorted') -> Tuple[Schema, List[Agg]]:
     rng = _rng(SEED_BASE + 3 if seed is None else seed)
     sch, feats, _ = _snowflake(
         rng, n_fact, 6,
         dim_feat={'D1': 4, 'Sub1': 2, 'Sub2': 1, 'D2': 3, 'D3': 2, 'D4': 2},
-        dim_cat={}, fk_s=0.8, cat_s=1.1, cat_lo=5, cat_hi=1000, label=True)
+        dim_cat={}, fk_s=0.8, cat_s=1.1, cat_lo=5, cat_hi=1000, label=True, fact_order=fact_order)
     # per feature: thresholds at the empirical j/(T+1) quantiles of a sample
     rows = rng.integers(0, n_fact, size=min(sample_rows, n_fact))
     thr = {}
@@ -314,13 +343,17 @@ def config3(n_fact: int = 10_000_000, seed: Optional[int] = None, n_nodes_depth:
 # ----------------------------------------------------------------------------
 # config 4: Chow-Liu pair counts + data cube
 # ----------------------------------------------------------------------------
-def config4(n_fact: int = 50_000_000, seed: Optional[int] = None) -> Tuple[Schema, List[Agg]]:
+def config4(n_fact: int = 50_000_000, seed: Optional[int] = None,
+            fact_order: str = 'sorted') -> Tuple[Schema, List[Agg]]:
+    _check_order(fact_order)
     rng = _rng(SEED_BASE + 4 if seed is None else seed)
     Ks = [200, 1000, 5000, 20000]
     ncat = [7, 7, 8, 8]
     cube_dom = {0: 50, 1: 20, 2: 10}
     fact = Relation('F', [Column(f'k{j + 1}', 'key', zipf_keys(rng, n_fact, Ks[j], 1.0))
                           for j in range(4)])
+    if fact_order == 'sorted':
+        fact = sort_by_join_attributes(fact, [f'k{j + 1}' for j in range(4)])
     rels = [fact]
     edges = []
     cats: List[str] = []
