@@ -111,8 +111,14 @@ typedef struct {
   int32_t root_rel;       /* LMF_ROOT_EXPLICIT: relation id of the root */
   int32_t no_merge;       /* 1: one record array per child view instead of one per
                              parent key (turns off merge case (1) of Sec. 3.4) */
-  int32_t reserved;
+  int32_t flags;          /* LMF_PLAN_* bits */
 } lmf_plan_opts;
+
+/* lmf_plan_opts.flags: the plain root scan is compiled at plan time with the
+   plan's layout as constants (the compilation step of Sec. 1.2 / App. C, done
+   with NVRTC) unless this bit is set or NVRTC cannot be loaded; the
+   interpreted kernel (same arithmetic, same results) runs otherwise. */
+#define LMF_PLAN_NO_JIT 1
 
 /* Statistics of a plan, for reporting (lmf_plan_info). */
 typedef struct {
@@ -140,6 +146,8 @@ typedef struct {
   int32_t resident_group;     /* probe group whose key is held per CTA (a root sorted on
                                  that foreign key), -1: none */
   int32_t resident_cells;     /* shared-memory counters of the resident-key tables */
+  int32_t jit;                /* 1: the root scan runs a kernel compiled for this plan */
+  int32_t reserved_stats;
 } lmf_plan_stats;
 
 /*

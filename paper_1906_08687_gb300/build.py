@@ -20,7 +20,10 @@ LIB = os.path.join(OUT_DIR, 'liblmf.so')
 
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 FLAGS = ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC', '--expt-relaxed-constexpr',
-         '-I', INCLUDE, '-I', CSRC]
+         '-I', INCLUDE, '-I', CSRC, '-I', OUT_DIR]
+# device headers the plan-time compiler (NVRTC) gets as in-memory sources
+JIT_HEADERS = ['lmf_internal.h', 'lmf_rowpass.cuh', 'lmf_root_plain.cuh']
+JIT_INC = os.path.join(OUT_DIR, 'lmf_jit_headers.inc')
 
 
 def _nvcc() -> str:
@@ -35,11 +38,31 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
+def write_jit_headers() -> None:
+    """Embed the device headers as raw string literals for lmf_jit.cu."""
+    names, texts = [], []
+    for h in JIT_HEADERS:
+        with open(os.path.join(CSRC, h)) as f:
+            t = f.read()
+        if ')LMFJIT"' in t:
+            raise RuntimeError(f'{h} contains the raw-string delimiter')
+        names.append(f'"{h}"')
+        texts.append('R"LMFJIT(' + t + ')LMFJIT"')
+    body = ('// generated by build.py from ' + ', '.join(JIT_HEADERS) + '\n'
+            'static const char* const kJitHeaderNames[] = {' + ', '.join(names) + '};\n'
+            'static const char* const kJitHeaderSrc[] = {\n' + ',\n'.join(texts) + '};\n')
+    old = open(JIT_INC).read() if os.path.exists(JIT_INC) else None
+    if old != body:
+        with open(JIT_INC, 'w') as f:
+            f.write(body)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, '*.cu')))
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
         return LIB
+    write_jit_headers()
     nvcc = _nvcc()
 
     def compile_one(src: str) -> str:
@@ -55,7 +78,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + f'.{os.getpid()}.tmp'
-    cmd = [nvcc] + ARCH + ['-shared', '-o', tmp] + objs
+    cmd = [nvcc] + ARCH + ['-shared', '-o', tmp] + objs + ['-ldl']
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f'link failed:\n{r.stderr}')

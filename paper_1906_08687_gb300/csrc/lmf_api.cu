@@ -13,6 +13,7 @@
 //                                      reverse views and the per-row grouped tables at once
 #include "lmf.h"
 #include "lmf_internal.h"
+#include "lmf_jit.h"
 #include "lmf_tree.h"
 #include "lmf_gram_tc.h"
 
@@ -134,6 +135,8 @@ struct Plan {
   std::unique_ptr<TreePlan> tree;
   // tensor-core Gram
   std::unique_ptr<GramTcPlan> tc;
+  // plain root scan compiled for this plan (null: the interpreted kernel)
+  cudaKernel_t jit_plain = nullptr;
   // results
   int64_t n_i64 = 0, n_f64 = 0;
   size_t res_i64_off = 0, res_f64_off = 0;
@@ -872,7 +875,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   std::vector<int> rv_used(rp.n_grp, 0);
   struct GPlan {
     int mode; int grp; int slot; int mu_word; int direct; double scale; int64_t cells; size_t out_off; int cache_off;
-    int res_off, res_q, res_word, res_n;
+    int res_off, res_q, res_word, res_n, res_lanes;
   };
   std::vector<GPlan> gplan(B.aggs.size());
   for (size_t a = 0; a < B.aggs.size(); ++a) {
@@ -975,7 +978,15 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   // one category from its group; their counters for the current key live in
   // shared memory (kResBudget of them in all)
   constexpr int64_t kResRun = 1024;
-  constexpr int kResBudget = 24 * 1024 / 4, kResTableMax = 4096;
+  constexpr int kResTableMax = 4096;
+  // shared memory left for the per-CTA counters (resident key, hot cells)
+  // when two CTAs share an SM; the resident key takes up to three quarters
+  int mp0 = 16;
+  while (mp0 < m) mp0 += 16;
+  const bool tc_planned = P->opts.precision == LMF_PREC_SPLIT_BF16 && gram_tc_supported(m) && P->unique_all;
+  const size_t base_smem = tc_planned ? gram_tc_smem(ncat, 0, 0) : root_plain_smem(mp0, ncat, 0, 0, P->unique_all);
+  const int64_t cell_budget = std::max<int64_t>(0, ((int64_t)108 * 1024 - (int64_t)base_smem) / 4);
+  const int64_t kResBudget = cell_budget * 3 / 4;
   int res_grp = -1, res_cells = 0;
   // changes between adjacent root rows of every probe group's foreign key;
   // a key whose runs average 4 rows or more gets its updates summed per run
@@ -1019,11 +1030,30 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
         }
       }
       if (n_in != 1 || n > kResTableMax || res_cells + n > kResBudget) continue;
-      gplan[a].res_off = res_cells;
+      gplan[a].res_off = 0;
       gplan[a].res_q = q_res;
       gplan[a].res_word = P->catword.at(ag.gb[q_res]).second;
       gplan[a].res_n = (int)n;
+      gplan[a].res_lanes = 0;
       res_cells += (int)n;
+    }
+    // tables of at most 32 cells, smallest first, get one counter per lane
+    // while the budget lasts (their few hot cells would serialise a warp's
+    // shared-memory atomics)
+    std::vector<size_t> small;
+    for (size_t a = 0; a < B.aggs.size(); ++a)
+      if (cls[a].kind == 1 && gplan[a].res_off >= 0 && gplan[a].res_n <= 32) small.push_back(a);
+    std::stable_sort(small.begin(), small.end(), [&](size_t x, size_t y) { return gplan[x].res_n < gplan[y].res_n; });
+    for (size_t a : small) {
+      if (res_cells + 31 * gplan[a].res_n > kResBudget) break;
+      gplan[a].res_lanes = 1;
+      res_cells += 31 * gplan[a].res_n;
+    }
+    res_cells = 0;
+    for (size_t a = 0; a < B.aggs.size(); ++a) {
+      if (cls[a].kind != 1 || gplan[a].res_off < 0) continue;
+      gplan[a].res_off = res_cells;
+      res_cells += gplan[a].res_n * (gplan[a].res_lanes ? 32 : 1);
     }
     if (res_cells == 0) res_grp = -1;
   }
@@ -1060,7 +1090,8 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     for (size_t a = 0; a < B.aggs.size(); ++a) {
       if (cls[a].kind != 1 || !gplan[a].direct || B.aggs[a].gb.size() != 2) continue;
       if (!cls[a].mono.empty() || !P->unique_all || gplan[a].res_off >= 0) continue;
-      if (cache_cells + kHotVals * kHotVals > kCacheBudget) break;
+      if (cache_cells + kHotVals * kHotVals > kCacheBudget || res_cells + cache_cells + kHotVals * kHotVals > cell_budget)
+        break;
       for (auto& gname : B.aggs[a].gb) {
         const int rc = P->rowcat.at(gname);
         if (hot_vals.count(rc)) continue;
@@ -1093,7 +1124,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   P->mp = mp;
   const int T = root_plain_tile_rows();
   P->n_tiles = (Root.nrows + T - 1) / T;
-  P->smem = root_plain_smem(mp, ncat, cache_cells, res_cells);
+  P->smem = root_plain_smem(mp, ncat, cache_cells, res_cells, P->unique_all);
   int cps = P->opts.ctas_per_sm > 0 ? P->opts.ctas_per_sm : (P->smem <= 110 * 1024 ? 2 : 1);
   P->grid = (int)std::max<int64_t>(1, std::min<int64_t>(P->n_tiles, (int64_t)c->num_sms * cps));
   CUDA_TRY(c, root_plain_prepare(mp, P->smem));
@@ -1233,6 +1264,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       d.res_q = gp.res_q;
       d.res_word = gp.res_word;
       d.res_n = gp.res_n;
+      d.res_lanes = gp.res_lanes;
       if (gp.cache_off >= 0) {
         const auto& va = hot_vals.at(d.cat[0]);
         const auto& vb = hot_vals.at(d.cat[1]);
@@ -1341,6 +1373,20 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   }
   if (use_tc) {
     gram_tc_finish(P->tc.get(), rp, P->arena.base);
+  }
+  // the compilation step (Sec. 1.2, App. C): the plain root scan with this
+  // plan's layout as constants; the interpreted kernel stays when NVRTC is
+  // missing or the compile fails (same arithmetic, same results)
+  if (!use_tc && !(P->opts.flags & LMF_PLAN_NO_JIT) && Root.nrows > 0 && jit_available()) {
+    std::string log;
+    cudaKernel_t k = nullptr;
+    if (jit_kernel(jit_plain_source(rp, P->mp, direct), "lmf_root_plain_jit", &k, &log)) {
+      CUDA_TRY(c, cudaFuncSetAttribute(reinterpret_cast<const void*>(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(P->smem)));
+      P->jit_plain = k;
+    } else {
+      std::fprintf(stderr, "lmf: plan-time compile failed, interpreted root scan kept: %.400s\n", log.c_str());
+    }
   }
   P->n_views = (int)P->post.size();
   P->root_scan = !P->maps.empty();
@@ -1458,7 +1504,13 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
     if (P->tc) {
       CUDA_TRY(c, gram_tc_launch(P->tc.get(), P->rootp, s));
     } else {
-      CUDA_TRY(c, launch_root_plain(P->rootp, P->mp, P->grid, P->n_tiles, P->smem, s));
+      if (P->jit_plain) {
+        void* args[] = {&P->rootp, &P->n_tiles};
+        CUDA_TRY(c, cudaLaunchKernel(reinterpret_cast<const void*>(P->jit_plain), dim3(P->grid), dim3(256), args,
+                                     P->smem, s));
+      } else {
+        CUDA_TRY(c, launch_root_plain(P->rootp, P->mp, P->grid, P->n_tiles, P->smem, s));
+      }
     }
     ++nk;
   }
@@ -1546,6 +1598,7 @@ lmf_status lmf_plan_info(lmf_ctx* c, int batch_id, lmf_plan_stats* info) {
   info->scratch_bytes = (int64_t)P->arena.size;
   info->resident_group = P->rootp.res_cells > 0 ? P->rootp.res_grp : -1;
   info->resident_cells = P->rootp.res_cells;
+  info->jit = P->jit_plain ? 1 : 0;
   return LMF_OK;
 }
 

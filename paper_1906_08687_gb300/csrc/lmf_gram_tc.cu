@@ -325,6 +325,9 @@ __global__ void k_combine_tc(const double* part, int grid, int m, const long lon
 }  // namespace
 
 bool gram_tc_supported(int m) { return m >= 1 && m <= 32; }
+size_t gram_tc_smem(int n_rowcat, int cache_cells, int res_cells) {
+  return tc_layout(n_rowcat, cache_cells, res_cells).total;
+}
 
 void gram_tc_shape(int m, int64_t N, int num_sms, int /*tile_rows*/, GramTcPlan* tp) {
   tp->m = m;

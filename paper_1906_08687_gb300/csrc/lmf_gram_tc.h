@@ -21,6 +21,8 @@ struct GramTcPlan {
 
 // z lengths the kernel handles (one 32-feature block per split piece)
 bool gram_tc_supported(int m);
+// dynamic shared memory of one CTA
+size_t gram_tc_smem(int n_rowcat, int cache_cells, int res_cells);
 void gram_tc_shape(int m, int64_t N, int num_sms, int tile_rows, GramTcPlan* tp);
 // shared memory / grid for a row-category vector of n_rowcat entries
 cudaError_t gram_tc_configure(GramTcPlan* tp, int n_rowcat, int ctas_per_sm, int cache_cells, int res_cells);

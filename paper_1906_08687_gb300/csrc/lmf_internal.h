@@ -7,8 +7,20 @@
 // record array (merge case (1) of Sec. 3.4) called a *probe group* here.
 #pragma once
 
+#ifdef __CUDACC_RTC__  // compiled at plan time by NVRTC: no host headers
+typedef signed char int8_t;
+typedef short int16_t;
+typedef int int32_t;
+typedef long long int64_t;
+typedef unsigned char uint8_t;
+typedef unsigned short uint16_t;
+typedef unsigned int uint32_t;
+typedef unsigned long long uint64_t;
+#else
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#endif
 
 namespace lmf {
 
@@ -121,7 +133,9 @@ struct DirectAgg {
   int32_t res_off;                   // first shared counter, -1: not resident
   int32_t res_q;                     // group-by position of the resident group's category
   int32_t res_word;                  // that category's word in the resident group's record
-  int32_t res_n;                     // counters: product of the other positions' domains
+  int32_t res_n;                     // cells: product of the other positions' domains
+  int32_t res_lanes;                 // 1: 32 counters per cell, one per lane (no same-address
+                                     //    conflicts inside a warp), 0: one counter per cell
   int32_t runs;                      // 1: its cells come in runs of equal values (sum them per warp)
 };
 
@@ -201,6 +215,7 @@ struct OutMap {
   double inv_scale;                  // kind 3
 };
 
+#ifndef __CUDACC_RTC__
 // ---------------------------------------------------------------------------
 // kernel launchers (lmf_kernels.cu)
 cudaError_t launch_view_unique(const ViewArgs& a, cudaStream_t s);
@@ -208,7 +223,7 @@ cudaError_t launch_view_general(const ViewArgs& a, cudaStream_t s);
 cudaError_t launch_view_finalize(const ViewFinalizeArgs& a, cudaStream_t s);
 cudaError_t launch_root_plain(const RootParams& p, int mp, int grid, int64_t n_tiles,
                               size_t smem, cudaStream_t s);
-size_t root_plain_smem(int mp, int n_rowcat, int cache_cells = 0, int res_cells = 0);
+size_t root_plain_smem(int mp, int n_rowcat, int cache_cells = 0, int res_cells = 0, bool unit_w = false);
 cudaError_t root_plain_prepare(int mp, size_t smem);
 int root_plain_tile_rows();
 cudaError_t launch_combine(const double* part, int grid, int mp, int m, const long long* cnt_part,
@@ -224,5 +239,6 @@ cudaError_t launch_key_stats(const int32_t* key, int64_t n, unsigned int* hist, 
                              int* minmax, cudaStream_t s);
 // *out += number of adjacent unequal pairs of key[0, n) (*out zeroed by the caller)
 cudaError_t launch_key_changes(const int32_t* key, int64_t n, unsigned long long* out, cudaStream_t s);
+#endif  // __CUDACC_RTC__
 
 }  // namespace lmf

@@ -147,12 +147,13 @@ __device__ __forceinline__ void rp_direct_add(const RootParams& p, const DirectA
 // table's row for the current key) and adds them to the table when the key
 // changes.  Counters are 32-bit: a CTA holds a key for fewer than 2^32 rows.
 
-// a row's counter within a resident table: the other positions, last fastest
+// a row's counter within a resident table: the cell of the other positions
+// (last fastest), times 32 plus the lane for lane-private counters
 __device__ __forceinline__ int res_index(const DirectAgg& A, const int32_t* crow) {
   int idx = 0;
   for (int q = 0; q < A.n_gb; ++q)
     if (q != A.res_q) idx = idx * A.dom[q] + crow[A.cat[q]];
-  return idx;
+  return A.res_lanes ? idx * 32 + static_cast<int>(threadIdx.x & 31) : idx;
 }
 
 // adds the counters of resident key k to their tables and clears them; every
@@ -165,9 +166,18 @@ __device__ __forceinline__ void root_res_flush(const RootParams& p, uint32_t* hi
     if (A.res_off < 0) continue;
     const int32_t a = static_cast<int32_t>(G.rec[k * G.stride + A.res_word]);
     for (int i = threadIdx.x; i < A.res_n; i += blockDim.x) {
-      const uint32_t v = hist[A.res_off + i];
+      uint32_t v = 0u;
+      if (A.res_lanes) {
+        uint32_t* h = hist + A.res_off + i * 32;
+        for (int l = 0; l < 32; ++l) {
+          v += h[l];
+          h[l] = 0u;
+        }
+      } else {
+        v = hist[A.res_off + i];
+        hist[A.res_off + i] = 0u;
+      }
       if (v == 0u) continue;
-      hist[A.res_off + i] = 0u;
       int rem = i;
       int64_t cell = 0, mult = 1;
       for (int q = A.n_gb - 1; q >= 0; --q) {
@@ -243,41 +253,54 @@ __device__ __forceinline__ void root_direct_one(const RootParams& p, const Direc
 // over the rows of each run of equal keys and issues one reduction per run, so
 // one instruction updates a key's consecutive slots.  zw: the warp's z rows,
 // ldz floats apart (zero for dead rows); fk: this lane's key, -1 when dead.
+// the key's join count of every run, issued by the run's first lane
+__device__ __forceinline__ void rv_count_runs(const WarpRuns& q, bool unit_w, long long fk, long long w,
+                                              unsigned long long* hist) {
+  const int lane = threadIdx.x & 31;
+  if (unit_w) {
+    const unsigned live = __ballot_sync(kFullWarp, w != 0);
+    if (q.head && fk >= 0) {
+      const unsigned run = (q.end == 32 ? 0xffffffffu : ((1u << q.end) - 1u)) & ~((1u << lane) - 1u);
+      rp_red_u64(hist + fk, static_cast<unsigned long long>(__popc(live & run)));
+    }
+  } else {
+    const long long h = warp_run_sum(q, w);
+    if (q.head && fk >= 0 && h != 0) rp_red_u64(hist + fk, static_cast<unsigned long long>(h));
+  }
+}
+
+// slot s of a reverse view with n_slot slots per key (this lane's slot when
+// `slot`; zi its z index, sc its fixed-point scale): sum over each run's rows,
+// one reduction per run
+__device__ __forceinline__ void rv_slot_runs(const WarpRuns& q, bool unit_w, long long fk, long long w,
+                                             const float* zw, int ldz, bool slot, int zi, float sc, long long* R,
+                                             int n_slot, int s) {
+  long long acc = 0;
+#pragma unroll 4
+  for (int j = 0; j < 32; ++j) {
+    if (unit_w) {  // w is 0 or 1 and z is zero for dead rows
+      acc += __float2ll_rn(zw[j * ldz + zi] * sc);
+    } else {
+      acc += rp_fixp(__shfl_sync(kFullWarp, w, j), zw[j * ldz + zi], sc);
+    }
+    if (j == 31 || ((q.heads >> (j + 1)) & 1u)) {  // row j ends a run (warp-uniform)
+      const long long kj = __shfl_sync(kFullWarp, fk, j);
+      if (slot && kj >= 0 && acc != 0) rp_add_ll(R + kj * n_slot + s, acc);
+      acc = 0;
+    }
+  }
+}
+
 __device__ __forceinline__ void root_rv_slots(const RootParams& p, const RevView& R, long long fk, long long w,
                                               const float* zw, int ldz) {
   const int lane = threadIdx.x & 31;
   const WarpRuns q = warp_runs(fk);
-  // the key's join count: one reduction from the head of every run
-  if (p.unit_w) {
-    const unsigned live = __ballot_sync(kFullWarp, w != 0);
-    if (q.head && fk >= 0) {
-      const unsigned run = (q.end == 32 ? 0xffffffffu : ((1u << q.end) - 1u)) & ~((1u << lane) - 1u);
-      rp_red_u64(R.hist + fk, static_cast<unsigned long long>(__popc(live & run)));
-    }
-  } else {
-    const long long h = warp_run_sum(q, w);
-    if (q.head && fk >= 0 && h != 0) rp_red_u64(R.hist + fk, static_cast<unsigned long long>(h));
-  }
-  if (R.n_slot == 0) return;
+  rv_count_runs(q, p.unit_w != 0, fk, w, R.hist);
   for (int s0 = 0; s0 < R.n_slot; s0 += 32) {
     const int s = s0 + lane;
     const bool slot = s < R.n_slot;
-    const int zi = slot ? R.slot_z[s] : 0;
-    const float sc = slot ? R.slot_scale[s] : 0.f;
-    long long acc = 0;
-#pragma unroll 4
-    for (int j = 0; j < 32; ++j) {
-      if (p.unit_w) {  // w is 0 or 1 and z is zero for dead rows
-        acc += __float2ll_rn(zw[j * ldz + zi] * sc);
-      } else {
-        acc += rp_fixp(__shfl_sync(kFullWarp, w, j), zw[j * ldz + zi], sc);
-      }
-      if (j == 31 || ((q.heads >> (j + 1)) & 1u)) {  // row j ends a run (warp-uniform)
-        const long long kj = __shfl_sync(kFullWarp, fk, j);
-        if (slot && kj >= 0 && acc != 0) rp_add_ll(R.R + kj * R.n_slot + s, acc);
-        acc = 0;
-      }
-    }
+    rv_slot_runs(q, p.unit_w != 0, fk, w, zw, ldz, slot, slot ? R.slot_z[s] : 0, slot ? R.slot_scale[s] : 0.f, R.R,
+                 R.n_slot, s);
   }
 }
 

@@ -27,6 +27,7 @@ LMF_ROOT_DECLARED, LMF_ROOT_EXPLICIT, LMF_ROOT_HEURISTIC = 0, 1, 2
 LMF_MAX_GROUP_BY = 3
 LMF_STAGES = 5
 LMF_PLAN_FEATURES = 24
+LMF_PLAN_NO_JIT = 1
 STAGE_NAMES = ['input', 'views', 'root_scan', 'tree', 'finalize']
 
 _ROLE = {'key': LMF_KEY, 'cont': LMF_CONT, 'cat': LMF_CAT}
@@ -53,7 +54,7 @@ class lmf_plan_opts(ctypes.Structure):
     _fields_ = [('precision', ctypes.c_int32), ('batching', ctypes.c_int32),
                 ('tile_rows', ctypes.c_int32), ('ctas_per_sm', ctypes.c_int32),
                 ('root_mode', ctypes.c_int32), ('root_rel', ctypes.c_int32),
-                ('no_merge', ctypes.c_int32), ('reserved', ctypes.c_int32)]
+                ('no_merge', ctypes.c_int32), ('flags', ctypes.c_int32)]
 
 
 class lmf_plan_stats(ctypes.Structure):
@@ -68,7 +69,8 @@ class lmf_plan_stats(ctypes.Structure):
                 ('tree_node_w', ctypes.c_int32), ('tree_ctas_per_sm', ctypes.c_int32),
                 ('tree_chunk', ctypes.c_int32),
                 ('root_rows', ctypes.c_int64), ('scratch_bytes', ctypes.c_int64),
-                ('resident_group', ctypes.c_int32), ('resident_cells', ctypes.c_int32)]
+                ('resident_group', ctypes.c_int32), ('resident_cells', ctypes.c_int32),
+                ('jit', ctypes.c_int32), ('reserved_stats', ctypes.c_int32)]
 
 
 # every symbol include/lmf.h declares, with its ctypes signature
@@ -224,8 +226,9 @@ class Engine:
 
     def plan(self, batch: int, precision: int = LMF_PREC_SPLIT_BF16, batching: int = LMF_BATCH_GRAPH,
              tile_rows: int = 0, ctas_per_sm: int = 0, root_mode: int = 0, root_rel: int = 0,
-             no_merge: int = 0):
-        o = lmf_plan_opts(precision, batching, tile_rows, ctas_per_sm, root_mode, root_rel, no_merge, 0)
+             no_merge: int = 0, jit: bool = True):
+        o = lmf_plan_opts(precision, batching, tile_rows, ctas_per_sm, root_mode, root_rel, no_merge,
+                          0 if jit else LMF_PLAN_NO_JIT)
         self._check(self.lib.lmf_plan(self.ctx, batch, ctypes.byref(o)), 'lmf_plan')
 
     def plan_info(self, batch: int) -> dict:

@@ -43,7 +43,7 @@ def to_pinned(schema):
 
 
 def run_engine(schema, batch, precision=1, batching=1, tensors=None, runs=1, engine=None,
-               tile_rows=0, ctas_per_sm=0):
+               tile_rows=0, ctas_per_sm=0, jit=True):
     """Register `schema`, declare and plan `batch`, run it `runs` times and
     return (list of per-aggregate numpy results of the last run, plan info)."""
     from paper_1906_08687_gb300 import Engine, register_schema
@@ -52,7 +52,7 @@ def run_engine(schema, batch, precision=1, batching=1, tensors=None, runs=1, eng
     register_schema(eng, schema, tensors)
     bid = eng.declare_batch(batch)
     eng.plan(bid, precision=precision, batching=batching, tile_rows=tile_rows,
-             ctas_per_sm=ctas_per_sm)
+             ctas_per_sm=ctas_per_sm, jit=jit)
     outs = []
     for _ in range(runs):
         eng.run(bid)

@@ -10,7 +10,7 @@ from oracle import oracle
 from workloads import (Agg, Column, Relation, Schema, config1, config2, covar_batch, grouped_batch,
                        pair_count_batch, sort_by_join_attributes, tiny_schema)
 
-from lmf_testlib import ARITH_FLOOR, compare, run_engine
+from lmf_testlib import ARITH_FLOOR, compare, run_engine, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -165,3 +165,31 @@ def test_config2_resident_key_engaged():
     got, info, eng = run_engine(sch, batch, precision=SPLIT, batching=GRAPH)
     assert info['resident_group'] == -1 and info['resident_cells'] == 0
     eng.close()
+
+
+@pytest.mark.parametrize('order', ['sorted', 'random'])
+def test_plan_compiled_scan_matches_interpreted(order):
+    """The root scan compiled for the plan (NVRTC) and the interpreted one give
+    bit-identical results: same values, same order of every float operation."""
+    sch, batch = config2(150_001, fact_order=order)
+    tens = to_device(sch)
+    a, ia, ea = run_engine(sch, batch, precision=PLAIN, batching=GRAPH, tensors=tens)
+    b, ib, eb = run_engine(sch, batch, precision=PLAIN, batching=GRAPH, tensors=tens, jit=False)
+    assert ia['jit'] == 1 and ib['jit'] == 0
+    for i, (x, y) in enumerate(zip(a, b)):
+        assert np.array_equal(x, y), batch[i]
+    ea.close()
+    eb.close()
+
+
+@pytest.mark.parametrize('seed', [2, 5, 11])
+def test_plan_compiled_scan_fanout(seed):
+    """Compiled scan on fanning-out joins (w above 1, interpreted per-row
+    tables inside the compiled pass) against the oracle and the interpreted scan."""
+    sch, _ = tiny_schema(7000 + seed, max_rows=40, unique_keys=False)
+    batch = covar_batch(sch.meta['features'])
+    got, info, e1 = _check(sch, batch, PLAIN, SINGLE, floor=ARITH_FLOOR)
+    ref, info0, e0 = run_engine(sch, batch, precision=PLAIN, batching=SINGLE, jit=False)
+    for x, y in zip(got, ref):
+        assert np.array_equal(x, y)
+    e0.close()
