@@ -1207,7 +1207,6 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     R.hist = P->at<unsigned long long>(rv_hist_off[q]);
     R.R = P->at<long long>(rv_R_off[q]);
     R.grp = q;
-    R.runs = has_runs[q];
     R.n_slot = (int)rv_slots[q].size();
     for (int s = 0; s < R.n_slot; ++s) {
       R.slot_z[s] = (int16_t)rv_slots[q][s];

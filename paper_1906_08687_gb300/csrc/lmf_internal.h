@@ -111,7 +111,6 @@ struct RevView {
   unsigned long long* hist;          // [K]
   long long* R;                      // [K][n_slot]
   int32_t grp;                       // root probe group
-  int32_t runs;                      // 1: its key comes in runs of equal values (sum them per warp)
   int32_t n_slot;
   int16_t slot_z[kMaxZ];             // z index of each slot
   float slot_scale[kMaxZ];           // fixed-point scale per slot (power of 2)

@@ -89,7 +89,7 @@ std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<Dir
   // slot tables of the reverse views summed per run: one entry per lane
   for (int r = 0; r < rp.n_rv; ++r) {
     const RevView& R = rp.rv[r];
-    if (!R.runs || R.n_slot == 0) continue;
+    if (R.n_slot == 0) continue;
     const int n = (R.n_slot + 31) / 32 * 32;
     o << "__device__ const int8_t kZi" << r << "[" << n << "] = {";
     for (int s = 0; s < n; ++s) o << (s < R.n_slot ? R.slot_z[s] : 0) << (s + 1 < n ? "," : "");
@@ -152,28 +152,13 @@ std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<Dir
     const RevView& R = rp.rv[r];
     o << "    {  // reverse view " << r << "\n"
       << "      const long long fk = live ? static_cast<long long>(__ldg(p.grp[" << R.grp << "].fk + row)) : -1ll;\n";
-    if (R.runs) {
-      o << "      const WarpRuns q = warp_runs(fk);\n"
-        << "      rv_count_runs(q, " << (unit_w ? "true" : "false") << ", fk, w, p.rv[" << r << "].hist);\n";
-      for (int s0 = 0; s0 < R.n_slot; s0 += 32) {
-        o << "      {\n        const int s = " << s0 << " + lane;\n"
-          << "        rv_slot_runs(q, " << (unit_w ? "true" : "false") << ", fk, w, zrow - lane * ldz, ldz, s < "
-          << R.n_slot << ", kZi" << r << "[s], kSc" << r << "[s], p.rv[" << r << "].R, " << R.n_slot << ", s);\n"
-          << "      }\n";
-      }
-    } else {
-      o << "      if (live) {\n"
-        << "        rp_red_u64(p.rv[" << r << "].hist + fk, static_cast<unsigned long long>(w));\n"
-        << "        long long* dst = p.rv[" << r << "].R + fk * " << R.n_slot << ";\n";
-      for (int s = 0; s < R.n_slot; ++s) {
-        if (unit_w)
-          o << "        rp_add_ll(dst + " << s << ", __float2ll_rn(zrow[" << R.slot_z[s] << "] * "
-            << flit(R.slot_scale[s]) << "));\n";
-        else
-          o << "        rp_add_ll(dst + " << s << ", rp_fixp(w, zrow[" << R.slot_z[s] << "], "
-            << flit(R.slot_scale[s]) << "));\n";
-      }
-      o << "      }\n";
+    o << "      const WarpRuns q = warp_runs(fk);\n"
+      << "      rv_count_runs(q, " << (unit_w ? "true" : "false") << ", fk, w, p.rv[" << r << "].hist);\n";
+    for (int s0 = 0; s0 < R.n_slot; s0 += 32) {
+      o << "      {\n        const int s = " << s0 << " + lane;\n"
+        << "        rv_slot_runs(q, " << (unit_w ? "true" : "false") << ", fk, w, zrow - lane * ldz, ldz, s < "
+        << R.n_slot << ", kZi" << r << "[s], kSc" << r << "[s], p.rv[" << r << "].R, " << R.n_slot << ", s);\n"
+        << "      }\n";
     }
     o << "    }\n";
   }

@@ -251,8 +251,9 @@ __device__ __forceinline__ void root_direct_one(const RootParams& p, const Direc
 
 // Reverse view R for the warp's 32 rows, slot-parallel: lane s sums slot s
 // over the rows of each run of equal keys and issues one reduction per run, so
-// one instruction updates a key's consecutive slots.  zw: the warp's z rows,
-// ldz floats apart (zero for dead rows); fk: this lane's key, -1 when dead.
+// one instruction updates a key's consecutive slots (a few L2 sectors instead
+// of one sector per row and slot).  zw: the warp's z rows, ldz floats apart
+// (zero for dead rows); fk: this lane's key, -1 when dead.
 // the key's join count of every run, issued by the run's first lane
 __device__ __forceinline__ void rv_count_runs(const WarpRuns& q, bool unit_w, long long fk, long long w,
                                               unsigned long long* hist) {
@@ -316,15 +317,7 @@ __device__ __forceinline__ void root_row_grouped(const RootParams& p, int64_t ro
   for (int r = 0; r < p.n_rv; ++r) {
     const RevView& R = p.rv[r];
     const long long fk = live ? static_cast<long long>(p.grp[R.grp].fk[row]) : -1ll;
-    if (R.runs) {  // keys in runs: slot-parallel sums per run (warp-uniform branch)
-      root_rv_slots(p, R, fk, w, zrow - (threadIdx.x & 31) * ldz, ldz);
-      continue;
-    }
-    if (live) {
-      long long* dst = R.R + fk * R.n_slot;
-      rp_red_u64(R.hist + fk, static_cast<unsigned long long>(w));
-      for (int s = 0; s < R.n_slot; ++s) rp_add_ll(dst + s, rp_fixp(w, zrow[R.slot_z[s]], R.slot_scale[s]));
-    }
+    root_rv_slots(p, R, fk, w, zrow - (threadIdx.x & 31) * ldz, ldz);
   }
   const int n_inline = p.n_direct < kDirInline ? p.n_direct : kDirInline;
   for (int d = 0; d < n_inline; ++d) root_direct_one(p, p.dir[d], row, zrow, crow, w, cache, res_hist, res_key, fres);
