@@ -126,6 +126,9 @@ struct Plan {
   std::map<std::string, std::pair<int, int>> catword;  // category -> (root group, word)
   std::map<std::string, int> feat_group;    // feature -> root group owning it (-1 root)
   std::vector<RvTask> rv_tasks;
+  std::vector<CatViewTask> cv_tasks;
+  size_t cvtask_off = 0;
+  int64_t cv_max_cells = 0;
   std::vector<DirectAgg> direct;
   std::vector<CorrTask> corr;
   std::vector<OutMap> maps;
@@ -869,6 +872,37 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   }
   rp.n_rowcat = ncat;
 
+  // ---- key runs: changes between adjacent root rows of every probe group's
+  // foreign key.  A key whose runs average 4 rows or more gets its updates
+  // summed per run inside a warp; the key with the fewest changes, if its
+  // runs average at least kResRun rows (a root sorted on its join attributes,
+  // Sec. 3.5), is held per CTA (the resident key)
+  constexpr int64_t kResRun = 1024;
+  int res_grp = -1;
+  std::vector<unsigned long long> changes(rp.n_grp, 0);
+  std::vector<int> has_runs(rp.n_grp, 0);
+  if (rp.n_grp > 0 && Root.nrows > 1) {
+    unsigned long long* d = nullptr;
+    CUDA_TRY(c, cudaMalloc(&d, sizeof(unsigned long long) * rp.n_grp));
+    CUDA_TRY(c, cudaMemsetAsync(d, 0, sizeof(unsigned long long) * rp.n_grp, c->stream));
+    for (int q = 0; q < rp.n_grp; ++q) {
+      GroupH& g = P->groups[RR.groups[q]];
+      const RelationH& O = c->rels[g.owner];
+      CUDA_TRY(c, launch_key_changes(static_cast<const int32_t*>(O.cols[O.find(g.fk)].dptr()), O.nrows, d + q,
+                                     c->stream));
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(changes.data(), d, sizeof(unsigned long long) * rp.n_grp, cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    cudaFree(d);
+    for (int q = 0; q < rp.n_grp; ++q) {
+      has_runs[q] = (int64_t)(changes[q] + 1) * 4 <= Root.nrows;
+      if (P->unique_all && Root.nrows >= 2 * kResRun && (int64_t)(changes[q] + 1) * kResRun <= Root.nrows &&
+          (res_grp < 0 || changes[q] < changes[res_grp]))
+        res_grp = q;
+    }
+  }
+
   // ---- grouped aggregates
   std::vector<size_t> rv_hist_off(rp.n_grp, 0), rv_R_off(rp.n_grp, 0);
   std::vector<std::vector<int>> rv_slots(rp.n_grp);     // z index per slot
@@ -876,7 +910,12 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   struct GPlan {
     int mode; int grp; int slot; int mu_word; int direct; double scale; int64_t cells; size_t out_off; int cache_off;
     int res_off, res_q, res_word, res_n, res_lanes;
+    int cv, cv_aword, cv_afirst, cv_doma;  // COUNT table read off category view cv (-1: none)
   };
+  // category views: (keying group, row category of b) -> view
+  struct CvPlan { int grp, bcat, bgrp, dom; size_t off; int res_off; };
+  std::vector<CvPlan> cvs;
+  std::map<std::pair<int, int>, int> cv_index;
   std::vector<GPlan> gplan(B.aggs.size());
   for (size_t a = 0; a < B.aggs.size(); ++a) {
     if (cls[a].kind != 1) continue;
@@ -892,11 +931,44 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     GPlan gp{};
     gp.cache_off = -1;
     gp.res_off = -1;
+    gp.cv = -1;
     gp.cells = cells;
     gp.direct = (gsrc < 0) ? 1 : 0;   // root categories or several keys: per-row table
+    if (gp.direct && cls[a].mono.empty() && ag.gb.size() == 2 && P->unique_all) {
+      // a COUNT table over two categories of different keys (or a key and the
+      // root): read it off a view keyed by one of the keys that keeps the other
+      // category; the resident key if it is one of them, else the key with
+      // fewer values (smaller view)
+      const int g0 = P->catword.at(ag.gb[0]).first, g1 = P->catword.at(ag.gb[1]).first;
+      int x = -1;
+      if (g0 >= 0 && (g0 == res_grp || g1 < 0)) x = 0;
+      else if (g1 >= 0 && (g1 == res_grp || g0 < 0)) x = 1;
+      else if (g0 >= 0 && g1 >= 0)
+        x = P->groups[RR.groups[g1]].K < P->groups[RR.groups[g0]].K ? 1 : 0;
+      if (x >= 0) {
+        const int gx = x == 0 ? g0 : g1;
+        const std::string& bname = ag.gb[1 - x];
+        const int bcat = P->rowcat.at(bname);
+        auto key = std::make_pair(gx, bcat);
+        auto it = cv_index.find(key);
+        if (it == cv_index.end() && (int)cvs.size() < kMaxCatViews) {
+          int col, r = owner_of(c, bname, &col);
+          cvs.push_back({gx, bcat, P->catword.at(bname).first, c->rels[r].cols[col].dom, 0, -1});
+          it = cv_index.emplace(key, (int)cvs.size() - 1).first;
+        }
+        if (it != cv_index.end()) {
+          int col, r = owner_of(c, ag.gb[x], &col);
+          gp.cv = it->second;
+          gp.cv_aword = P->catword.at(ag.gb[x]).second;
+          gp.cv_afirst = x == 0 ? 1 : 0;
+          gp.cv_doma = c->rels[r].cols[col].dom;
+          gp.direct = 0;
+        }
+      }
+    }
     std::string f = cls[a].mono.empty() ? "" : cls[a].mono[0];
     gp.scale = f.empty() ? 1.0 : std::ldexp(1.0, fixp_exp(W * bound[f]));
-    if (!gp.direct) {
+    if (!gp.direct && gp.cv < 0) {
       gp.grp = gsrc;
       rv_used[gsrc] = 1;
       if (f.empty()) {
@@ -925,6 +997,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   }
   for (size_t a = 0; a < B.aggs.size(); ++a)
     if (cls[a].kind == 1) gplan[a].out_off = A.take((size_t)gplan[a].cells * 8);
+  for (auto& v : cvs) v.off = A.take((size_t)P->groups[RR.groups[v.grp]].K * v.dom * 8 + 8);
   // omega accumulators of fanning-out root children
   std::vector<std::pair<int, size_t>> omega;  // child relation, offset
   for (int q = 0; q < rp.n_grp; ++q)
@@ -977,7 +1050,6 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   // its join attributes, Sec. 3.5), carries the COUNT tables that take exactly
   // one category from its group; their counters for the current key live in
   // shared memory (kResBudget of them in all)
-  constexpr int64_t kResRun = 1024;
   constexpr int kResTableMax = 4096;
   // shared memory left for the per-CTA counters (resident key, hot cells)
   // when two CTAs share an SM; the resident key takes up to three quarters
@@ -987,34 +1059,16 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   const size_t base_smem = tc_planned ? gram_tc_smem(ncat, 0, 0) : root_plain_smem(mp0, ncat, 0, 0, P->unique_all);
   const int64_t cell_budget = std::max<int64_t>(0, ((int64_t)108 * 1024 - (int64_t)base_smem) / 4);
   const int64_t kResBudget = cell_budget * 3 / 4;
-  int res_grp = -1, res_cells = 0;
-  // changes between adjacent root rows of every probe group's foreign key;
-  // a key whose runs average 4 rows or more gets its updates summed per run
-  // inside a warp
-  std::vector<unsigned long long> changes(rp.n_grp, 0);
-  std::vector<int> has_runs(rp.n_grp, 0);
-  if (rp.n_grp > 0 && Root.nrows > 1) {
-    unsigned long long* d = nullptr;
-    CUDA_TRY(c, cudaMalloc(&d, sizeof(unsigned long long) * rp.n_grp));
-    CUDA_TRY(c, cudaMemsetAsync(d, 0, sizeof(unsigned long long) * rp.n_grp, c->stream));
-    for (int q = 0; q < rp.n_grp; ++q) {
-      GroupH& g = P->groups[RR.groups[q]];
-      const RelationH& O = c->rels[g.owner];
-      CUDA_TRY(c, launch_key_changes(static_cast<const int32_t*>(O.cols[O.find(g.fk)].dptr()), O.nrows, d + q,
-                                     c->stream));
-    }
-    CUDA_TRY(c, cudaMemcpyAsync(changes.data(), d, sizeof(unsigned long long) * rp.n_grp, cudaMemcpyDeviceToHost,
-                                c->stream));
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    cudaFree(d);
-    for (int q = 0; q < rp.n_grp; ++q) {
-      has_runs[q] = (int64_t)(changes[q] + 1) * 4 <= Root.nrows;
-      if (P->unique_all && Root.nrows >= 2 * kResRun && (int64_t)(changes[q] + 1) * kResRun <= Root.nrows &&
-          (res_grp < 0 || changes[q] < changes[res_grp]))
-        res_grp = q;
-    }
-  }
+  int res_cells = 0;
+  int cv_res_cells = 0;
   if (res_grp >= 0) {
+    // category views keyed by the resident key: one counter per value of b
+    for (auto& v : cvs)
+      if (v.grp == res_grp && cv_res_cells + v.dom <= kResBudget) {
+        v.res_off = cv_res_cells;
+        cv_res_cells += v.dom;
+      }
+    res_cells = cv_res_cells;
     for (size_t a = 0; a < B.aggs.size(); ++a) {
       if (cls[a].kind != 1 || !gplan[a].direct || !cls[a].mono.empty()) continue;
       const AggH& ag = B.aggs[a];
@@ -1049,7 +1103,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       gplan[a].res_lanes = 1;
       res_cells += 31 * gplan[a].res_n;
     }
-    res_cells = 0;
+    res_cells = cv_res_cells;
     for (size_t a = 0; a < B.aggs.size(); ++a) {
       if (cls[a].kind != 1 || gplan[a].res_off < 0) continue;
       gplan[a].res_off = res_cells;
@@ -1167,6 +1221,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   // device tables
   size_t n_rvt_est = B.aggs.size() + 1;
   P->rvtask_off = A.take(sizeof(RvTask) * n_rvt_est);
+  P->cvtask_off = A.take(sizeof(CatViewTask) * n_rvt_est);
   P->direct_off = A.take(sizeof(DirectAgg) * n_rvt_est);
   P->corr_off = A.take(sizeof(CorrTask) * (omega.size() + 1));
   P->maps_off = A.take(sizeof(OutMap) * (B.aggs.size() + 1));
@@ -1244,7 +1299,17 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     const GPlan& gp = gplan[a];
     const AggH& ag = B.aggs[a];
     std::string f = cls[a].mono.empty() ? "" : cls[a].mono[0];
-    if (gp.direct) {
+    if (gp.cv >= 0) {
+      CatViewTask t{};
+      t.view = gp.cv;
+      t.a_word = gp.cv_aword;
+      t.dom_a = gp.cv_doma;
+      t.a_first = gp.cv_afirst;
+      t.out = P->at<long long>(gp.out_off);
+      P->cv_tasks.push_back(t);
+      const CvPlan& v = cvs[gp.cv];
+      P->cv_max_cells = std::max<int64_t>(P->cv_max_cells, (int64_t)P->groups[RR.groups[v.grp]].K * v.dom);
+    } else if (gp.direct) {
       DirectAgg d{};
       d.n_gb = (int)ag.gb.size();
       d.runs = 1;
@@ -1295,6 +1360,16 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
                            cudaMemcpyHostToDevice));
   P->rv_tasks = tasks;
   P->direct = direct;
+  rp.n_cv = (int)cvs.size();
+  for (size_t i = 0; i < cvs.size(); ++i) {
+    CatView& C = rp.cv[i];
+    C.grp = cvs[i].grp;
+    C.bcat = cvs[i].bcat;
+    C.dom = cvs[i].dom;
+    C.res_off = res_grp >= 0 ? cvs[i].res_off : -1;
+    C.runs = has_runs[cvs[i].grp] && cvs[i].bgrp >= 0 && has_runs[cvs[i].bgrp];
+    C.V = P->at<long long>(cvs[i].off);
+  }
   rp.n_direct = (int)direct.size();
   rp.direct = P->at<DirectAgg>(P->direct_off);
   for (int d = 0; d < rp.n_direct && d < kDirInline; ++d) rp.dir[d] = direct[d];
@@ -1347,6 +1422,8 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   P->maps = maps;
   P->corr = corr;
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->rvtask_off, tasks.data(), sizeof(RvTask) * tasks.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(P->arena.base + P->cvtask_off, P->cv_tasks.data(), sizeof(CatViewTask) * P->cv_tasks.size(),
+                         cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->direct_off, direct.data(), sizeof(DirectAgg) * direct.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->corr_off, corr.data(), sizeof(CorrTask) * corr.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->maps_off, maps.data(), sizeof(OutMap) * maps.size(), cudaMemcpyHostToDevice));
@@ -1534,6 +1611,11 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
   }
   if (!P->rv_tasks.empty()) {
     CUDA_TRY(c, launch_rv_tasks(P->at<RvTask>(P->rvtask_off), (int)P->rv_tasks.size(), P->rootp, P->max_group_K, s));
+    ++nk;
+  }
+  if (!P->cv_tasks.empty()) {
+    CUDA_TRY(c, launch_cv_tasks(P->at<CatViewTask>(P->cvtask_off), (int)P->cv_tasks.size(), P->rootp,
+                                P->cv_max_cells, s));
     ++nk;
   }
   if (!P->maps.empty()) {

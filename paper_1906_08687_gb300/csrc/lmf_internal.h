@@ -30,6 +30,7 @@ constexpr int kMaxOwn = 48;          // own continuous columns of one relation
 constexpr int kMaxCat = 32;          // categorical words of one record / root row
 constexpr int kMaxQ = kMaxZ * (kMaxZ + 1) / 2;
 constexpr int kDirInline = 96;        // per-row tables whose descriptors ride in the kernel parameters
+constexpr int kMaxCatViews = 64;      // category views of one root scan
 
 // device status bits (OR-ed by kernels, read by lmf_sync)
 constexpr uint32_t kStatusCatRange = 1u;      // category outside [0, domain)
@@ -138,6 +139,33 @@ struct DirectAgg {
   int32_t runs;                      // 1: its cells come in runs of equal values (sum them per warp)
 };
 
+// A directional view from the root towards probe group grp that keeps one
+// more group-by attribute, the category b of another probe group or of the
+// root (Sec. 3.2: a view's group-by holds its join key and the attributes the
+// aggregates above it need): V[k][vb] = sum of w over the root rows with key
+// k and b = vb.  Every COUNT table (a, b) with a carried by grp is read off it
+// by a pass over grp's keys, so a root row makes one update per view instead
+// of one per table.
+struct CatView {
+  int32_t grp;                       // keying probe group
+  int32_t bcat;                      // row-category index of b
+  int32_t dom;                       // domain of b
+  int32_t res_off;                   // grp is the resident group: first of dom shared counters, else -1
+  int32_t runs;                      // 1: (key, b) comes in runs (sum them per warp)
+  int32_t pad;
+  long long* V;                      // [K of grp][dom]
+};
+
+// COUNT table (a, b) read off its category view: for every key k,
+// T[a(k)][vb] += V[k][vb]
+struct CatViewTask {
+  int32_t view;                      // index into RootParams::cv
+  int32_t a_word;                    // a's word in the keying group's record
+  int32_t dom_a;
+  int32_t a_first;                   // 1: cells a * dom_b + b, 0: b * dom_a + a
+  long long* out;
+};
+
 struct OmegaAcc {                    // SUM over root rows of w / cnt_e per key of e
   int32_t grp;
   int32_t cnt_word;
@@ -166,6 +194,8 @@ struct RootParams {
   const DirectAgg* direct;           // device array of all n_direct (read for d >= kDirInline)
   int32_t n_om;
   OmegaAcc om[kMaxGroups * 4];
+  int32_t n_cv;
+  CatView cv[kMaxCatViews];
   uint32_t* status;
   // per-CTA shared-memory cache of the hot cells of pair-count tables (Zipf-hot
   // category values), 32-bit counters flushed once per CTA
@@ -230,6 +260,8 @@ cudaError_t launch_combine(const double* part, int grid, int mp, int m, const lo
 cudaError_t launch_corr(const void* tasks_dev, int n, double* G, int m, cudaStream_t s);
 cudaError_t launch_rv_tasks(const RvTask* tasks, int n_tasks, const RootParams& p,
                             int max_K, cudaStream_t s);
+cudaError_t launch_cv_tasks(const CatViewTask* tasks, int n_tasks, const RootParams& p, int64_t max_cells,
+                            cudaStream_t s);
 cudaError_t launch_out_map(const OutMap* maps, int n_maps, int64_t max_cells, const double* G, int m,
                            const long long* count, long long* res_i64, double* res_f64,
                            cudaStream_t s);

@@ -162,6 +162,24 @@ std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<Dir
     }
     o << "    }\n";
   }
+  // category views
+  for (int v = 0; v < rp.n_cv; ++v) {
+    const CatView& C = rp.cv[v];
+    o << "    {  // category view " << v << "\n"
+      << "      const long long fk = live ? static_cast<long long>(__ldg(p.grp[" << C.grp << "].fk + row)) : -1ll;\n"
+      << "      const int b = live ? crow[" << C.bcat << "] : 0;\n";
+    if (C.res_off >= 0) {
+      o << "      if (res_key >= 0) {\n        if (live) {\n"
+        << "          if (fk == res_key) rp_red_shared_u32(res_hist + " << C.res_off << " + b, static_cast<uint32_t>(w));\n"
+        << "          else rp_add_ll(p.cv[" << v << "].V + fk * " << C.dom << " + b, w);\n"
+        << "        }\n      } else {\n        root_cv_one(p.cv[" << v << "], fk, b, w, res_hist, res_key);\n      }\n";
+    } else if (C.runs) {
+      o << "      root_cv_one(p.cv[" << v << "], fk, b, w, res_hist, res_key);\n";
+    } else {
+      o << "      if (live) rp_add_ll(p.cv[" << v << "].V + fk * " << C.dom << " + b, w);\n";
+    }
+    o << "    }\n";
+  }
   // per-row tables: the common kinds straight-line, the rest through the
   // interpreted routine
   const int n_inl = rp.n_direct < kDirInline ? rp.n_direct : kDirInline;

@@ -375,6 +375,33 @@ __global__ void k_rv_tasks(const RvTask* tasks, int n_tasks, const __grid_consta
   }
 }
 
+// COUNT tables read off category views: one pass over each view's cells;
+// consecutive threads take consecutive b values of one key, so the table
+// updates of a warp fall on one row of the table
+__global__ void k_cv_tasks(const CatViewTask* tasks, const __grid_constant__ RootParams p) {
+  const CatViewTask t = tasks[blockIdx.y];
+  const CatView& C = p.cv[t.view];
+  const GroupDesc& G = p.grp[C.grp];
+  const int64_t n = static_cast<int64_t>(G.K) * C.dom;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const long long v = C.V[i];
+    if (v == 0) continue;
+    const int64_t k = i / C.dom;
+    const int b = static_cast<int>(i - k * C.dom);
+    const int a = static_cast<int32_t>(G.rec[k * G.stride + t.a_word]);
+    add_ll(t.out + (t.a_first ? static_cast<int64_t>(a) * C.dom + b : static_cast<int64_t>(b) * t.dom_a + a), v);
+  }
+}
+
+cudaError_t launch_cv_tasks(const CatViewTask* tasks, int n_tasks, const RootParams& p, int64_t max_cells,
+                            cudaStream_t s) {
+  if (n_tasks <= 0) return cudaSuccess;
+  const int64_t gb = (max_cells + 255) / 256;
+  dim3 grid((unsigned)(gb < 256 ? (gb < 1 ? 1 : gb) : 256), (unsigned)n_tasks);
+  k_cv_tasks<<<grid, 256, 0, s>>>(tasks, p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rv_tasks(const RvTask* tasks, int n_tasks, const RootParams& p, int max_K,
                             cudaStream_t s) {
   if (n_tasks <= 0) return cudaSuccess;

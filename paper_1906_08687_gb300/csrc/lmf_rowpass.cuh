@@ -160,6 +160,16 @@ __device__ __forceinline__ int res_index(const DirectAgg& A, const int32_t* crow
 // thread of the CTA calls this
 __device__ __forceinline__ void root_res_flush(const RootParams& p, uint32_t* hist, long long k) {
   if (k < 0) return;  // no row counted under "no key"
+  for (int v = 0; v < p.n_cv; ++v) {
+    const CatView& C = p.cv[v];
+    if (C.res_off < 0) continue;
+    for (int i = threadIdx.x; i < C.dom; i += blockDim.x) {
+      const uint32_t n = hist[C.res_off + i];
+      if (n == 0u) continue;
+      hist[C.res_off + i] = 0u;
+      rp_red_u64(reinterpret_cast<unsigned long long*>(C.V + k * C.dom + i), n);
+    }
+  }
   const GroupDesc& G = p.grp[p.res_grp];
   for (int d = 0; d < p.n_direct; ++d) {
     const DirectAgg& A = d < kDirInline ? p.dir[d] : p.direct[d];
@@ -305,6 +315,29 @@ __device__ __forceinline__ void root_rv_slots(const RootParams& p, const RevView
   }
 }
 
+// category view C for the warp's rows (every lane calls this): fk is the row's
+// key of C's group (-1 when dead), b its category value
+__device__ __forceinline__ void root_cv_one(const CatView& C, long long fk, int b, long long w, uint32_t* res_hist,
+                                            long long res_key) {
+  const bool live = w != 0;
+  if (C.res_off >= 0 && res_key >= 0) {  // resident form (warp-uniform branch)
+    if (!live) return;
+    if (fk == res_key) rp_red_shared_u32(res_hist + C.res_off + b, static_cast<uint32_t>(w));
+    else rp_add_ll(C.V + fk * C.dom + b, w);
+    return;
+  }
+  const long long cell = live ? fk * C.dom + b : -1ll;
+  if (C.runs) {  // warp-uniform
+    const WarpRuns q = warp_runs(cell);
+    if (q.sum) {
+      const long long t = warp_run_sum(q, w);
+      if (q.head && live) rp_add_ll(C.V + cell, t);
+      return;
+    }
+  }
+  if (live) rp_add_ll(C.V + cell, w);
+}
+
 // Grouped updates of the warp's 32 rows; every lane of the warp calls this,
 // w == 0 marks a row that does not join (or lies past the relation's end).
 // cache (may be null) holds the CTA's counters for the hot cells of
@@ -318,6 +351,11 @@ __device__ __forceinline__ void root_row_grouped(const RootParams& p, int64_t ro
     const RevView& R = p.rv[r];
     const long long fk = live ? static_cast<long long>(p.grp[R.grp].fk[row]) : -1ll;
     root_rv_slots(p, R, fk, w, zrow - (threadIdx.x & 31) * ldz, ldz);
+  }
+  for (int v = 0; v < p.n_cv; ++v) {
+    const CatView& C = p.cv[v];
+    const long long fk = live ? static_cast<long long>(p.grp[C.grp].fk[row]) : -1ll;
+    root_cv_one(C, fk, live ? crow[C.bcat] : 0, w, res_hist, res_key);
   }
   const int n_inline = p.n_direct < kDirInline ? p.n_direct : kDirInline;
   for (int d = 0; d < n_inline; ++d) root_direct_one(p, p.dir[d], row, zrow, crow, w, cache, res_hist, res_key, fres);
