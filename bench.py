@@ -38,6 +38,8 @@ PROFILE_SUMMARY = os.path.join(ROOT, 'profiles', 'root_scan_snowflake20M.md')
 KERNEL_SOURCES = ['paper_1906_08687_gb300/csrc/lmf_kernels.cu',
                   'paper_1906_08687_gb300/csrc/lmf_gram_tc.cu',
                   'paper_1906_08687_gb300/csrc/lmf_rowpass.cuh',
+                  'paper_1906_08687_gb300/csrc/lmf_root_plain.cuh',
+                  'paper_1906_08687_gb300/csrc/lmf_jit.cu',
                   'paper_1906_08687_gb300/csrc/lmf_internal.h']
 
 
@@ -48,14 +50,16 @@ def parse():
     ap.add_argument('--warmup', type=int, default=5)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--n-fact', type=int, default=20_000_000)
-    ap.add_argument('--precision', default='split', choices=['split', 'plain'])
+    ap.add_argument('--precision', default='auto', choices=['auto', 'split', 'plain'],
+                    help='Gram precision of the chosen plan; auto times both candidates '
+                         '(split-bf16 tensor cores, FP32 CUDA cores) and keeps the faster')
     ap.add_argument('--fact-order', default='sorted', choices=['sorted', 'random'],
                     help='fact rows sorted by their join attributes (the input order of the '
                          "paper's experiments) or in generation order")
     ap.add_argument('--cpu-sample-rows', type=int, default=10_000_000)
     ap.add_argument('--ref-sample-rows', type=int, default=200_000)
-    ap.add_argument('--check-aggs', type=int, default=48,
-                    help='aggregates re-evaluated by the oracle over the full join (0: skip)')
+    ap.add_argument('--check-aggs', type=int, default=-1,
+                    help='aggregates re-evaluated by the oracle over the full join (0: skip, -1: all)')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     return ap.parse_args()
 
@@ -223,13 +227,11 @@ def main():
     dev = to_device(sch, f'cuda:{local}')
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
-    prec = 1 if args.precision == 'split' else 0
-
-    def make(precision, batching, tensors, on_host=False):
+    def make(precision, batching, tensors, on_host=False, jit=True):
         eng = Engine(local)
         register_schema(eng, sch, tensors, on_host=on_host)
         bid = eng.declare_batch(batch)
-        eng.plan(bid, precision=precision, batching=batching)
+        eng.plan(bid, precision=precision, batching=batching, jit=jit)
         return eng, bid
 
     def timed(eng, bid, steps, warmup, sampler=None):
@@ -251,8 +253,26 @@ def main():
         eng.sync(bid)
         return max_over_ranks(ws, e0.elapsed_time(e1) / steps), clocks
 
-    # chosen form: split-bf16 Gram (when planned), one CUDA graph per run
-    eng, bid = make(prec, 1, dev)
+    # chosen form: one CUDA graph per run, the root scan compiled for the plan;
+    # the Gram precision is the faster of the two candidates (auto) or fixed
+    names = {'split': 1, 'plain': 0}
+    cands = ['split', 'plain'] if args.precision == 'auto' else [args.precision]
+    cand_ms = {}
+    best = None
+    for cname in cands:
+        e_c, b_c = make(names[cname], 1, dev)
+        if e_c.plan_info(b_c)['precision'] != names[cname]:   # not plannable in this form
+            e_c.close()
+            continue
+        cand_ms[cname], _ = timed(e_c, b_c, max(3, args.steps // 2), args.warmup)
+        if best is None or cand_ms[cname] < cand_ms[best[0]]:
+            if best is not None:
+                best[1].close()
+            best = (cname, e_c, b_c)
+        else:
+            e_c.close()
+    chosen, eng, bid = best
+    prec = names[chosen]
     info = eng.plan_info(bid)
     join_rows = info['root_rows']   # unique dimension keys: |join| = fact rows
     sampler = ClockSampler(local)
@@ -270,8 +290,9 @@ def main():
     # results of the chosen form for the accuracy check
     got = eng.results(bid, n_agg)
 
-    # plain form: FP32 CUDA-core Gram, kernels enqueued one by one
-    eng_p, bid_p = make(0, 0, dev)
+    # plain form: FP32 CUDA-core Gram, interpreted root scan (no plan-time
+    # compile), kernels enqueued one by one
+    eng_p, bid_p = make(0, 0, dev, jit=False)
     ms_plain, _ = timed(eng_p, bid_p, args.steps, args.warmup)
     eng_p.close()
 
@@ -308,7 +329,7 @@ def main():
     peaks = measured_peaks()
     achieved = algo / (root_ms * 1e-3) / 1e9
     roof = {'bound': 'hbm', 'achieved': achieved, 'peak': peaks['hbm_gbs'], 'unit': 'GB/s',
-            'frac': achieved / peaks['hbm_gbs'], 'traffic': profiled_traffic(args.precision),
+            'frac': achieved / peaks['hbm_gbs'], 'traffic': profiled_traffic(chosen),
             'peak_source': peaks['source'], 'kernel': 'root scan (stage root_scan)',
             'algorithmic_bytes_per_launch': algo, 'launch_ms': root_ms,
             'stage_ms': {n: float(v) for n, v in zip(STAGE_NAMES, stage)}}
@@ -322,6 +343,10 @@ def main():
         'config': {'workload': f'snowflake-{args.n_fact} (3 FKs, 8 fact + 22 dimension features, '
                                f'10 categoricals; covar + grouped + pair counts)',
                    'n_aggregates': n_agg, 'join_rows': join_rows, 'precision': info['precision'],
+                   'plan': {'gram': 'split-bf16 tcgen05' if prec == 1 else 'FP32 CUDA cores (TwoSum)',
+                            'root_scan_compiled': bool(info['jit']),
+                            'resident_group': info['resident_group'],
+                            'candidates_ms_per_step': cand_ms},
                    'fact_order': (FACT_ORDER_SORTED if args.fact_order == 'sorted'
                                   else 'generation order (i.i.d. rows)'),
                    'batching': 'cuda-graph', 'kernels_per_step': info['n_kernels_per_run'],
@@ -329,6 +354,7 @@ def main():
                    'parallelism': f'replicas x{ws}'},
         'hbm_pct_of_peak': 100.0 * roof['frac'],
         'speedup_vs_plain': ms_plain / ms, 'plain_ms_per_step': ms_plain,
+        'plain_form': 'FP32 Gram, interpreted root scan, kernels launched one by one',
         'roofline': roof,
         'e2e': {'value': ws * join_rows * n_agg / (e2e_ms * 1e-3) / 1e9, 'unit': UNIT,
                 'h2d_bytes_per_step': h2d, 'd2h_bytes_per_step': d2h, 'ms_per_step': e2e_ms},
@@ -336,11 +362,14 @@ def main():
         'clocks': clocks,
     }
 
-    if rank == 0 and args.check_aggs > 0:
+    if rank == 0 and args.check_aggs != 0:
         from oracle import oracle
         oracle.build()
         rng = np.random.default_rng(0)
-        pick = sorted(set([0] + list(rng.choice(n_agg, size=min(args.check_aggs, n_agg), replace=False))))
+        if args.check_aggs < 0 or args.check_aggs >= n_agg:
+            pick = list(range(n_agg))
+        else:
+            pick = sorted(set([0] + list(rng.choice(n_agg, size=args.check_aggs, replace=False))))
         want = oracle.evaluate(sch, [batch[i] for i in pick])
         fails, stats = compare([got[i] for i in pick], want)
         line['accuracy'] = {'checked_aggregates': len(pick), 'failures': len(fails), **stats,

@@ -127,6 +127,9 @@ struct Plan {
   std::map<std::string, int> feat_group;    // feature -> root group owning it (-1 root)
   std::vector<RvTask> rv_tasks;
   std::vector<CatViewTask> cv_tasks;
+  std::vector<GroupGram> ggram;
+  size_t ggram_off = 0, ggram_part_off = 0;
+  static constexpr int kGgChunks = 2048;  // key ranges (one warp each) of the key-level Gram
   size_t cvtask_off = 0;
   int64_t cv_max_cells = 0;
   std::vector<DirectAgg> direct;
@@ -989,6 +992,12 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     gplan[a] = gp;
     ++P->n_grouped;
   }
+  // the Gram block of a group's view means is taken at the key level
+  // (GroupGram) wherever the group keeps its key counts; a group whose key
+  // comes in runs always does (on a sorted root the row-level FP32 sums would
+  // add the same products over and over)
+  for (int q = 0; q < rp.n_grp; ++q)
+    if (P->groups[RR.groups[q]].n_mu > 0 && has_runs[q]) rv_used[q] = 1;
   for (int q = 0; q < rp.n_grp; ++q) {
     if (!rv_used[q]) continue;
     GroupH& g = P->groups[RR.groups[q]];
@@ -1222,6 +1231,15 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   size_t n_rvt_est = B.aggs.size() + 1;
   P->rvtask_off = A.take(sizeof(RvTask) * n_rvt_est);
   P->cvtask_off = A.take(sizeof(CatViewTask) * n_rvt_est);
+  {
+    size_t npart = 0;
+    for (int q = 0; q < rp.n_grp; ++q) {
+      const int n = P->groups[RR.groups[q]].n_mu;
+      if (n > 0) npart += (size_t)((n + 1) * (n + 2) / 2 - 1);
+    }
+    P->ggram_off = A.take(sizeof(GroupGram) * (rp.n_grp + 1));
+    P->ggram_part_off = A.take(sizeof(double) * (npart * Plan::kGgChunks + 1));
+  }
   P->direct_off = A.take(sizeof(DirectAgg) * n_rvt_est);
   P->corr_off = A.take(sizeof(CorrTask) * (omega.size() + 1));
   P->maps_off = A.take(sizeof(OutMap) * (B.aggs.size() + 1));
@@ -1272,6 +1290,23 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     }
     rv_index[q] = rp.n_rv++;
   }
+  {
+    int part = 0;
+    for (int q = 0; q < rp.n_grp; ++q) {
+      const GroupDesc& G = rp.grp[q];
+      if (G.n_mu <= 0 || rv_index[q] < 0) continue;
+      GroupGram g{};
+      g.grp = q;
+      g.rv = rv_index[q];
+      g.n = G.n_mu;
+      g.zoff = rp.grp_zoff[q];
+      g.mu_word = G.n_cnt;
+      g.npair = (g.n + 1) * (g.n + 2) / 2 - 1;
+      g.part_off = part;
+      part += g.npair;
+      P->ggram.push_back(g);
+    }
+  }
   // hot-cell tables: category value -> hot index, and the global cell every
   // cache cell flushes to
   std::vector<long long*> cache_dst(cache_cells, P->at<long long>(P->count_off));
@@ -1291,6 +1326,11 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   rp.res_grp = res_grp < 0 ? 0 : res_grp;
   rp.res_cells = res_cells;
   rp.unit_w = P->unique_all ? 1 : 0;
+  {
+    int n_runs = 0;
+    for (int q = 0; q < rp.n_grp; ++q) n_runs += has_runs[q];
+    rp.fold = n_runs >= 2 ? 8 : 0;
+  }
   rp.cache_dst = P->at<long long*>(cache_dst_off);
   std::vector<RvTask> tasks;
   std::vector<DirectAgg> direct;
@@ -1423,6 +1463,8 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   P->corr = corr;
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->rvtask_off, tasks.data(), sizeof(RvTask) * tasks.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->cvtask_off, P->cv_tasks.data(), sizeof(CatViewTask) * P->cv_tasks.size(),
+                         cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(P->arena.base + P->ggram_off, P->ggram.data(), sizeof(GroupGram) * P->ggram.size(),
                          cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->direct_off, direct.data(), sizeof(DirectAgg) * direct.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->corr_off, corr.data(), sizeof(CorrTask) * corr.size(), cudaMemcpyHostToDevice));
@@ -1604,6 +1646,11 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
                                  P->at<long long>(P->count_off), s));
     }
     ++nk;
+    if (!P->ggram.empty()) {
+      CUDA_TRY(c, launch_group_gram(P->at<GroupGram>(P->ggram_off), (int)P->ggram.size(), Plan::kGgChunks, P->rootp,
+                                    P->at<double>(P->ggram_part_off), P->at<double>(P->G_off), s));
+      nk += 2;
+    }
   }
   if (!P->corr.empty()) {
     CUDA_TRY(c, launch_corr(P->arena.base + P->corr_off, (int)P->corr.size(), P->at<double>(P->G_off), P->rootp.m, s));

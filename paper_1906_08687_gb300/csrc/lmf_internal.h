@@ -166,6 +166,24 @@ struct CatViewTask {
   long long* out;
 };
 
+// Gram block of one probe group's view means, taken at the key level: for z
+// slots i, j of the group (i = -1: the constant 1),
+//   G[i][j] = sum over root rows of w z_i z_j = sum over keys k of hist(k) m_i(k) m_j(k)
+// since z_i = m_i(k) on every row with key k (the aggregate evaluated at the
+// group's own root, Sec. 3.3, over the view of counts from the root).  FP64
+// over the keys, in a fixed order: no FP32 rounding repeated over a run of
+// equal keys.
+struct GroupGram {
+  int32_t grp;                       // probe group
+  int32_t rv;                        // reverse view holding hist(k)
+  int32_t n;                         // means of the group (z slots zoff .. zoff + n - 1)
+  int32_t zoff;
+  int32_t mu_word;                   // record word of the first mean
+  int32_t npair;                     // (n + 1)(n + 2)/2 - 1 pairs (i <= j, not both -1)
+  int32_t part_off;                  // first partial of this block: [npair][n_parts]
+  int32_t pad;
+};
+
 struct OmegaAcc {                    // SUM over root rows of w / cnt_e per key of e
   int32_t grp;
   int32_t cnt_word;
@@ -211,6 +229,8 @@ struct RootParams {
   int32_t res_grp;
   int32_t res_cells;
   int32_t unit_w;                    // 1: every w is 0 or 1 (unique child keys)
+  int32_t fold;                      // rows per FP32 chain of the plain Gram before it is
+                                     // folded into the two-float accumulator (0: once per tile)
 };
 
 // answering a grouped aggregate from a reverse view: loop over the group's keys
@@ -262,6 +282,8 @@ cudaError_t launch_rv_tasks(const RvTask* tasks, int n_tasks, const RootParams& 
                             int max_K, cudaStream_t s);
 cudaError_t launch_cv_tasks(const CatViewTask* tasks, int n_tasks, const RootParams& p, int64_t max_cells,
                             cudaStream_t s);
+cudaError_t launch_group_gram(const GroupGram* gg, int n_gg, int n_parts, const RootParams& p, double* part,
+                              double* G, cudaStream_t s);
 cudaError_t launch_out_map(const OutMap* maps, int n_maps, int64_t max_cells, const double* G, int m,
                            const long long* count, long long* res_i64, double* res_f64,
                            cudaStream_t s);

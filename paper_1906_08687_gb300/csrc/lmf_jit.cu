@@ -98,6 +98,7 @@ std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<Dir
     o << "};\n";
   }
   o << "struct JitRowPass {\n"
+    << "  static __device__ __forceinline__ constexpr int fold(const RootParams&) { return " << rp.fold << "; }\n"
        "  template <int MP>\n"
        "  static __device__ __forceinline__ long long run(const RootParams& p, int64_t row, float* zrow, int ldz,\n"
        "                                                  int32_t* crow, uint32_t* cache, uint32_t* res_hist,\n"

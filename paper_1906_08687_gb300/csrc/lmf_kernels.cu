@@ -370,7 +370,9 @@ __global__ void k_rv_tasks(const RvTask* tasks, int n_tasks, const __grid_consta
     long long v;
     if (t.mode == 0) v = static_cast<long long>(h);
     else if (t.mode == 1) v = R.R[(int64_t)k * R.n_slot + t.slot];
-    else v = fixp(static_cast<long long>(h), __uint_as_float(rec[t.mu_word]), t.scale);
+    else  // hist * mean * scale is exact in FP64 (49 bits): one rounding per key
+      v = __double2ll_rn(static_cast<double>(h) * static_cast<double>(__uint_as_float(rec[t.mu_word])) *
+                         static_cast<double>(t.scale));
     add_ll(t.out + cell, v);
   }
 }
@@ -399,6 +401,87 @@ cudaError_t launch_cv_tasks(const CatViewTask* tasks, int n_tasks, const RootPar
   const int64_t gb = (max_cells + 255) / 256;
   dim3 grid((unsigned)(gb < 256 ? (gb < 1 ? 1 : gb) : 256), (unsigned)n_tasks);
   k_cv_tasks<<<grid, 256, 0, s>>>(tasks, p);
+  return cudaGetLastError();
+}
+
+// pair p of a group block: (i, j), -1 <= i <= j < n, not both -1
+__device__ __forceinline__ void gg_pair(int p, int n, int& i, int& j) {
+  i = -1;
+  int row = n;  // pairs with first index i: n - i (i = -1 contributes n: (-1, 0..n-1))
+  while (p >= row) {
+    p -= row;
+    ++i;
+    row = n - i;
+  }
+  j = (i < 0 ? 0 : i) + p;
+}
+
+// partial sums over one range of the keys per warp; lane l takes the pairs
+// l, l + 32, .. (up to kGgLane of them per sweep over the keys)
+constexpr int kGgLane = 4;
+__global__ void k_group_gram_part(const GroupGram* gg, int n_parts, const __grid_constant__ RootParams p,
+                                  double* part) {
+  const GroupGram g = gg[blockIdx.y];
+  const GroupDesc& G = p.grp[g.grp];
+  const unsigned long long* hist = p.rv[g.rv].hist;
+  const int lane = threadIdx.x & 31;
+  const int64_t part_id = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t k0 = part_id * G.K / n_parts, k1 = (part_id + 1) * G.K / n_parts;
+  for (int q0 = 0; q0 < g.npair; q0 += 32 * kGgLane) {
+    int pi[kGgLane], pj[kGgLane];
+    double s[kGgLane];
+#pragma unroll
+    for (int u = 0; u < kGgLane; ++u) {
+      const int q = q0 + lane + 32 * u;
+      pi[u] = -1;
+      pj[u] = 0;
+      if (q < g.npair) gg_pair(q, g.n, pi[u], pj[u]);
+      s[u] = 0.0;
+    }
+#pragma unroll 4
+    for (int64_t k = k0; k < k1; ++k) {
+      const double h = static_cast<double>(hist[k]);
+      const uint32_t* rec = G.rec + k * G.stride + g.mu_word;
+#pragma unroll
+      for (int u = 0; u < kGgLane; ++u) {
+        const double mj = static_cast<double>(__uint_as_float(rec[pj[u]]));
+        const double mi = pi[u] < 0 ? 1.0 : static_cast<double>(__uint_as_float(rec[pi[u]]));
+        s[u] += h * (mi * mj);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kGgLane; ++u) {
+      const int q = q0 + lane + 32 * u;
+      if (q < g.npair) part[static_cast<int64_t>(g.part_off + q) * n_parts + part_id] = s[u];
+    }
+  }
+}
+
+// the partials of each pair summed in a fixed order (one warp per pair); the
+// block replaces the row-level Gram entries
+__global__ void k_group_gram_fin(const GroupGram* gg, int n_parts, const double* part, double* G, int m) {
+  const GroupGram g = gg[blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  for (int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < g.npair; q += gridDim.x * (blockDim.x >> 5)) {
+    const double* src = part + static_cast<int64_t>(g.part_off + q) * n_parts;
+    double s = 0.0;
+    for (int c = lane; c < n_parts; c += 32) s += src[c];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      int i, j;
+      gg_pair(q, g.n, i, j);
+      const int zi = i < 0 ? 0 : g.zoff + i, zj = g.zoff + j;
+      G[zi * m + zj] = s;
+      G[zj * m + zi] = s;
+    }
+  }
+}
+
+cudaError_t launch_group_gram(const GroupGram* gg, int n_gg, int n_parts, const RootParams& p, double* part,
+                              double* G, cudaStream_t s) {
+  if (n_gg <= 0) return cudaSuccess;
+  k_group_gram_part<<<dim3(n_parts / 8, n_gg), 256, 0, s>>>(gg, n_parts, p, part);
+  k_group_gram_fin<<<dim3(16, n_gg), 256, 0, s>>>(gg, n_parts, part, G, p.m);
   return cudaGetLastError();
 }
 

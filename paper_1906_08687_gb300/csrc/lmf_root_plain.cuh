@@ -5,7 +5,7 @@
 // foreign keys, view records, z, w, grouped updates) and writes z (and w*z
 // when w can exceed 1) to shared memory; phase 2 accumulates the upper
 // triangle of sum_r w_r z_r z_r^T in 4x4 register blocks with FP32 FMAs,
-// folded after every tile into a two-float (TwoSum) accumulator; each CTA
+// folded every 8 rows into a two-float (TwoSum) accumulator; each CTA
 // writes its FP64 partial Gram.  The row pass is a policy: GenericRowPass
 // reads the plan's descriptors, a plan-specialised one has them as constants.
 #pragma once
@@ -26,6 +26,7 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
 }
 
 struct GenericRowPass {
+  static __device__ __forceinline__ int fold(const RootParams& p) { return p.fold; }
   template <int MP>
   static __device__ __forceinline__ long long run(const RootParams& p, int64_t row, float* zrow, int ldz,
                                                   int32_t* crow, uint32_t* cache, uint32_t* res_hist,
@@ -94,9 +95,15 @@ __device__ __forceinline__ void root_plain_body(const RootParams& p, int64_t n_t
     __syncthreads();
     // ---------------- phase 2: Gram blocks
     if (active) {
+      // FP32 sums of at most p.fold products, each folded into the two-float
+      // accumulator: on a root sorted on two or more keys consecutive rows
+      // repeat the same cross products, and a long FP32 chain would round
+      // them the same way in every tile
+      const int fold = RowPass::fold(p) > 0 ? RowPass::fold(p) : T;
       float acc[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+      int t = 0;
       for (int r = grow; r < T; r += RG) {
         const float4 a = *reinterpret_cast<const float4*>(Za + r * LD + 4 * bi);
         const float4 b = *reinterpret_cast<const float4*>(Zb + r * LD + 4 * bj);
@@ -106,6 +113,14 @@ __device__ __forceinline__ void root_plain_body(const RootParams& p, int64_t n_t
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fmaf(av[u], bv[v], acc[u * 4 + v]);
+        if (++t == fold) {
+          t = 0;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            two_sum(hi[q], lo[q], acc[q]);
+            acc[q] = 0.f;
+          }
+        }
       }
 #pragma unroll
       for (int q = 0; q < 16; ++q) two_sum(hi[q], lo[q], acc[q]);

@@ -1,6 +1,7 @@
 """Parity at the benchmark sizes under the strict error rule (no arithmetic
-floor): the whole batch runs on the GPU, the oracle re-evaluates a seeded
-sample of its aggregates over the full join."""
+floor): the whole batch runs on the GPU and the oracle evaluates, over the full
+join, every aggregate of the snowflake and Chow-Liu/cube batches and a seeded
+sample of the tree batch."""
 import numpy as np
 import pytest
 
@@ -17,14 +18,25 @@ def _sample(n, k, seed):
     return sorted(set([0] + rng.choice(n, size=min(k, n), replace=False).tolist()))
 
 
-@pytest.mark.parametrize('precision,order', [(0, 'sorted'), (1, 'sorted'), (1, 'random')])
-def test_config2_full_size(precision, order):
-    sch, batch = config2(20_000_000, fact_order=order)
+_C2_CACHE = {}
+
+
+def _config2_full(order):
+    """The 20M-row snowflake and the oracle over all of its 851 aggregates."""
+    if order not in _C2_CACHE:
+        sch, batch = config2(20_000_000, fact_order=order)
+        _C2_CACHE.clear()
+        _C2_CACHE[order] = (sch, batch, oracle.evaluate(sch, batch))
+    return _C2_CACHE[order]
+
+
+@pytest.mark.parametrize('order,precision', [('sorted', 0), ('sorted', 1), ('random', 0), ('random', 1)])
+def test_config2_full_size(order, precision):
+    """Every aggregate of the benchmark batch, both fact orders, both Gram forms."""
+    sch, batch, want = _config2_full(order)
     got, info, eng = run_engine(sch, batch, precision=precision, batching=1)
     assert info['precision'] == precision and info['root_rows'] == 20_000_000
-    idx = _sample(len(batch), 64, 7 + precision)
-    want = oracle.evaluate(sch, [batch[i] for i in idx])
-    fails, stats = compare([got[i] for i in idx], want)
+    fails, stats = compare(got, want)
     assert not fails, (fails[:3], stats)
     eng.close()
 
@@ -37,6 +49,17 @@ def test_config3_full_size():
     want = oracle.evaluate(sch, [batch[i] for i in idx])
     fails, stats = compare([got[i] for i in idx], want)
     assert not fails, (fails[:3], stats)
+    eng.close()
+
+
+def test_config4_full_size_exact():
+    """50M-row Chow-Liu pair counts, marginals and the data cube: every count
+    bit-exact."""
+    sch, batch = config4(50_000_000)
+    got, info, eng = run_engine(sch, batch, precision=0, batching=1)
+    assert info['root_rows'] == 50_000_000
+    fails, stats = compare(got, oracle.evaluate(sch, batch))
+    assert not fails, fails[:3]
     eng.close()
 
 
