@@ -948,6 +948,17 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       else if (g1 >= 0 && (g1 == res_grp || g0 < 0)) x = 1;
       else if (g0 >= 0 && g1 >= 0)
         x = P->groups[RR.groups[g1]].K < P->groups[RR.groups[g0]].K ? 1 : 0;
+      // a view holds K x dom(b) 32-bit counters: keep it within kCvMaxCells
+      // (else try the other key, else the per-row table)
+      auto cells_of = [&](int xx) -> int64_t {
+        const int gx = xx == 0 ? g0 : g1;
+        if (gx < 0) return INT64_MAX;
+        int col, r = owner_of(c, ag.gb[1 - xx], &col);
+        return (int64_t)P->groups[RR.groups[gx]].K * c->rels[r].cols[col].dom;
+      };
+      constexpr int64_t kCvMaxCells = 8 << 20;
+      if (x >= 0 && cells_of(x) > kCvMaxCells) x = cells_of(1 - x) <= kCvMaxCells ? 1 - x : -1;
+      if (Root.nrows >= ((int64_t)1 << 32)) x = -1;
       if (x >= 0) {
         const int gx = x == 0 ? g0 : g1;
         const std::string& bname = ag.gb[1 - x];
@@ -1006,7 +1017,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   }
   for (size_t a = 0; a < B.aggs.size(); ++a)
     if (cls[a].kind == 1) gplan[a].out_off = A.take((size_t)gplan[a].cells * 8);
-  for (auto& v : cvs) v.off = A.take((size_t)P->groups[RR.groups[v.grp]].K * v.dom * 8 + 8);
+  for (auto& v : cvs) v.off = A.take((size_t)P->groups[RR.groups[v.grp]].K * v.dom * 4 + 16);
   // omega accumulators of fanning-out root children
   std::vector<std::pair<int, size_t>> omega;  // child relation, offset
   for (int q = 0; q < rp.n_grp; ++q)
@@ -1408,7 +1419,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     C.dom = cvs[i].dom;
     C.res_off = res_grp >= 0 ? cvs[i].res_off : -1;
     C.runs = has_runs[cvs[i].grp] && cvs[i].bgrp >= 0 && has_runs[cvs[i].bgrp];
-    C.V = P->at<long long>(cvs[i].off);
+    C.V = P->at<uint32_t>(cvs[i].off);
   }
   rp.n_direct = (int)direct.size();
   rp.direct = P->at<DirectAgg>(P->direct_off);

@@ -153,7 +153,7 @@ struct CatView {
   int32_t res_off;                   // grp is the resident group: first of dom shared counters, else -1
   int32_t runs;                      // 1: (key, b) comes in runs (sum them per warp)
   int32_t pad;
-  long long* V;                      // [K of grp][dom]
+  uint32_t* V;                       // [K of grp][dom] counts (w is 0 or 1, fewer than 2^32 rows)
 };
 
 // COUNT table (a, b) read off its category view: for every key k,

@@ -106,21 +106,25 @@ std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<Dir
        "    const int lane = threadIdx.x & 31;\n"
        "#pragma unroll\n"
        "    for (int i = 0; i < MP; i += 4) *reinterpret_cast<float4*>(zrow + i) = make_float4(0.f, 0.f, 0.f, 0.f);\n"
-       "    long long w = 0;\n"
-       "    if (row < p.N) {\n"
+       "    long long w = 0;\n";
+  // the root's columns are read once per launch: streaming loads (evict
+  // first), so they do not push the views the atomics update out of L2
+  for (int g = 0; g < rp.n_grp; ++g) o << "    int32_t fk" << g << " = -1;\n";
+  o << "    if (row < p.N) {\n"
        "      w = 1;\n"
        "      zrow[0] = 1.f;\n";
   for (int i = 0; i < rp.n_x; ++i) {
     if (rp.x[i].dtype == 2)
-      o << "      zrow[" << 1 + i << "] = static_cast<float>(__ldg(static_cast<const double*>(p.x[" << i
+      o << "      zrow[" << 1 + i << "] = static_cast<float>(__ldcs(static_cast<const double*>(p.x[" << i
         << "].p) + row));\n";
     else
-      o << "      zrow[" << 1 + i << "] = __ldg(static_cast<const float*>(p.x[" << i << "].p) + row);\n";
+      o << "      zrow[" << 1 + i << "] = __ldcs(static_cast<const float*>(p.x[" << i << "].p) + row);\n";
   }
   for (int g = 0; g < rp.n_grp; ++g) {
     const GroupDesc& G = rp.grp[g];
     const int nw = G.n_cnt + G.n_mu + G.n_cat;
-    o << "      {\n        const int32_t fk = __ldg(p.grp[" << g << "].fk + row);\n"
+    o << "      {\n        const int32_t fk = __ldcs(p.grp[" << g << "].fk + row);\n"
+      << "        fk" << g << " = fk;\n"
       << "        if (fk < 0 || fk >= " << G.K << ") {\n          w = 0;\n        } else {\n"
       << "          const uint4* rec = reinterpret_cast<const uint4*>(p.grp[" << g
       << "].rec + static_cast<int64_t>(fk) * " << G.stride << ");\n";
@@ -133,7 +137,7 @@ std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<Dir
     o << "        }\n      }\n";
   }
   for (int i = 0; i < rp.n_rcat; ++i) {
-    o << "      {\n        int32_t v = __ldg(p.rcat[" << i << "] + row);\n"
+    o << "      {\n        int32_t v = __ldcs(p.rcat[" << i << "] + row);\n"
       << "        if (v < 0 || v >= " << rp.rcat_dom[i] << ") {\n"
       << "          atomicOr(p.status, kStatusCatRange);\n          v = 0;\n        }\n"
       << "        crow[" << rp.n_rowcat - rp.n_rcat + i << "] = v;\n      }\n";
@@ -144,15 +148,15 @@ std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<Dir
        "    __syncwarp();\n"
        "    const bool live = w != 0;\n";
   if (rp.res_cells > 0)
-    o << "    const long long fres = (live && res_key >= 0) ? static_cast<long long>(__ldg(p.grp[" << rp.res_grp
-      << "].fk + row)) : -2ll;\n";
+    o << "    const long long fres = (live && res_key >= 0) ? static_cast<long long>(fk" << rp.res_grp
+      << ") : -2ll;\n";
   else
     o << "    const long long fres = -2ll;\n";
   // reverse views
   for (int r = 0; r < rp.n_rv; ++r) {
     const RevView& R = rp.rv[r];
     o << "    {  // reverse view " << r << "\n"
-      << "      const long long fk = live ? static_cast<long long>(__ldg(p.grp[" << R.grp << "].fk + row)) : -1ll;\n";
+      << "      const long long fk = live ? static_cast<long long>(fk" << R.grp << ") : -1ll;\n";
     o << "      const WarpRuns q = warp_runs(fk);\n"
       << "      rv_count_runs(q, " << (unit_w ? "true" : "false") << ", fk, w, p.rv[" << r << "].hist);\n";
     for (int s0 = 0; s0 < R.n_slot; s0 += 32) {
@@ -167,17 +171,17 @@ std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<Dir
   for (int v = 0; v < rp.n_cv; ++v) {
     const CatView& C = rp.cv[v];
     o << "    {  // category view " << v << "\n"
-      << "      const long long fk = live ? static_cast<long long>(__ldg(p.grp[" << C.grp << "].fk + row)) : -1ll;\n"
+      << "      const long long fk = live ? static_cast<long long>(fk" << C.grp << ") : -1ll;\n"
       << "      const int b = live ? crow[" << C.bcat << "] : 0;\n";
     if (C.res_off >= 0) {
       o << "      if (res_key >= 0) {\n        if (live) {\n"
         << "          if (fk == res_key) rp_red_shared_u32(res_hist + " << C.res_off << " + b, static_cast<uint32_t>(w));\n"
-        << "          else rp_add_ll(p.cv[" << v << "].V + fk * " << C.dom << " + b, w);\n"
+        << "          else rp_red_u32(p.cv[" << v << "].V + fk * " << C.dom << " + b, static_cast<uint32_t>(w));\n"
         << "        }\n      } else {\n        root_cv_one(p.cv[" << v << "], fk, b, w, res_hist, res_key);\n      }\n";
     } else if (C.runs) {
       o << "      root_cv_one(p.cv[" << v << "], fk, b, w, res_hist, res_key);\n";
     } else {
-      o << "      if (live) rp_add_ll(p.cv[" << v << "].V + fk * " << C.dom << " + b, w);\n";
+      o << "      if (live) rp_red_u32(p.cv[" << v << "].V + fk * " << C.dom << " + b, static_cast<uint32_t>(w));\n";
     }
     o << "    }\n";
   }

@@ -386,7 +386,7 @@ __global__ void k_cv_tasks(const CatViewTask* tasks, const __grid_constant__ Roo
   const GroupDesc& G = p.grp[C.grp];
   const int64_t n = static_cast<int64_t>(G.K) * C.dom;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const long long v = C.V[i];
+    const long long v = static_cast<long long>(C.V[i]);
     if (v == 0) continue;
     const int64_t k = i / C.dom;
     const int b = static_cast<int>(i - k * C.dom);

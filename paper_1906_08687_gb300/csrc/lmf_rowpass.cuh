@@ -22,6 +22,9 @@ __device__ __forceinline__ void rp_red_u64(unsigned long long* p, unsigned long 
 __device__ __forceinline__ void rp_add_ll(long long* p, long long v) {
   rp_red_u64(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
 }
+__device__ __forceinline__ void rp_red_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ void rp_red_shared_u32(uint32_t* p, uint32_t v) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))), "r"(v)
                : "memory");
@@ -167,7 +170,7 @@ __device__ __forceinline__ void root_res_flush(const RootParams& p, uint32_t* hi
       const uint32_t n = hist[C.res_off + i];
       if (n == 0u) continue;
       hist[C.res_off + i] = 0u;
-      rp_red_u64(reinterpret_cast<unsigned long long*>(C.V + k * C.dom + i), n);
+      rp_red_u32(C.V + k * C.dom + i, n);
     }
   }
   const GroupDesc& G = p.grp[p.res_grp];
@@ -323,7 +326,7 @@ __device__ __forceinline__ void root_cv_one(const CatView& C, long long fk, int 
   if (C.res_off >= 0 && res_key >= 0) {  // resident form (warp-uniform branch)
     if (!live) return;
     if (fk == res_key) rp_red_shared_u32(res_hist + C.res_off + b, static_cast<uint32_t>(w));
-    else rp_add_ll(C.V + fk * C.dom + b, w);
+    else rp_red_u32(C.V + fk * C.dom + b, static_cast<uint32_t>(w));
     return;
   }
   const long long cell = live ? fk * C.dom + b : -1ll;
@@ -331,11 +334,11 @@ __device__ __forceinline__ void root_cv_one(const CatView& C, long long fk, int 
     const WarpRuns q = warp_runs(cell);
     if (q.sum) {
       const long long t = warp_run_sum(q, w);
-      if (q.head && live) rp_add_ll(C.V + cell, t);
+      if (q.head && live) rp_red_u32(C.V + cell, static_cast<uint32_t>(t));
       return;
     }
   }
-  if (live) rp_add_ll(C.V + cell, w);
+  if (live) rp_red_u32(C.V + cell, static_cast<uint32_t>(w));
 }
 
 // Grouped updates of the warp's 32 rows; every lane of the warp calls this,
