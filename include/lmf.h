@@ -83,10 +83,18 @@ typedef struct {
   int32_t dtype;          /* LMF_I32 / LMF_F32 / LMF_F64 */
   int32_t role;           /* LMF_KEY / LMF_CONT / LMF_CAT */
   const void* data;       /* nrows elements; device pointer, or pinned host pointer
-                             when on_host = 1 (copied to the device by every lmf_run) */
+                             when on_host is LMF_HOST_COPY or LMF_HOST_MAPPED */
   int32_t cat_domain;     /* LMF_CAT: number of categories */
-  int32_t on_host;        /* 0: device memory (borrowed); 1: host memory */
+  int32_t on_host;        /* LMF_DEVICE, LMF_HOST_COPY or LMF_HOST_MAPPED */
 } lmf_column;
+
+/* lmf_column.on_host */
+#define LMF_DEVICE      0  /* device memory, borrowed */
+#define LMF_HOST_COPY   1  /* pinned host memory, copied to a device staging buffer by every lmf_run */
+#define LMF_HOST_MAPPED 2  /* pinned (mapped) host memory read in place by the kernels over the host
+                              link, no staging copy: for columns the scan streams once (a root's
+                              columns); lmf_register_relation fails with LMF_ERR_ARG when the
+                              pointer is not device-accessible page-locked memory */
 
 typedef struct {
   const char* attr;

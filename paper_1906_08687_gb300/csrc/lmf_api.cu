@@ -37,7 +37,8 @@ struct ColumnH {
   int dtype, role, dom, on_host;
   const void* data;      // user pointer
   void* dev = nullptr;   // device copy of a host column
-  const void* dptr() const { return on_host ? dev : data; }
+  const void* mapped = nullptr;  // LMF_HOST_MAPPED: the device's address of the host data
+  const void* dptr() const { return on_host == LMF_HOST_COPY ? dev : on_host == LMF_HOST_MAPPED ? mapped : data; }
   size_t esize() const { return dtype == LMF_F64 ? 8 : 4; }
 };
 
@@ -310,8 +311,19 @@ lmf_status lmf_register_relation(lmf_ctx* c, const char* name, int64_t nrows, co
     if (!ok) return fail(c, LMF_ERR_DTYPE, "column %s: dtype %d does not fit role %d", s.name, s.dtype, s.role);
     if (s.role == LMF_CAT && s.cat_domain <= 0)
       return fail(c, LMF_ERR_ARG, "column %s: cat_domain must be positive", s.name);
-    ColumnH h{s.name, s.dtype, s.role, s.cat_domain, s.on_host ? 1 : 0, s.data};
-    if (h.on_host && nrows > 0) {
+    if (s.on_host < LMF_DEVICE || s.on_host > LMF_HOST_MAPPED)
+      return fail(c, LMF_ERR_ARG, "column %s: on_host %d", s.name, s.on_host);
+    ColumnH h{s.name, s.dtype, s.role, s.cat_domain, s.on_host, s.data};
+    if (h.on_host == LMF_HOST_MAPPED && nrows > 0) {
+      cudaPointerAttributes at{};
+      if (cudaPointerGetAttributes(&at, s.data) != cudaSuccess || at.type != cudaMemoryTypeHost ||
+          at.devicePointer == nullptr) {
+        cudaGetLastError();
+        return fail(c, LMF_ERR_ARG, "column %s: LMF_HOST_MAPPED needs page-locked, device-mapped host memory", s.name);
+      }
+      h.mapped = at.devicePointer;
+    }
+    if (h.on_host == LMF_HOST_COPY && nrows > 0) {
       if (cudaMalloc(&h.dev, (size_t)nrows * h.esize()) != cudaSuccess)
         return fail(c, LMF_ERR_OOM, "staging buffer for %s", s.name);
       cudaMemcpy(h.dev, h.data, (size_t)nrows * h.esize(), cudaMemcpyHostToDevice);
@@ -1538,7 +1550,7 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
   // host-resident columns are copied in first
   for (auto& r : c->rels)
     for (auto& col : r.cols)
-      if (col.on_host && r.nrows > 0)
+      if (col.on_host == LMF_HOST_COPY && r.nrows > 0)
         CUDA_TRY(c, cudaMemcpyAsync(col.dev, col.data, (size_t)r.nrows * col.esize(), cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemsetAsync(P->arena.base + P->zero_off, 0, P->zero_len, s));
   mark(1);

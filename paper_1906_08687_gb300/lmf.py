@@ -28,6 +28,7 @@ LMF_MAX_GROUP_BY = 3
 LMF_STAGES = 5
 LMF_PLAN_FEATURES = 24
 LMF_PLAN_NO_JIT = 1
+LMF_DEVICE, LMF_HOST_COPY, LMF_HOST_MAPPED = 0, 1, 2
 STAGE_NAMES = ['input', 'views', 'root_scan', 'tree', 'finalize']
 
 _ROLE = {'key': LMF_KEY, 'cont': LMF_CONT, 'cat': LMF_CAT}
@@ -389,21 +390,24 @@ def column_dtype(arr) -> int:
     raise TypeError(f'unsupported column dtype {s}')
 
 
-def register_schema(engine: Engine, schema, tensors: dict, on_host: bool = False) -> None:
+def register_schema(engine: Engine, schema, tensors: dict, on_host=False) -> None:
     """Register every relation of `schema` and its join tree.
 
     schema: object with .relations (each .name, .columns with .name, .role
     ('key'|'cont'|'cat'), .cat_domain), .edges ((parent, child, key)) and
     .root.  tensors[(relation, column)] is the buffer holding that column
     (device tensor, or pinned host tensor when on_host); its .data_ptr() is
-    passed to the C ABI.
+    passed to the C ABI.  on_host: one LMF_DEVICE / LMF_HOST_COPY /
+    LMF_HOST_MAPPED mode (a bool means device / copy) or a dict relation name
+    -> mode.
     """
     for r in schema.relations:
+        mode = on_host.get(r.name, LMF_DEVICE) if isinstance(on_host, dict) else int(on_host)
         cols = []
         for c in r.columns:
             t = tensors[(r.name, c.name)]
             cols.append(dict(name=c.name, dtype=column_dtype(t), role=_ROLE[c.role], data=t.data_ptr(),
-                             cat_domain=int(c.cat_domain), on_host=int(on_host)))
+                             cat_domain=int(c.cat_domain), on_host=mode))
         engine.register_relation(r.name, int(r.nrows), cols)
     ids = engine.rel_ids
     engine.declare_join([(ids[p], ids[c], k) for p, c, k in schema.edges])

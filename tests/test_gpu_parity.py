@@ -193,3 +193,40 @@ def test_plan_compiled_scan_fanout(seed):
     for x, y in zip(got, ref):
         assert np.array_equal(x, y)
     e0.close()
+
+
+def test_host_mapped_root_matches_device():
+    """Root columns read in place from pinned host memory (LMF_HOST_MAPPED),
+    dimensions copied per run (LMF_HOST_COPY): same results as device columns,
+    over two runs (the host data could change between runs)."""
+    from paper_1906_08687_gb300 import Engine, register_schema
+    from paper_1906_08687_gb300.lmf import LMF_HOST_COPY, LMF_HOST_MAPPED
+    from lmf_testlib import to_pinned
+    sch, batch = config2(120_001)
+    ref, _, e0 = run_engine(sch, batch, precision=PLAIN, batching=GRAPH)
+    e0.close()
+    host = to_pinned(sch)
+    eng = Engine(0)
+    register_schema(eng, sch, host, on_host={r.name: (LMF_HOST_MAPPED if r.name == sch.root else LMF_HOST_COPY)
+                                             for r in sch.relations})
+    bid = eng.declare_batch(batch)
+    eng.plan(bid, precision=PLAIN, batching=GRAPH)
+    for _ in range(2):
+        eng.run(bid)
+        eng.sync(bid)
+        got = eng.results(bid, len(batch))
+        for x, y in zip(got, ref):
+            assert np.array_equal(x, y)
+    eng.close()
+
+
+def test_host_mapped_rejects_pageable_memory():
+    from paper_1906_08687_gb300 import Engine, LmfError
+    from paper_1906_08687_gb300.lmf import LMF_HOST_MAPPED, LMF_I32, LMF_KEY
+    a = np.arange(1000, dtype=np.int32)          # pageable numpy memory
+    eng = Engine(0)
+    with pytest.raises(LmfError) as e:
+        eng.register_relation('R', 1000, [dict(name='k', dtype=LMF_I32, role=LMF_KEY, data=a.ctypes.data,
+                                                on_host=LMF_HOST_MAPPED)])
+    assert e.value.status == -1
+    eng.close()
