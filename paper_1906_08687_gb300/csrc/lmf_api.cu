@@ -128,6 +128,7 @@ struct Plan {
   std::map<std::string, int> feat_group;    // feature -> root group owning it (-1 root)
   std::vector<RvTask> rv_tasks;
   std::vector<CatViewTask> cv_tasks;
+  TaskRanges rv_ranges{}, cv_ranges{};
   std::vector<GroupGram> ggram;
   size_t ggram_off = 0, ggram_part_off = 0;
   static constexpr int kGgChunks = 2048;  // key ranges (one warp each) of the key-level Gram
@@ -1421,6 +1422,18 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   if (cache_cells > 0)
     CUDA_TRY(c, cudaMemcpy(P->arena.base + cache_dst_off, cache_dst.data(), sizeof(long long*) * cache_cells,
                            cudaMemcpyHostToDevice));
+  // tasks grouped by their view: one pass over a view serves all of them
+  auto group_by_view = [](auto& v, int n_views, auto view_of, TaskRanges* rg) {
+    std::stable_sort(v.begin(), v.end(), [&](const auto& a, const auto& b) { return view_of(a) < view_of(b); });
+    rg->n_views = n_views;
+    int t = 0;
+    for (int i = 0; i <= n_views; ++i) {
+      while (t < (int)v.size() && view_of(v[t]) < i) ++t;
+      rg->begin[i] = t;
+    }
+  };
+  group_by_view(tasks, rp.n_rv, [](const RvTask& t) { return t.rv; }, &P->rv_ranges);
+  group_by_view(P->cv_tasks, (int)cvs.size(), [](const CatViewTask& t) { return t.view; }, &P->cv_ranges);
   P->rv_tasks = tasks;
   P->direct = direct;
   rp.n_cv = (int)cvs.size();
@@ -1680,12 +1693,11 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
     ++nk;
   }
   if (!P->rv_tasks.empty()) {
-    CUDA_TRY(c, launch_rv_tasks(P->at<RvTask>(P->rvtask_off), (int)P->rv_tasks.size(), P->rootp, P->max_group_K, s));
+    CUDA_TRY(c, launch_rv_tasks(P->at<RvTask>(P->rvtask_off), P->rv_ranges, P->rootp, P->max_group_K, s));
     ++nk;
   }
   if (!P->cv_tasks.empty()) {
-    CUDA_TRY(c, launch_cv_tasks(P->at<CatViewTask>(P->cvtask_off), (int)P->cv_tasks.size(), P->rootp,
-                                P->cv_max_cells, s));
+    CUDA_TRY(c, launch_cv_tasks(P->at<CatViewTask>(P->cvtask_off), P->cv_ranges, P->rootp, P->cv_max_cells, s));
     ++nk;
   }
   if (!P->maps.empty()) {

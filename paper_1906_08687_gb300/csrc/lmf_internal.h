@@ -278,9 +278,14 @@ int root_plain_tile_rows();
 cudaError_t launch_combine(const double* part, int grid, int mp, int m, const long long* cnt_part,
                            double* G, long long* count, cudaStream_t s);
 cudaError_t launch_corr(const void* tasks_dev, int n, double* G, int m, cudaStream_t s);
-cudaError_t launch_rv_tasks(const RvTask* tasks, int n_tasks, const RootParams& p,
+// tasks sorted by their view; view v owns tasks [begin[v], begin[v + 1])
+struct TaskRanges {
+  int32_t n_views;
+  int32_t begin[kMaxCatViews + 1];
+};
+cudaError_t launch_rv_tasks(const RvTask* tasks, const TaskRanges& rg, const RootParams& p,
                             int max_K, cudaStream_t s);
-cudaError_t launch_cv_tasks(const CatViewTask* tasks, int n_tasks, const RootParams& p, int64_t max_cells,
+cudaError_t launch_cv_tasks(const CatViewTask* tasks, const TaskRanges& rg, const RootParams& p, int64_t max_cells,
                             cudaStream_t s);
 cudaError_t launch_group_gram(const GroupGram* gg, int n_gg, int n_parts, const RootParams& p, double* part,
                               double* G, cudaStream_t s);

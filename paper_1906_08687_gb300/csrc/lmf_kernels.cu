@@ -356,51 +356,63 @@ cudaError_t launch_corr(const void* tasks_dev, int n, double* G, int m, cudaStre
   return cudaGetLastError();
 }
 
-// grouped aggregates answered from a reverse view: one pass over the group's keys
-__global__ void k_rv_tasks(const RvTask* tasks, int n_tasks, const __grid_constant__ RootParams p) {
-  const RvTask t = tasks[blockIdx.y];
-  const RevView& R = p.rv[t.rv];
+// grouped aggregates answered from a reverse view: one pass over the group's
+// keys, every task of the view served from the key's record and slots
+__global__ void k_rv_tasks(const RvTask* tasks, const TaskRanges rg, const __grid_constant__ RootParams p) {
+  const int r = blockIdx.y;
+  const int t0 = rg.begin[r], t1 = rg.begin[r + 1];
+  if (t0 == t1) return;
+  const RevView& R = p.rv[r];
   const GroupDesc& G = p.grp[R.grp];
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G.K; k += gridDim.x * blockDim.x) {
     const unsigned long long h = R.hist[k];
     if (h == 0) continue;
     const uint32_t* rec = G.rec + (int64_t)k * G.stride;
-    int64_t cell = 0;
-    for (int q = 0; q < t.n_gb; ++q) cell = cell * t.dom[q] + static_cast<int32_t>(rec[t.cat_word[q]]);
-    long long v;
-    if (t.mode == 0) v = static_cast<long long>(h);
-    else if (t.mode == 1) v = R.R[(int64_t)k * R.n_slot + t.slot];
-    else  // hist * mean * scale is exact in FP64 (49 bits): one rounding per key
-      v = __double2ll_rn(static_cast<double>(h) * static_cast<double>(__uint_as_float(rec[t.mu_word])) *
-                         static_cast<double>(t.scale));
-    add_ll(t.out + cell, v);
+    for (int ti = t0; ti < t1; ++ti) {
+      const RvTask& t = tasks[ti];
+      int64_t cell = 0;
+      for (int q = 0; q < t.n_gb; ++q) cell = cell * t.dom[q] + static_cast<int32_t>(rec[t.cat_word[q]]);
+      long long v;
+      if (t.mode == 0) v = static_cast<long long>(h);
+      else if (t.mode == 1) v = R.R[(int64_t)k * R.n_slot + t.slot];
+      else  // hist * mean * scale is exact in FP64 (49 bits): one rounding per key
+        v = __double2ll_rn(static_cast<double>(h) * static_cast<double>(__uint_as_float(rec[t.mu_word])) *
+                           static_cast<double>(t.scale));
+      add_ll(t.out + cell, v);
+    }
   }
 }
 
-// COUNT tables read off category views: one pass over each view's cells;
-// consecutive threads take consecutive b values of one key, so the table
-// updates of a warp fall on one row of the table
-__global__ void k_cv_tasks(const CatViewTask* tasks, const __grid_constant__ RootParams p) {
-  const CatViewTask t = tasks[blockIdx.y];
-  const CatView& C = p.cv[t.view];
+// COUNT tables read off category views: one pass over each view's cells,
+// every table of the view updated from the same cell (the view read once)
+__global__ void k_cv_tasks(const CatViewTask* tasks, const TaskRanges rg, const __grid_constant__ RootParams p) {
+  const int v = blockIdx.y;
+  const int t0 = rg.begin[v], t1 = rg.begin[v + 1];
+  if (t0 == t1) return;
+  const CatView& C = p.cv[v];
   const GroupDesc& G = p.grp[C.grp];
   const int64_t n = static_cast<int64_t>(G.K) * C.dom;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const long long v = static_cast<long long>(C.V[i]);
-    if (v == 0) continue;
+    const long long val = static_cast<long long>(C.V[i]);
+    if (val == 0) continue;
     const int64_t k = i / C.dom;
     const int b = static_cast<int>(i - k * C.dom);
-    const int a = static_cast<int32_t>(G.rec[k * G.stride + t.a_word]);
-    add_ll(t.out + (t.a_first ? static_cast<int64_t>(a) * C.dom + b : static_cast<int64_t>(b) * t.dom_a + a), v);
+    const uint32_t* rec = G.rec + k * G.stride;
+    for (int t = t0; t < t1; ++t) {
+      const CatViewTask& T = tasks[t];
+      const int a = static_cast<int32_t>(rec[T.a_word]);
+      add_ll(T.out + (T.a_first ? static_cast<int64_t>(a) * C.dom + b : static_cast<int64_t>(b) * T.dom_a + a),
+             val);
+    }
   }
 }
 
-cudaError_t launch_cv_tasks(const CatViewTask* tasks, int n_tasks, const RootParams& p, int64_t max_cells,
+cudaError_t launch_cv_tasks(const CatViewTask* tasks, const TaskRanges& rg, const RootParams& p, int64_t max_cells,
                             cudaStream_t s) {
-  if (n_tasks <= 0) return cudaSuccess;
+  if (rg.n_views <= 0) return cudaSuccess;
   const int64_t gb = (max_cells + 255) / 256;
-  dim3 grid((unsigned)(gb < 256 ? (gb < 1 ? 1 : gb) : 256), (unsigned)n_tasks);
-  k_cv_tasks<<<grid, 256, 0, s>>>(tasks, p);
+  dim3 grid((unsigned)(gb < 1024 ? (gb < 1 ? 1 : gb) : 1024), (unsigned)rg.n_views);
+  k_cv_tasks<<<grid, 256, 0, s>>>(tasks, rg, p);
   return cudaGetLastError();
 }
 
@@ -485,11 +497,11 @@ cudaError_t launch_group_gram(const GroupGram* gg, int n_gg, int n_parts, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_rv_tasks(const RvTask* tasks, int n_tasks, const RootParams& p, int max_K,
+cudaError_t launch_rv_tasks(const RvTask* tasks, const TaskRanges& rg, const RootParams& p, int max_K,
                             cudaStream_t s) {
-  if (n_tasks <= 0) return cudaSuccess;
-  dim3 grid((unsigned)min((max_K + 255) / 256, 64), (unsigned)n_tasks);
-  k_rv_tasks<<<grid, 256, 0, s>>>(tasks, n_tasks, p);
+  if (rg.n_views <= 0) return cudaSuccess;
+  dim3 grid((unsigned)min((max_K + 255) / 256, 512), (unsigned)rg.n_views);
+  k_rv_tasks<<<grid, 256, 0, s>>>(tasks, rg, p);
   return cudaGetLastError();
 }
 
