@@ -13,6 +13,12 @@ placement) with the inputs resident in HBM.  Metric: joined tuples x
 aggregates / step time, in G joined-tuple-aggregates/s.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload snowflake|tree|chowliu|star]
+
+The default workload is the snowflake batch above; --workload selects the
+other batches of the same engine (the regression-tree level batch, the
+Chow-Liu pair counts with a data cube, the star covar batch) at their own
+sizes, reported in the same JSON form.
 
 Under torchrun (N > 1) every rank runs its own seeded instance (weak scaling,
 no collective on the data path); rank 0 prints one JSON line.
@@ -34,8 +40,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = 'G joined-tuple-aggregates/s, HBM % of peak; speedup vs plain at ≤1e-6 rel err'
 UNIT = 'G joined-tuple-aggregates/s'
-PROFILE_SUMMARY = os.path.join(ROOT, 'profiles', 'root_scan_snowflake20M.md')
-KERNEL_SOURCES = ['paper_1906_08687_gb300/csrc/lmf_kernels.cu',
+# workload -> (generator, config index, fact rows, CPU-baseline rows, reference-arm rows per step,
+# aggregates checked by the oracle (-1: all), ncu summary in profiles/)
+WORKLOADS = {
+    'snowflake': ('config2', 2, 20_000_000, 10_000_000, 200_000, -1, 'root_scan_snowflake20M.md'),
+    'tree': ('config3', 3, 10_000_000, 100_000, 20_000, 300, 'tree_level_10M.md'),
+    'chowliu': ('config4', 4, 50_000_000, 20_000_000, 500_000, -1, 'pair_counts_chowliu50M.md'),
+    'star': ('config1', 1, 200_000, 200_000, 200_000, -1, 'star_covar200k.md'),
+}
+KERNEL_SOURCES = ['paper_1906_08687_gb300/csrc/lmf_tree.cu',
+                  'paper_1906_08687_gb300/csrc/lmf_kernels.cu',
                   'paper_1906_08687_gb300/csrc/lmf_gram_tc.cu',
                   'paper_1906_08687_gb300/csrc/lmf_rowpass.cuh',
                   'paper_1906_08687_gb300/csrc/lmf_root_plain.cuh',
@@ -49,19 +63,35 @@ def parse():
     ap.add_argument('--steps', type=int, default=20)
     ap.add_argument('--warmup', type=int, default=5)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
-    ap.add_argument('--n-fact', type=int, default=20_000_000)
+    ap.add_argument('--workload', default='snowflake', choices=sorted(WORKLOADS))
+    ap.add_argument('--n-fact', type=int, default=None, help='fact rows (default: the workload\'s)')
     ap.add_argument('--precision', default='auto', choices=['auto', 'split', 'plain'],
                     help='Gram precision of the chosen plan; auto times both candidates '
                          '(split-bf16 tensor cores, FP32 CUDA cores) and keeps the faster')
     ap.add_argument('--fact-order', default='sorted', choices=['sorted', 'random'],
                     help='fact rows sorted by their join attributes (the input order of the '
                          "paper's experiments) or in generation order")
-    ap.add_argument('--cpu-sample-rows', type=int, default=10_000_000)
-    ap.add_argument('--ref-sample-rows', type=int, default=200_000)
-    ap.add_argument('--check-aggs', type=int, default=-1,
+    ap.add_argument('--cpu-sample-rows', type=int, default=None)
+    ap.add_argument('--ref-sample-rows', type=int, default=None)
+    ap.add_argument('--check-aggs', type=int, default=None,
                     help='aggregates re-evaluated by the oracle over the full join (0: skip, -1: all)')
     ap.add_argument('--no-cpu-baseline', action='store_true')
-    return ap.parse_args()
+    args = ap.parse_args()
+    gen, idx, n, cpu_rows, ref_rows, check, prof = WORKLOADS[args.workload]
+    args.gen, args.cfg_index, args.profile = gen, idx, os.path.join(ROOT, 'profiles', prof)
+    args.n_fact = n if args.n_fact is None else args.n_fact
+    args.cpu_sample_rows = cpu_rows if args.cpu_sample_rows is None else args.cpu_sample_rows
+    args.ref_sample_rows = ref_rows if args.ref_sample_rows is None else args.ref_sample_rows
+    args.check_aggs = check if args.check_aggs is None else args.check_aggs
+    return args
+
+
+def make_workload(args, rank=0):
+    """The seeded schema and batch of the selected workload (rank r: seed + 1000 r)."""
+    import workloads
+    from workloads import SEED_BASE
+    return getattr(workloads, args.gen)(args.n_fact, seed=SEED_BASE + args.cfg_index + 1000 * rank,
+                                        fact_order=args.fact_order)
 
 
 # ----------------------------------------------------------------------------
@@ -148,12 +178,12 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(precision: str):
-    """DRAM bytes per root-scan launch from the committed ncu summary, when it
-    was taken on the current kernel sources (else None)."""
-    if not os.path.exists(PROFILE_SUMMARY):
+def profiled_traffic(precision: str, summary: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, when it was taken on the current kernel sources (else None)."""
+    if not os.path.exists(summary):
         return None
-    with open(PROFILE_SUMMARY) as f:
+    with open(summary) as f:
         text = f.read()
     m = re.search(rf'traffic_bytes_per_launch\[{precision}\]:\s*([0-9.e+]+)\s+sources:\s*([0-9a-f]+)', text)
     if not m or m.group(2) != kernel_hash():
@@ -165,6 +195,14 @@ FACT_ORDER_SORTED = ('sorted by the join attributes, fewest distinct values firs
                      'the scan order of Sec. 3.5, as the paper\'s experiments load every relation')
 
 
+WORKLOAD_TEXT = {
+    'snowflake': '{name} (3 FKs, 8 fact + 22 dimension features, 10 categoricals; covar + grouped + pair counts)',
+    'tree': '{name} (64 tree nodes x 20 features x <=32 thresholds x COUNT/SUM(y)/SUM(y^2))',
+    'chowliu': '{name} (4 FKs, 30 categoricals; 435 pair counts, 30 marginals, 3-attribute cube)',
+    'star': '{name} (2 FKs, 10 FP64 features; COUNT + all degree <= 2 monomials)',
+}
+
+
 # ----------------------------------------------------------------------------
 def run_reference(args):
     """The oracle on this host's cores, one bounded sample of the workload per step."""
@@ -172,9 +210,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     from oracle import oracle
-    from workloads import config2
     oracle.build()
-    sch, batch = config2(args.n_fact, fact_order=args.fact_order)
+    sch, batch = make_workload(args)
     S = min(args.ref_sample_rows, args.n_fact)
     nt = oracle.max_threads()
     times = []
@@ -193,7 +230,7 @@ def run_reference(args):
         'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': ws,
         'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': t * 1e3, 'higher_is_better': True,
         'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
-        'config': {'workload': f'snowflake-{args.n_fact}', 'n_aggregates': len(batch),
+        'config': {'workload': sch.meta['name'], 'n_aggregates': len(batch),
                    'fact_order': args.fact_order, 'sample_rows_per_step': S},
         'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': nt, 'kind': 'oracle', 'sample': sample},
         'e2e': {'value': value, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
@@ -219,10 +256,9 @@ def main():
     engine_build.build()
     from paper_1906_08687_gb300 import Engine, register_schema
     from paper_1906_08687_gb300.lmf import STAGE_NAMES
-    from workloads import config2, SEED_BASE
     from lmf_testlib import compare, to_device, to_pinned
 
-    sch, batch = config2(args.n_fact, seed=SEED_BASE + 2 + 1000 * rank, fact_order=args.fact_order)
+    sch, batch = make_workload(args, rank)
     n_agg = len(batch)
     dev = to_device(sch, f'cuda:{local}')
     stream = torch.cuda.Stream()
@@ -285,7 +321,9 @@ def main():
     for _ in range(args.steps):
         stage += np.array(eng.run_profiled(bid, sh))
     stage /= args.steps
-    root_ms = float(stage[STAGE_NAMES.index('root_scan')])
+    # the dominant stage: the root scan, or the tree pass for filtered batches
+    dom_stage = max(('root_scan', 'tree'), key=lambda n: stage[STAGE_NAMES.index(n)])
+    root_ms = float(stage[STAGE_NAMES.index(dom_stage)])
 
     # results of the chosen form for the accuracy check
     got = eng.results(bid, n_agg)
@@ -339,8 +377,8 @@ def main():
     peaks = measured_peaks()
     achieved = algo / (root_ms * 1e-3) / 1e9
     roof = {'bound': 'hbm', 'achieved': achieved, 'peak': peaks['hbm_gbs'], 'unit': 'GB/s',
-            'frac': achieved / peaks['hbm_gbs'], 'traffic': profiled_traffic(chosen),
-            'peak_source': peaks['source'], 'kernel': 'root scan (stage root_scan)',
+            'frac': achieved / peaks['hbm_gbs'], 'traffic': profiled_traffic(chosen, args.profile),
+            'peak_source': peaks['source'], 'kernel': f'{dom_stage} stage',
             'algorithmic_bytes_per_launch': algo, 'launch_ms': root_ms,
             'stage_ms': {n: float(v) for n, v in zip(STAGE_NAMES, stage)}}
 
@@ -350,8 +388,7 @@ def main():
         'vs_baseline': None,
         'dtype': 'bf16-split3/f32-acc' if info['precision'] == 1 else 'f32',
         'data': 'synthetic',
-        'config': {'workload': f'snowflake-{args.n_fact} (3 FKs, 8 fact + 22 dimension features, '
-                               f'10 categoricals; covar + grouped + pair counts)',
+        'config': {'workload': WORKLOAD_TEXT.get(args.workload, '{name}').format(name=sch.meta['name']),
                    'n_aggregates': n_agg, 'join_rows': join_rows, 'precision': info['precision'],
                    'plan': {'gram': 'split-bf16 tcgen05' if prec == 1 else 'FP32 CUDA cores (TwoSum)',
                             'root_scan_compiled': bool(info['jit']),
