@@ -290,6 +290,13 @@ __device__ __forceinline__ void rv_slot_runs(const WarpRuns& q, bool unit_w, lon
                                              const float* zw, int ldz, bool slot, int zi, float sc, long long* R,
                                              int n_slot, int s) {
   long long acc = 0;
+  if (unit_w && q.heads == 1u) {  // one run over the whole warp (warp-uniform): one reduction
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) acc += __float2ll_rn(zw[j * ldz + zi] * sc);
+    const long long k0 = __shfl_sync(kFullWarp, fk, 0);
+    if (slot && k0 >= 0 && acc != 0) rp_add_ll(R + k0 * n_slot + s, acc);
+    return;
+  }
 #pragma unroll 4
   for (int j = 0; j < 32; ++j) {
     if (unit_w) {  // w is 0 or 1 and z is zero for dead rows
