@@ -1214,6 +1214,11 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   P->smem = root_plain_smem(mp, ncat, cache_cells, res_cells, P->unique_all);
   int cps = P->opts.ctas_per_sm > 0 ? P->opts.ctas_per_sm : (P->smem <= 110 * 1024 ? 2 : 1);
   P->grid = (int)std::max<int64_t>(1, std::min<int64_t>(P->n_tiles, (int64_t)c->num_sms * cps));
+  // the compiled scan is built for three CTAs per SM (its launch bounds cap the
+  // registers) when its shared memory allows a third one
+  const bool jit3 = P->opts.ctas_per_sm <= 0 && P->smem <= 74 * 1024;
+  const int grid_jit =
+      jit3 ? (int)std::max<int64_t>(1, std::min<int64_t>(P->n_tiles, (int64_t)c->num_sms * 3)) : P->grid;
   CUDA_TRY(c, root_plain_prepare(mp, P->smem));
   // the split-bf16 tensor-core Gram needs w in {0, 1} (unique child keys) and
   // z within one 32-feature block; other plans keep the plain FP32 Gram
@@ -1225,8 +1230,9 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     CUDA_TRY(c, gram_tc_configure(P->tc.get(), ncat, P->opts.ctas_per_sm, cache_cells, res_cells));
     P->grid = P->tc->grid;
   }
-  P->part_off = A.take((size_t)P->grid * mp * mp * 8);
-  P->cntp_off = A.take((size_t)P->grid * 8);
+  const int grid_max = std::max(P->grid, grid_jit);
+  P->part_off = A.take((size_t)grid_max * mp * mp * 8);
+  P->cntp_off = A.take((size_t)grid_max * 8);
   P->G_off = A.take((size_t)m * m * 8);
   P->count_off = A.take(8);
   if (use_tc) gram_tc_alloc(P->tc.get(), [&](size_t n) { return A.take(n); });
@@ -1534,10 +1540,11 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   if (!use_tc && !(P->opts.flags & LMF_PLAN_NO_JIT) && Root.nrows > 0 && jit_available()) {
     std::string log;
     cudaKernel_t k = nullptr;
-    if (jit_kernel(jit_plain_source(rp, P->mp, direct), "lmf_root_plain_jit", &k, &log)) {
+    if (jit_kernel(jit_plain_source(rp, P->mp, direct, jit3 ? 3 : 1), "lmf_root_plain_jit", &k, &log)) {
       CUDA_TRY(c, cudaFuncSetAttribute(reinterpret_cast<const void*>(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(P->smem)));
       P->jit_plain = k;
+      P->grid = grid_jit;
     } else {
       std::fprintf(stderr, "lmf: plan-time compile failed, interpreted root scan kept: %.400s\n", log.c_str());
     }

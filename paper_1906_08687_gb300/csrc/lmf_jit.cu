@@ -82,7 +82,7 @@ void gen_record_word(std::ostringstream& o, const RootParams& rp, int g, int wd,
 
 bool jit_available() { return nvrtc().ok; }
 
-std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<DirectAgg>& direct) {
+std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<DirectAgg>& direct, int min_ctas) {
   std::ostringstream o;
   const bool unit_w = rp.unit_w != 0;
   o << "// plan-specialised root scan (generated)\n#include \"lmf_root_plain.cuh\"\nnamespace lmf {\n";
@@ -239,7 +239,7 @@ std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<Dir
          "      }\n    }\n";
   }
   o << "    (void)lane;\n    (void)fres;\n    return w;\n  }\n};\n}  // namespace lmf\n"
-    << "extern \"C\" __global__ void __launch_bounds__(256) lmf_root_plain_jit(const __grid_constant__ "
+    << "extern \"C\" __global__ void __launch_bounds__(256, " << min_ctas << ") lmf_root_plain_jit(const __grid_constant__ "
        "lmf::RootParams p, int64_t n_tiles) {\n"
     << "  lmf::root_plain_body<" << mp << ", lmf::JitRowPass>(p, n_tiles);\n}\n";
   return o.str();

@@ -22,8 +22,9 @@ bool jit_available();
 // CUDA source of the plain root scan for a plan: rp carries the plan's
 // constants (its device pointers are read from the kernel parameter at run
 // time, so plans of the same shape share the source), direct all of its
-// per-row tables.  The kernel is named lmf_root_plain_jit.
-std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<DirectAgg>& direct);
+// per-row tables; min_ctas the CTAs per SM its launch bounds ask for.  The
+// kernel is named lmf_root_plain_jit.
+std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<DirectAgg>& direct, int min_ctas);
 
 // compiles src for sm_103a, or finds it in the process-wide cache of compiled
 // sources; on failure returns false with NVRTC's log in *log
