@@ -361,6 +361,19 @@ lmf_status lmf_plan_learned(lmf_ctx* ctx, int batch_id, lmf_mlp* model, const lm
 lmf_status lmf_gram_noalloc(const float* const* dev_cols, int ncols, int64_t nrows, double* dev_gram,
                             void* cuda_stream);
 
+/*
+ * Failure-detection check (no counterpart in the paper).  Every device wait of
+ * the engine is bounded: the tensor-core root scan waits on an mbarrier for
+ * its MMAs, and after a fixed number of polls (about 0.3 s) it stops waiting,
+ * sets the timeout bit of the plan's status word and returns, so that lmf_sync
+ * reports LMF_ERR_TIMEOUT and the context stays usable.  This call runs that
+ * same bounded wait on a barrier nothing ever arrives at, on ctx's device and
+ * stream, and reads the status back: it returns LMF_ERR_TIMEOUT when the wait
+ * gave up and reported it (the expected result), LMF_OK if the wait
+ * completed, LMF_ERR_CUDA on a CUDA failure.  Synchronous; allocates one word.
+ */
+lmf_status lmf_wait_selftest(lmf_ctx* ctx);
+
 /* Static text of a status code. */
 const char* lmf_status_string(lmf_status s);
 

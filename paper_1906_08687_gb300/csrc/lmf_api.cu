@@ -1828,6 +1828,22 @@ lmf_status lmf_run_profiled(lmf_ctx* c, int batch_id, void* cuda_stream, float* 
   return st;
 }
 
+lmf_status lmf_wait_selftest(lmf_ctx* c) {
+  if (!c) return LMF_ERR_ARG;
+  cudaSetDevice(c->device);
+  uint32_t* d = nullptr;
+  CUDA_TRY(c, cudaMalloc(&d, sizeof(uint32_t)));
+  uint32_t st = 0;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(uint32_t), c->stream);
+  if (e == cudaSuccess) e = gram_tc_wait_selftest(d, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, d, sizeof(st), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(c, LMF_ERR_CUDA, "wait self-test: %s", cudaGetErrorString(e));
+  if (st & kStatusTimeout) return fail(c, LMF_ERR_TIMEOUT, "the bounded wait gave up (as expected)");
+  return LMF_OK;
+}
+
 lmf_status lmf_sync(lmf_ctx* c, int batch_id) {
   if (!c || batch_id < 0 || batch_id >= (int)c->batches.size()) return fail(c, LMF_ERR_ARG, "sync: bad batch id");
   BatchH& B = *c->batches[batch_id];

@@ -162,6 +162,16 @@ __device__ __forceinline__ void pack_row(unsigned char* sA, unsigned char* sB, c
   }
 }
 
+// one thread waits, bounded, on a fresh mbarrier that nothing arrives at
+__global__ void k_wait_selftest(uint32_t* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = smem_u32(&bar);
+  mbar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait(b, 0)) atomicOr(status, kStatusTimeout);
+}
+
 struct TcLayout {
   uint32_t z_off, c_off, cache_off, bar_off, slot_off, cred_off, total;
 };
@@ -353,6 +363,11 @@ cudaError_t gram_tc_configure(GramTcPlan* tp, int n_rowcat, int ctas_per_sm, int
 }
 
 void gram_tc_finish(GramTcPlan* tp, RootParams& /*rp*/, char* base) { tp->part = reinterpret_cast<double*>(base + tp->part_off); }
+
+cudaError_t gram_tc_wait_selftest(uint32_t* status, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(status);
+  return cudaGetLastError();
+}
 
 cudaError_t gram_tc_launch(GramTcPlan* tp, const RootParams& rp, cudaStream_t s) {
   k_root_tc<<<tp->grid, kTcThreads, tp->smem, s>>>(rp, tp->n_tiles, tp->part);

@@ -29,6 +29,9 @@ cudaError_t gram_tc_configure(GramTcPlan* tp, int n_rowcat, int ctas_per_sm, int
 void gram_tc_alloc(GramTcPlan* tp, const std::function<size_t(size_t)>& take);
 void gram_tc_finish(GramTcPlan* tp, RootParams& rp, char* base);
 cudaError_t gram_tc_launch(GramTcPlan* tp, const RootParams& rp, cudaStream_t s);
+// the bounded mbarrier wait of k_root_tc against a barrier nothing arrives at;
+// sets kStatusTimeout in *status when it gives up
+cudaError_t gram_tc_wait_selftest(uint32_t* status, cudaStream_t s);
 // ordered FP64 combine of the per-CTA blocks into G (m x m) and the count
 cudaError_t gram_tc_combine(GramTcPlan* tp, const RootParams& rp, double* G, long long* count, cudaStream_t s);
 

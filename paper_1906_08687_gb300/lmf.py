@@ -110,6 +110,7 @@ _SIGNATURES = {
     'lmf_mlp_grad': (_I, [_P, _P, _P, _I, _P, ctypes.POINTER(ctypes.c_float)]),
     'lmf_mlp_train_step': (_I, [_P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
     'lmf_gram_noalloc': (_I, [ctypes.POINTER(ctypes.c_void_p), _I, ctypes.c_int64, _P, _P]),
+    'lmf_wait_selftest': (_I, [_P]),
     'lmf_status_string': (ctypes.c_char_p, [_I]),
     'lmf_error_message': (ctypes.c_char_p, [_P]),
 }
@@ -273,6 +274,11 @@ class Engine:
     def read_result(self, batch: int, agg: int, dst: int):
         self._check(self.lib.lmf_read_result(self.ctx, batch, agg, ctypes.c_void_p(dst)),
                     'lmf_read_result')
+
+    def wait_selftest(self) -> int:
+        """Status of lmf_wait_selftest: LMF_ERR_TIMEOUT when the bounded device
+        wait gave up and reported it (expected)."""
+        return int(self.lib.lmf_wait_selftest(self.ctx))
 
     def plan_opts(self, batch: int, opts: 'lmf_plan_opts'):
         self._check(self.lib.lmf_plan(self.ctx, batch, ctypes.byref(opts)), 'lmf_plan')
