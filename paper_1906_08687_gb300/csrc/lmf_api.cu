@@ -143,8 +143,8 @@ struct Plan {
   std::unique_ptr<TreePlan> tree;
   // tensor-core Gram
   std::unique_ptr<GramTcPlan> tc;
-  // plain root scan compiled for this plan (null: the interpreted kernel)
-  cudaKernel_t jit_plain = nullptr;
+  // root scan compiled for this plan (null: the interpreted kernel)
+  cudaKernel_t jit_plain = nullptr, jit_tc = nullptr;
   // results
   int64_t n_i64 = 0, n_f64 = 0;
   size_t res_i64_off = 0, res_f64_off = 0;
@@ -1537,6 +1537,17 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   // the compilation step (Sec. 1.2, App. C): the plain root scan with this
   // plan's layout as constants; the interpreted kernel stays when NVRTC is
   // missing or the compile fails (same arithmetic, same results)
+  if (use_tc && !(P->opts.flags & LMF_PLAN_NO_JIT) && Root.nrows > 0 && jit_available()) {
+    std::string log;
+    cudaKernel_t k = nullptr;
+    if (jit_kernel(jit_tc_source(rp, direct), "lmf_root_tc_jit", &k, &log)) {
+      CUDA_TRY(c, cudaFuncSetAttribute(reinterpret_cast<const void*>(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(P->tc->smem)));
+      P->jit_tc = k;
+    } else {
+      std::fprintf(stderr, "lmf: plan-time compile failed, interpreted root scan kept: %.400s\n", log.c_str());
+    }
+  }
   if (!use_tc && !(P->opts.flags & LMF_PLAN_NO_JIT) && Root.nrows > 0 && jit_available()) {
     std::string log;
     cudaKernel_t k = nullptr;
@@ -1662,7 +1673,11 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
   // root scan: Gram, counts, reverse views, per-row grouped tables (skipped when
   // the batch has only threshold-filtered aggregates)
   if (P->root_scan) {
-    if (P->tc) {
+    if (P->tc && P->jit_tc) {
+      void* args[] = {&P->rootp, &P->tc->n_tiles, &P->tc->part};
+      CUDA_TRY(c, cudaLaunchKernel(reinterpret_cast<const void*>(P->jit_tc), dim3(P->tc->grid), dim3(128), args,
+                                   P->tc->smem, s));
+    } else if (P->tc) {
       CUDA_TRY(c, gram_tc_launch(P->tc.get(), P->rootp, s));
     } else {
       if (P->jit_plain) {
@@ -1768,7 +1783,7 @@ lmf_status lmf_plan_info(lmf_ctx* c, int batch_id, lmf_plan_stats* info) {
   info->scratch_bytes = (int64_t)P->arena.size;
   info->resident_group = P->rootp.res_cells > 0 ? P->rootp.res_grp : -1;
   info->resident_cells = P->rootp.res_cells;
-  info->jit = P->jit_plain ? 1 : 0;
+  info->jit = (P->jit_plain || P->jit_tc) ? 1 : 0;
   return LMF_OK;
 }
 

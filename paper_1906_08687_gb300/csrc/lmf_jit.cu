@@ -12,7 +12,8 @@
 #include <sstream>
 
 // the device headers the generated source includes, as text (written by the
-// build from lmf_internal.h, lmf_rowpass.cuh and lmf_root_plain.cuh)
+// build from lmf_internal.h, lmf_rowpass.cuh, lmf_root_plain.cuh and
+// lmf_root_tc.cuh)
 #include "lmf_jit_headers.inc"
 
 namespace lmf {
@@ -83,9 +84,18 @@ void gen_record_word(std::ostringstream& o, const RootParams& rp, int g, int wd,
 bool jit_available() { return nvrtc().ok; }
 
 std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<DirectAgg>& direct, int min_ctas) {
+  return jit_source(rp, mp, direct, min_ctas, false);
+}
+
+std::string jit_tc_source(const RootParams& rp, const std::vector<DirectAgg>& direct) {
+  return jit_source(rp, 32, direct, 1, true);
+}
+
+std::string jit_source(const RootParams& rp, int mp, const std::vector<DirectAgg>& direct, int min_ctas, bool tc) {
   std::ostringstream o;
   const bool unit_w = rp.unit_w != 0;
-  o << "// plan-specialised root scan (generated)\n#include \"lmf_root_plain.cuh\"\nnamespace lmf {\n";
+  o << "// plan-specialised root scan (generated)\n#include \"" << (tc ? "lmf_root_tc.cuh" : "lmf_root_plain.cuh")
+    << "\"\nnamespace lmf {\n";
   // slot tables of the reverse views summed per run: one entry per lane
   for (int r = 0; r < rp.n_rv; ++r) {
     const RevView& R = rp.rv[r];
@@ -238,10 +248,15 @@ std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<Dir
          "        rp_red_u64(O.omega + fk, static_cast<unsigned long long>(w / ce));\n"
          "      }\n    }\n";
   }
-  o << "    (void)lane;\n    (void)fres;\n    return w;\n  }\n};\n}  // namespace lmf\n"
-    << "extern \"C\" __global__ void __launch_bounds__(256, " << min_ctas << ") lmf_root_plain_jit(const __grid_constant__ "
-       "lmf::RootParams p, int64_t n_tiles) {\n"
-    << "  lmf::root_plain_body<" << mp << ", lmf::JitRowPass>(p, n_tiles);\n}\n";
+  o << "    (void)lane;\n    (void)fres;\n    return w;\n  }\n};\n}  // namespace lmf\n";
+  if (tc)
+    o << "extern \"C\" __global__ void __launch_bounds__(128) lmf_root_tc_jit(const __grid_constant__ "
+         "lmf::RootParams p, int64_t n_tiles, double* part) {\n"
+      << "  lmf::root_tc_body<lmf::JitRowPass>(p, n_tiles, part);\n}\n";
+  else
+    o << "extern \"C\" __global__ void __launch_bounds__(256, " << min_ctas << ") lmf_root_plain_jit(const __grid_constant__ "
+         "lmf::RootParams p, int64_t n_tiles) {\n"
+      << "  lmf::root_plain_body<" << mp << ", lmf::JitRowPass>(p, n_tiles);\n}\n";
   return o.str();
 }
 

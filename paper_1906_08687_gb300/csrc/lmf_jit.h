@@ -25,6 +25,10 @@ bool jit_available();
 // per-row tables; min_ctas the CTAs per SM its launch bounds ask for.  The
 // kernel is named lmf_root_plain_jit.
 std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<DirectAgg>& direct, int min_ctas);
+// the same row pass inside the tensor-core scan (lmf_root_tc.cuh); the
+// kernel is named lmf_root_tc_jit
+std::string jit_tc_source(const RootParams& rp, const std::vector<DirectAgg>& direct);
+std::string jit_source(const RootParams& rp, int mp, const std::vector<DirectAgg>& direct, int min_ctas, bool tc);
 
 // compiles src for sm_103a, or finds it in the process-wide cache of compiled
 // sources; on failure returns false with NVRTC's log in *log

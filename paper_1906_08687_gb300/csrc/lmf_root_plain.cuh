@@ -25,16 +25,6 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
   lo += e;
 }
 
-struct GenericRowPass {
-  static __device__ __forceinline__ int fold(const RootParams& p) { return p.fold; }
-  template <int MP>
-  static __device__ __forceinline__ long long run(const RootParams& p, int64_t row, float* zrow, int ldz,
-                                                  int32_t* crow, uint32_t* cache, uint32_t* res_hist,
-                                                  long long res_key) {
-    return root_row_pass<MP>(p, row, zrow, ldz, crow, cache, res_hist, res_key);
-  }
-};
-
 template <int MP, class RowPass>
 __device__ __forceinline__ void root_plain_body(const RootParams& p, int64_t n_tiles) {
   constexpr int T = kPlainT;

@@ -405,4 +405,15 @@ __device__ __forceinline__ long long root_row_pass(const RootParams& p, int64_t 
   return w;
 }
 
+// the row pass that reads the plan's descriptors at run time
+struct GenericRowPass {
+  static __device__ __forceinline__ int fold(const RootParams& p) { return p.fold; }
+  template <int MP>
+  static __device__ __forceinline__ long long run(const RootParams& p, int64_t row, float* zrow, int ldz,
+                                                  int32_t* crow, uint32_t* cache, uint32_t* res_hist,
+                                                  long long res_key) {
+    return root_row_pass<MP>(p, row, zrow, ldz, crow, cache, res_hist, res_key);
+  }
+};
+
 }  // namespace lmf
