@@ -22,7 +22,7 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-from .lmf import (LMF_BATCH_GRAPH, LMF_PLAN_FEATURES, LMF_PREC_SPLIT_BF16, LMF_ROOT_HEURISTIC, Engine,
+from .lmf import (LMF_BATCH_GRAPH, LMF_PLAN_FEATURES, LMF_PLAN_NO_JIT, LMF_PREC_SPLIT_BF16, LMF_ROOT_HEURISTIC, Engine,
                   LmfError, Mlp, lmf_plan_opts, register_schema)
 
 
@@ -51,9 +51,12 @@ def time_run(eng: Engine, bid: int, runs: int, max_ms: float) -> float:
     return float(statistics.median(out))
 
 
-def collect(schemas, runs: int = 3, max_ms: float = 200.0, device: int = 0, log=None) -> List[Dict]:
+def collect(schemas, runs: int = 3, max_ms: float = 200.0, device: int = 0, log=None, jit: bool = False
+            ) -> List[Dict]:
     """schemas: iterable of (schema, batch).  One record per schema with every
-    candidate's features and time, and the root rule's plan time."""
+    candidate's features and time, and the root rule's plan time.  Candidates
+    run the interpreted root scan unless jit (plan-time compilation of every
+    candidate would dominate a study of thousands of plans)."""
     import torch
     recs = []
     for si, (sch, batch) in enumerate(schemas):
@@ -63,7 +66,9 @@ def collect(schemas, runs: int = 3, max_ms: float = 200.0, device: int = 0, log=
         register_schema(eng, sch, tensors)
         bid = eng.declare_batch(batch)
         cands, feats, ms = [], [], []
-        for o in eng.plan_candidates(bid):
+        flags = 0 if jit else LMF_PLAN_NO_JIT
+        base = lmf_plan_opts(LMF_PREC_SPLIT_BF16, LMF_BATCH_GRAPH, 0, 0, 0, 0, 0, flags)
+        for o in eng.plan_candidates(bid, base):
             try:
                 eng.plan_opts(bid, o)
             except LmfError:
@@ -71,7 +76,7 @@ def collect(schemas, runs: int = 3, max_ms: float = 200.0, device: int = 0, log=
             feats.append(eng.plan_features(bid))
             ms.append(time_run(eng, bid, runs, max_ms))
             cands.append(_opts_tuple(o))
-        h = lmf_plan_opts(LMF_PREC_SPLIT_BF16, LMF_BATCH_GRAPH, 0, 0, LMF_ROOT_HEURISTIC, 0, 0, 0)
+        h = lmf_plan_opts(LMF_PREC_SPLIT_BF16, LMF_BATCH_GRAPH, 0, 0, LMF_ROOT_HEURISTIC, 0, 0, flags)
         eng.plan_opts(bid, h)
         heur_ms = time_run(eng, bid, runs, max_ms)
         heur_root = eng.plan_info(bid)['root_rel']
