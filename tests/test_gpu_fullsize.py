@@ -72,3 +72,26 @@ def test_config4_reduced_exact(order):
     fails, stats = compare(got, want)
     assert not fails, fails[:3]
     eng.close()
+
+
+def test_many_per_row_tables_exact():
+    """More per-row tables than ride in the kernel parameters (96): 3-way
+    COUNT tables over categories of three different keys, read by the
+    compiled and the interpreted scan from the device descriptor array."""
+    import itertools
+    from workloads import Agg
+    sch, _ = config4(100_003)
+    cats = sch.meta['cats']
+    dim = {c: c.split('_')[0] for c in cats}
+    dom = {c: sch.owner(c).col(c).cat_domain for c in cats}
+    triples = [t for t in itertools.combinations(cats, 3)
+               if len({dim[c] for c in t}) == 3 and dom[t[0]] * dom[t[1]] * dom[t[2]] <= 20_000]
+    assert len(triples) >= 130
+    batch = [Agg(group_by=t) for t in triples[:130]]
+    want = oracle.evaluate(sch, batch)
+    for jit in (True, False):
+        got, info, eng = run_engine(sch, batch, precision=0, batching=1, jit=jit)
+        assert info['jit'] == int(jit)
+        fails, _ = compare(got, want)
+        assert not fails, fails[:3]
+        eng.close()
