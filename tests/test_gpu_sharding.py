@@ -3,7 +3,7 @@ the whole batch over its rows (dimensions replicated), the partial results
 are summed on the host (int64 counts exactly, FP64 sums), and the sum equals
 the unsharded run -- counts bit for bit, sums within the error rule against
 the oracle.  This is the exchange a multi-GPU run would do with one
-all-reduce; here every box has one GPU."""
+all-reduce, emulated on one GPU."""
 import dataclasses
 
 import numpy as np
