@@ -46,7 +46,7 @@ WORKLOADS = {
     'snowflake': ('config2', 2, 20_000_000, 10_000_000, 200_000, -1, 'root_scan_snowflake20M.md'),
     'tree': ('config3', 3, 10_000_000, 100_000, 20_000, 300, 'tree_level_10M.md'),
     'chowliu': ('config4', 4, 50_000_000, 20_000_000, 500_000, -1, 'pair_counts_chowliu50M.md'),
-    'star': ('config1', 1, 200_000, 200_000, 200_000, -1, 'star_covar200k.md'),
+    'star': ('config1', 1, 200_000, 200_000, 200_000, -1, None),
 }
 KERNEL_SOURCES = ['paper_1906_08687_gb300/csrc/lmf_tree.cu',
                   'paper_1906_08687_gb300/csrc/lmf_kernels.cu',
@@ -78,7 +78,8 @@ def parse():
     ap.add_argument('--no-cpu-baseline', action='store_true')
     args = ap.parse_args()
     gen, idx, n, cpu_rows, ref_rows, check, prof = WORKLOADS[args.workload]
-    args.gen, args.cfg_index, args.profile = gen, idx, os.path.join(ROOT, 'profiles', prof)
+    args.gen, args.cfg_index = gen, idx
+    args.profile = os.path.join(ROOT, 'profiles', prof) if prof else ''
     args.n_fact = n if args.n_fact is None else args.n_fact
     args.cpu_sample_rows = cpu_rows if args.cpu_sample_rows is None else args.cpu_sample_rows
     args.ref_sample_rows = ref_rows if args.ref_sample_rows is None else args.ref_sample_rows
@@ -182,7 +183,7 @@ def kernel_hash() -> str:
 def profiled_traffic(precision: str, summary: str):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, when it was taken on the current kernel sources (else None)."""
-    if not os.path.exists(summary):
+    if not summary or not os.path.exists(summary):
         return None
     with open(summary) as f:
         text = f.read()
