@@ -31,19 +31,21 @@ POW, LE, GT = 0, 1, 2
 _KIND = {'pow': POW, 'le': LE, 'gt': GT}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with the host C compiler (OpenMP when available)."""
-    os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
-        return LIB
-    tmp = LIB + f'.{os.getpid()}.tmp'
-    base = ['gcc', '-O2', '-std=c11', '-fPIC', '-shared', SRC, '-o', tmp, '-lm']
+def build(force: bool = False, src: str = SRC, out: str = LIB) -> str:
+    """Compile the oracle with the host C compiler (OpenMP when available).
+    `src`/`out` default to this package's source and library; the tests that
+    plant mistakes in a copy of the source build that copy the same way."""
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+        return out
+    tmp = out + f'.{os.getpid()}.tmp'
+    base = ['gcc', '-O2', '-std=c11', '-fPIC', '-shared', src, '-o', tmp, '-lm']
     try:
         subprocess.run(base[:1] + ['-fopenmp'] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
         subprocess.run(base, check=True, capture_output=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
 
 
 class _Rel(ctypes.Structure):
@@ -73,26 +75,30 @@ class _Agg(ctypes.Structure):
                 ('offset', ctypes.c_int64)]
 
 
+def load_library(path: str):
+    """ctypes handle of a compiled oracle library with its signatures set."""
+    lib = ctypes.CDLL(path)
+    lib.orc_evaluate.restype = ctypes.c_int
+    lib.orc_evaluate.argtypes = [
+        ctypes.c_int, ctypes.POINTER(_Rel), ctypes.c_int, ctypes.c_int,
+        ctypes.POINTER(_Edge), ctypes.c_int, ctypes.POINTER(_Agg),
+        ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+        ctypes.POINTER(ctypes.c_int64)]
+    lib.orc_max_threads.restype = ctypes.c_int
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = ctypes.CDLL(LIB)
-            lib.orc_evaluate.restype = ctypes.c_int
-            lib.orc_evaluate.argtypes = [
-                ctypes.c_int, ctypes.POINTER(_Rel), ctypes.c_int, ctypes.c_int,
-                ctypes.POINTER(_Edge), ctypes.c_int, ctypes.POINTER(_Agg),
-                ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
-                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                ctypes.POINTER(ctypes.c_int64)]
-            lib.orc_max_threads.restype = ctypes.c_int
-            _lib = lib
+            _lib = load_library(build())
     return _lib
 
 
-def max_threads() -> int:
-    return int(_load().orc_max_threads())
+def max_threads(lib=None) -> int:
+    return int((lib if lib is not None else _load()).orc_max_threads())
 
 
 def _i32(seq) -> np.ndarray:
@@ -108,9 +114,11 @@ class OracleResult:
         self.join_size: int = join_size
 
 
-def evaluate(schema, batch: Sequence, root_range=None, nthreads: Optional[int] = None
-             ) -> OracleResult:
-    lib = _load()
+def evaluate(schema, batch: Sequence, root_range=None, nthreads: Optional[int] = None,
+             lib=None) -> OracleResult:
+    """`lib`: a handle from load_library() to evaluate with instead of this
+    package's library."""
+    lib = lib if lib is not None else _load()
     rels = schema.relations
     rindex = {r.name: i for i, r in enumerate(rels)}
     keep = []   # keep every buffer alive across the call
@@ -199,7 +207,7 @@ def evaluate(schema, batch: Sequence, root_range=None, nthreads: Optional[int] =
     js = ctypes.c_int64(0)
     root = rindex[schema.root]
     b, e = (0, rels[root].nrows) if root_range is None else root_range
-    nt = max_threads() if nthreads is None else int(nthreads)
+    nt = max_threads(lib) if nthreads is None else int(nthreads)
     rc = lib.orc_evaluate(len(rels), c_rels, root, len(schema.edges), c_edges, len(batch),
                           c_aggs, n_sum, n_cnt, int(b), int(e), nt,
                           out_sum.ctypes.data, out_abs.ctypes.data, out_cnt.ctypes.data,

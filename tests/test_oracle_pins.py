@@ -14,7 +14,6 @@
   left and right views L_i * R_i;
 * the aggregate-count formulas of Sec. 2.
 """
-import itertools
 import json
 import math
 import os
@@ -23,6 +22,8 @@ import numpy as np
 import pytest
 
 from oracle import oracle
+from oracle_pinlib import (assert_close, brute_force, check_against_brute_force,
+                           check_compensated_sum, shared_attribute_schema)
 from workloads import (Agg, Column, Relation, Schema, chain_schema, config1, config2,
                        config3, config4, covar_batch, cube_batch, pair_count_batch,
                        tiny_schema)
@@ -31,85 +32,38 @@ GOLDEN = os.path.join(os.path.dirname(__file__), 'golden')
 
 
 # ----------------------------------------------------------------------------
-def brute_force(schema, batch):
-    """Cartesian product of all relations, keep tuples that agree on every
-    shared attribute name (the natural join), evaluate each aggregate."""
-    rels = schema.relations
-    out = []
-    cells = []
-    for agg in batch:
-        dom = [_domain(schema, g) for g in agg.group_by]
-        n = int(np.prod(dom)) if dom else 1
-        is_count = all(f[1] != 'pow' for f in agg.factors)
-        cells.append((dom, is_count))
-        out.append([0] * n if is_count else [[] for _ in range(n)])
-    size = 0
-    for combo in itertools.product(*[range(r.nrows) for r in rels]):
-        vals = {}
-        ok = True
-        for r, row in zip(rels, combo):
-            for c in r.columns:
-                v = c.data[row].item()
-                if c.name in vals and vals[c.name] != v:
-                    ok = False
-                    break
-                vals[c.name] = v
-            if not ok:
-                break
-        if not ok:
-            continue
-        size += 1
-        for a, agg in enumerate(batch):
-            v = 1.0
-            for attr, kind, p in agg.factors:
-                x = vals[attr]
-                if kind == 'pow':
-                    v *= x ** int(p)
-                elif kind == 'le':
-                    v *= 1.0 if x <= p else 0.0
-                else:
-                    v *= 1.0 if x > p else 0.0
-            dom, is_count = cells[a]
-            cell = 0
-            for g, d in zip(agg.group_by, dom):
-                cell = cell * d + int(vals[g])
-            if is_count:
-                out[a][cell] += int(v)
-            else:
-                out[a][cell].append(v)
-    res = []
-    for a in range(len(batch)):
-        if cells[a][1]:
-            res.append(np.array(out[a], np.int64))
-        else:
-            res.append(np.array([math.fsum(c) for c in out[a]], np.float64))
-    return res, size
-
-
-def _domain(schema, attr):
-    for r in schema.relations:
-        for c in r.columns:
-            if c.name == attr:
-                return c.cat_domain
-    raise KeyError(attr)
-
-
-def assert_close(got, want, rel=1e-12, absolute=1e-12):
-    np.testing.assert_allclose(got, want, rtol=rel, atol=absolute)
-
-
-# ----------------------------------------------------------------------------
 @pytest.mark.parametrize('seed', list(range(40)))
 def test_brute_force_tiny(seed):
     sch, batch = tiny_schema(1000 + seed, unique_keys=(seed % 4 == 3))
-    res = oracle.evaluate(sch, batch, nthreads=1 + seed % 3)
-    want, size = brute_force(sch, batch)
-    assert res.join_size == size
-    for a in range(len(batch)):
-        if res.kinds[a] == 'count':
-            assert np.array_equal(res.values[a], want[a]), (a, batch[a])
-        else:
-            assert_close(res.values[a], want[a])
+    check_against_brute_force(sch, batch, nthreads=1 + seed % 3)
+
+
+@pytest.mark.parametrize('seed', list(range(12)))
+def test_brute_force_tiny_float32(seed):
+    """FP32 feature columns (the benchmark's dtype) are read exactly."""
+    sch, batch = tiny_schema(1000 + seed, feat_dtype=np.float32)
+    check_against_brute_force(sch, batch, nthreads=1 + seed % 2)
+
+
+@pytest.mark.parametrize('seed', list(range(3)))
+def test_join_on_two_shared_attributes(seed):
+    """A child sharing two attributes with its parent joins on both."""
+    sch, batch = shared_attribute_schema(seed)
+    check_against_brute_force(sch, batch, nthreads=1 + seed % 2)
+    # the pin has teeth: joined on the key alone, the join is larger
+    S = sch.rel('S')
+    renamed = Relation('S', [Column('b2' if c.name == 'b' else c.name, c.role, c.data,
+                                    c.cat_domain) for c in S.columns])
+    key_only = Schema([sch.rel('R'), renamed, sch.rel('U')], sch.edges, sch.root)
+    _, size, _ = brute_force(sch, [Agg()])
+    _, size_key_only, _ = brute_force(key_only, [Agg()])
+    assert size_key_only > size > 0
+
+
+@pytest.mark.parametrize('nthreads', [1, 3])
+def test_compensated_sum_is_exact(nthreads):
+    """Terms of size 1e16 that cancel down to 4: the compensated sum is exact."""
+    check_compensated_sum(nthreads=nthreads)
 
 
 def test_brute_force_covers_fanout_and_dangling():
@@ -120,7 +74,7 @@ def test_brute_force_covers_fanout_and_dangling():
     for seed in range(40):
         sch, batch = tiny_schema(1000 + seed, unique_keys=(seed % 4 == 3))
         root_rows = sch.rel(sch.root).nrows
-        _, size = brute_force(sch, [Agg()])
+        _, size, _ = brute_force(sch, [Agg()])
         seen['fanout'] |= size > root_rows
         seen['dangling'] |= size < root_rows
         seen['empty'] |= any(r.nrows == 0 for r in sch.relations)
@@ -331,7 +285,7 @@ def test_chain_example_left_right_views():
     res = oracle.evaluate(sch, batch)
     for i in range(1, n + 1):
         assert np.array_equal(res.values[i - 1], (L[i] * R[i]).astype(np.int64)), i
-    want, size_bf = brute_force(sch, batch)
+    want, size_bf, _ = brute_force(sch, batch)
     assert res.join_size == size_bf
     for i in range(n):
         assert np.array_equal(res.values[i], want[i])
