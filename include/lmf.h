@@ -226,7 +226,10 @@ lmf_status lmf_plan_info(lmf_ctx* ctx, int batch_id, lmf_plan_stats* info);
  * Run a planned batch on `cuda_stream` (a cudaStream_t; NULL = the context's
  * own stream).  Asynchronous: it only enqueues work (host-resident columns
  * are copied in on the same stream first).  Device-detected errors are
- * latched and returned by lmf_sync.
+ * latched and returned by lmf_sync.  The stream must stay valid until the
+ * batch's next run, or until lmf_sync / lmf_read_result have returned: those
+ * calls wait on the stream of the last run.  Planning the batch again waits
+ * for the whole device before it frees the old plan.
  */
 lmf_status lmf_run(lmf_ctx* ctx, int batch_id, void* cuda_stream);
 

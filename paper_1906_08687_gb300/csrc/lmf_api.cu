@@ -72,6 +72,21 @@ struct AggH {
 };
 
 // ---- plan ------------------------------------------------------------------
+// a device allocation freed when its scope ends, error returns included
+struct DevScratch {
+  void* p = nullptr;
+  DevScratch() = default;
+  DevScratch(const DevScratch&) = delete;
+  DevScratch& operator=(const DevScratch&) = delete;
+  ~DevScratch() {
+    if (p) cudaFree(p);
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
 struct Arena {
   char* base = nullptr;
   size_t size = 0, used = 0;
@@ -166,6 +181,22 @@ struct Plan {
   bool root_scan = true;         // some aggregate needs the Gram / counts / grouped tables
   template <class T>
   T* at(size_t off) const { return reinterpret_cast<T*>(arena.base + off); }
+  // device resources of the plan; a plan that fails half-way releases what it
+  // had allocated when it is dropped
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (graph_stream) cudaStreamDestroy(graph_stream);
+    if (arena.base) cudaFree(arena.base);
+    exec = nullptr;
+    graph = nullptr;
+    graph_stream = nullptr;
+    arena.base = nullptr;
+  }
+  Plan() = default;
+  Plan(const Plan&) = delete;
+  Plan& operator=(const Plan&) = delete;
+  ~Plan() { release(); }
 };
 
 struct BatchH {
@@ -210,14 +241,7 @@ lmf_status fail(lmf_ctx* c, lmf_status s, const char* fmt, ...) {
   } while (0)
 
 void free_plan(Plan* p) {
-  if (!p) return;
-  if (p->exec) cudaGraphExecDestroy(p->exec);
-  if (p->graph) cudaGraphDestroy(p->graph);
-  if (p->graph_stream) cudaStreamDestroy(p->graph_stream);
-  if (p->arena.base) cudaFree(p->arena.base);
-  p->exec = nullptr;
-  p->graph = nullptr;
-  p->arena.base = nullptr;
+  if (p) p->release();
 }
 
 // which relation holds attribute `a` (non-key attributes are unique)
@@ -302,6 +326,16 @@ lmf_status lmf_register_relation(lmf_ctx* c, const char* name, int64_t nrows, co
   RelationH r;
   r.name = name;
   r.nrows = nrows;
+  // on any failure below, the staging copies made so far are freed
+  struct Staged {
+    RelationH* r;
+    bool keep = false;
+    ~Staged() {
+      if (!keep)
+        for (auto& col : r->cols)
+          if (col.dev) cudaFree(col.dev);
+    }
+  } staged{&r};
   for (int i = 0; i < ncols; ++i) {
     const lmf_column& s = cols[i];
     if (!s.name || (!s.data && nrows > 0)) return fail(c, LMF_ERR_ARG, "column %d: null name/data", i);
@@ -327,7 +361,10 @@ lmf_status lmf_register_relation(lmf_ctx* c, const char* name, int64_t nrows, co
     if (h.on_host == LMF_HOST_COPY && nrows > 0) {
       if (cudaMalloc(&h.dev, (size_t)nrows * h.esize()) != cudaSuccess)
         return fail(c, LMF_ERR_OOM, "staging buffer for %s", s.name);
-      cudaMemcpy(h.dev, h.data, (size_t)nrows * h.esize(), cudaMemcpyHostToDevice);
+      r.cols.push_back(h);
+      const cudaError_t e = cudaMemcpy(h.dev, h.data, (size_t)nrows * h.esize(), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return fail(c, LMF_ERR_CUDA, "column %s: host copy: %s", s.name, cudaGetErrorString(e));
+      continue;
     }
     r.cols.push_back(h);
   }
@@ -339,6 +376,7 @@ lmf_status lmf_register_relation(lmf_ctx* c, const char* name, int64_t nrows, co
                     other.name.c_str(), name);
   }
   *rel_id = (int)c->rels.size();
+  staged.keep = true;
   c->rels.push_back(std::move(r));
   return LMF_OK;
 }
@@ -421,8 +459,9 @@ lmf_status lmf_declare_join(lmf_ctx* c, int n_edges, const int* parent_rel, cons
         if (c->rels[lca].find(col.name) < 0) return fail(c, LMF_ERR_NOT_TREE, "attribute %s breaks running intersection", col.name.c_str());
       }
   // key index of every child: range and multiplicity (A1)
-  int* mm = nullptr;
-  CUDA_TRY(c, cudaMalloc(&mm, 2 * sizeof(int)));
+  DevScratch mm_buf;
+  CUDA_TRY(c, cudaMalloc(&mm_buf.p, 2 * sizeof(int)));
+  int* mm = mm_buf.as<int>();
   for (int ch = 0; ch < n; ++ch) {
     RelationH& R = c->rels[ch];
     if (R.parent < 0) continue;
@@ -437,24 +476,20 @@ lmf_status lmf_declare_join(lmf_ctx* c, int n_edges, const int* parent_rel, cons
     CUDA_TRY(c, launch_key_stats(static_cast<const int32_t*>(kc.dptr()), R.nrows, nullptr, 0, mm, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(h_mm, mm, sizeof(h_mm), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    if (h_mm[0] < 0) {
-      cudaFree(mm);
-      return fail(c, LMF_ERR_KEY, "relation %s: negative key %d", R.name.c_str(), h_mm[0]);
-    }
+    if (h_mm[0] < 0) return fail(c, LMF_ERR_KEY, "relation %s: negative key %d", R.name.c_str(), h_mm[0]);
     if ((int64_t)h_mm[1] >= 4 * R.nrows + 4096) {
-      cudaFree(mm);
       return fail(c, LMF_ERR_KEY, "relation %s: keys too sparse for direct addressing (max %d, %lld rows)",
                   R.name.c_str(), h_mm[1], (long long)R.nrows);
     }
     R.K = h_mm[1] + 1;
-    unsigned int* hist = nullptr;
-    CUDA_TRY(c, cudaMalloc(&hist, sizeof(unsigned int) * R.K));
+    DevScratch hist_buf;
+    CUDA_TRY(c, cudaMalloc(&hist_buf.p, sizeof(unsigned int) * R.K));
+    unsigned int* hist = hist_buf.as<unsigned int>();
     CUDA_TRY(c, cudaMemsetAsync(hist, 0, sizeof(unsigned int) * R.K, c->stream));
     CUDA_TRY(c, launch_key_stats(static_cast<const int32_t*>(kc.dptr()), R.nrows, hist, R.K, nullptr, c->stream));
     std::vector<unsigned int> h(R.K);
     CUDA_TRY(c, cudaMemcpyAsync(h.data(), hist, sizeof(unsigned int) * R.K, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    cudaFree(hist);
     R.max_mult = (int)*std::max_element(h.begin(), h.end());
   }
   // the parent's side of every edge (its foreign-key column), which becomes the
@@ -480,17 +515,16 @@ lmf_status lmf_declare_join(lmf_ctx* c, int n_edges, const int* parent_rel, cons
       continue;
     }
     R.fk_K = h_mm[1] + 1;
-    unsigned int* hist = nullptr;
-    CUDA_TRY(c, cudaMalloc(&hist, sizeof(unsigned int) * R.fk_K));
+    DevScratch hist_buf;
+    CUDA_TRY(c, cudaMalloc(&hist_buf.p, sizeof(unsigned int) * R.fk_K));
+    unsigned int* hist = hist_buf.as<unsigned int>();
     CUDA_TRY(c, cudaMemsetAsync(hist, 0, sizeof(unsigned int) * R.fk_K, c->stream));
     CUDA_TRY(c, launch_key_stats(static_cast<const int32_t*>(fc.dptr()), P.nrows, hist, R.fk_K, nullptr, c->stream));
     std::vector<unsigned int> h(R.fk_K);
     CUDA_TRY(c, cudaMemcpyAsync(h.data(), hist, sizeof(unsigned int) * R.fk_K, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    cudaFree(hist);
     R.fk_mult = (int)*std::max_element(h.begin(), h.end());
   }
-  cudaFree(mm);
   c->root = root;
   c->joined = true;
   return LMF_OK;
@@ -751,9 +785,11 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   cudaSetDevice(c->device);
   BatchH& B = *c->batches[batch_id];
   if (B.plan) {
-    cudaStreamSynchronize(c->stream);
-    free_plan(B.plan.get());
+    // the old plan may still run on a caller's stream: wait for the device
+    // before its arena and graph go
+    cudaDeviceSynchronize();
     B.plan.reset();
+    B.last_stream = nullptr;
   }
   auto P = std::make_unique<Plan>();
   P->opts = opts;
@@ -831,14 +867,14 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
           rows.push_back(c->rels[r].nrows);
         }
     if (!cols.empty()) {
-      double* d = nullptr;
-      CUDA_TRY(c, cudaMalloc(&d, sizeof(double) * cols.size()));
+      DevScratch d_buf;
+      CUDA_TRY(c, cudaMalloc(&d_buf.p, sizeof(double) * cols.size()));
+      double* d = d_buf.as<double>();
       CUDA_TRY(c, cudaMemsetAsync(d, 0, sizeof(double) * cols.size(), c->stream));
       for (size_t i = 0; i < cols.size(); ++i) CUDA_TRY(c, launch_colmaxabs(&cols[i], 1, rows[i], d + i, c->stream));
       std::vector<double> h(cols.size());
       CUDA_TRY(c, cudaMemcpyAsync(h.data(), d, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
       CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-      cudaFree(d);
       for (size_t i = 0; i < h.size(); ++i) bound[names[i]] = h[i];
     }
   }
@@ -898,8 +934,9 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   std::vector<unsigned long long> changes(rp.n_grp, 0);
   std::vector<int> has_runs(rp.n_grp, 0);
   if (rp.n_grp > 0 && Root.nrows > 1) {
-    unsigned long long* d = nullptr;
-    CUDA_TRY(c, cudaMalloc(&d, sizeof(unsigned long long) * rp.n_grp));
+    DevScratch d_buf;
+    CUDA_TRY(c, cudaMalloc(&d_buf.p, sizeof(unsigned long long) * rp.n_grp));
+    unsigned long long* d = d_buf.as<unsigned long long>();
     CUDA_TRY(c, cudaMemsetAsync(d, 0, sizeof(unsigned long long) * rp.n_grp, c->stream));
     for (int q = 0; q < rp.n_grp; ++q) {
       GroupH& g = P->groups[RR.groups[q]];
@@ -910,7 +947,6 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     CUDA_TRY(c, cudaMemcpyAsync(changes.data(), d, sizeof(unsigned long long) * rp.n_grp, cudaMemcpyDeviceToHost,
                                 c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    cudaFree(d);
     for (int q = 0; q < rp.n_grp; ++q) {
       has_runs[q] = (int64_t)(changes[q] + 1) * 4 <= Root.nrows;
       if (P->unique_all && Root.nrows >= 2 * kResRun && (int64_t)(changes[q] + 1) * kResRun <= Root.nrows &&
@@ -1156,14 +1192,14 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   {
     auto top_of = [&](const int32_t* col, int64_t n, int K, int h, std::vector<int32_t>* out) -> lmf_status {
       if (n <= 0 || K <= 0) return LMF_OK;
-      unsigned int* d = nullptr;
-      CUDA_TRY(c, cudaMalloc(&d, sizeof(unsigned int) * K));
+      DevScratch d_buf;
+      CUDA_TRY(c, cudaMalloc(&d_buf.p, sizeof(unsigned int) * K));
+      unsigned int* d = d_buf.as<unsigned int>();
       CUDA_TRY(c, cudaMemsetAsync(d, 0, sizeof(unsigned int) * K, c->stream));
       CUDA_TRY(c, launch_key_stats(col, n, d, K, nullptr, c->stream));
       std::vector<unsigned int> cnt(K);
       CUDA_TRY(c, cudaMemcpyAsync(cnt.data(), d, sizeof(unsigned int) * K, cudaMemcpyDeviceToHost, c->stream));
       CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-      cudaFree(d);
       std::vector<int32_t> idx(K);
       for (int i = 0; i < K; ++i) idx[i] = i;
       const int take = std::min(h, K);
@@ -1832,14 +1868,19 @@ lmf_status lmf_run_profiled(lmf_ctx* c, int batch_id, void* cuda_stream, float* 
     lmf_status st = ensure_tuned(c, B, s);
     if (st) return st;
   }
-  cudaEvent_t ev[LMF_STAGES + 1];
-  for (auto& e : ev) CUDA_TRY(c, cudaEventCreate(&e));
-  lmf_status st = enqueue(c, B, s, ev);
+  struct Events {
+    cudaEvent_t e[LMF_STAGES + 1] = {};
+    ~Events() {
+      for (auto x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } ev;
+  for (auto& e : ev.e) CUDA_TRY(c, cudaEventCreate(&e));
+  lmf_status st = enqueue(c, B, s, ev.e);
   if (st == LMF_OK) {
-    CUDA_TRY(c, cudaEventSynchronize(ev[LMF_STAGES]));
-    for (int i = 0; i < LMF_STAGES; ++i) cudaEventElapsedTime(&stage_ms[i], ev[i], ev[i + 1]);
+    CUDA_TRY(c, cudaEventSynchronize(ev.e[LMF_STAGES]));
+    for (int i = 0; i < LMF_STAGES; ++i) cudaEventElapsedTime(&stage_ms[i], ev.e[i], ev.e[i + 1]);
   }
-  for (auto& e : ev) cudaEventDestroy(e);
   return st;
 }
 
