@@ -193,8 +193,15 @@ def profiled_traffic(precision: str, summary: str):
     return float(m.group(1))
 
 
-FACT_ORDER_SORTED = ('sorted by the join attributes, fewest distinct values first (k3, k2, k1): '
-                     'the scan order of Sec. 3.5, as the paper\'s experiments load every relation')
+def fact_order_text(sch, fact_order: str) -> str:
+    """How the fact rows are ordered; a sorted root lists its join attributes in
+    sort order (fewest distinct values first: the child with fewer keys)."""
+    if fact_order != 'sorted':
+        return 'generation order (i.i.d. rows)'
+    keys = sorted((sch.rel(c).nrows, k) for p, c, k in sch.edges if p == sch.root)
+    names = list(dict.fromkeys(k for _, k in keys))
+    return (f"sorted by the join attributes, fewest distinct values first ({', '.join(names)}): "
+            "the scan order of Sec. 3.5, as the paper's experiments load every relation")
 
 
 WORKLOAD_TEXT = {
@@ -232,8 +239,10 @@ def run_reference(args):
         'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': ws,
         'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': t * 1e3, 'higher_is_better': True,
         'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
-        'config': {'workload': sch.meta['name'], 'n_aggregates': len(batch),
-                   'fact_order': args.fact_order, 'sample_rows_per_step': S},
+        'config': {'workload': WORKLOAD_TEXT.get(args.workload, '{name}').format(name=sch.meta['name']),
+                   'n_aggregates': len(batch),
+                   'fact_order': fact_order_text(sch, args.fact_order),
+                   'sample_rows_per_step': S},
         'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': nt, 'kind': 'oracle', 'sample': sample},
         'e2e': {'value': value, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
     }
@@ -396,8 +405,7 @@ def main():
                             'root_scan_compiled': bool(info['jit']),
                             'resident_group': info['resident_group'],
                             'candidates_ms_per_step': cand_ms},
-                   'fact_order': (FACT_ORDER_SORTED if args.fact_order == 'sorted'
-                                  else 'generation order (i.i.d. rows)'),
+                   'fact_order': fact_order_text(sch, args.fact_order),
                    'batching': 'cuda-graph', 'kernels_per_step': info['n_kernels_per_run'],
                    'l2': f'inputs larger than L2 ({fact_bytes / 1e6:.0f} MB fact table per step)',
                    'parallelism': f'replicas x{ws}'},
