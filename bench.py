@@ -29,6 +29,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -213,6 +214,48 @@ WORKLOAD_TEXT = {
 
 
 # ----------------------------------------------------------------------------
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu's, else /proc/cpuinfo's, else the machine type)."""
+    try:
+        out = subprocess.run(['lscpu'], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith('Model name:'):
+                return ln.split(':', 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open('/proc/cpuinfo') as f:
+            for ln in f:
+                if ln.lower().startswith('model name'):
+                    return ln.split(':', 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def cpu_baseline(sch, batch, n_fact: int, sample_rows: int, single_thread: bool = False) -> dict:
+    """The oracle, as it stands, on this host's cores over the first sample_rows
+    fact rows of the workload (all aggregates); with single_thread also on one
+    core."""
+    from oracle import oracle
+    oracle.build()
+    S = min(sample_rows, n_fact)
+    nt = oracle.max_threads()
+    t0 = time.perf_counter()
+    res = oracle.evaluate(sch, batch, root_range=(0, S), nthreads=nt)
+    dt = time.perf_counter() - t0
+    out = {'value': res.join_size * len(batch) / dt / 1e9, 'unit': UNIT, 'cores': nt,
+           'kind': 'oracle', 'cpu': cpu_model(),
+           'sample': f'first {S} fact rows of the same workload, all {len(batch)} aggregates ({dt:.1f} s)'}
+    if single_thread:
+        t0 = time.perf_counter()
+        res1 = oracle.evaluate(sch, batch, root_range=(0, S), nthreads=1)
+        dt1 = time.perf_counter() - t0
+        out['value_1thread'] = res1.join_size * len(batch) / dt1 / 1e9
+    return out
+
+
+# ----------------------------------------------------------------------------
 def run_reference(args):
     """The oracle on this host's cores, one bounded sample of the workload per step."""
     ws, rank, _ = dist_env()
@@ -243,7 +286,8 @@ def run_reference(args):
                    'n_aggregates': len(batch),
                    'fact_order': fact_order_text(sch, args.fact_order),
                    'sample_rows_per_step': S},
-        'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': nt, 'kind': 'oracle', 'sample': sample},
+        'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': nt, 'kind': 'oracle', 'cpu': cpu_model(),
+                         'sample': sample},
         'e2e': {'value': value, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
     }
     print(json.dumps(line), flush=True)
@@ -436,17 +480,8 @@ def main():
                             'rule': '|g-r| <= 1e-6*max(|r|, 1e-3*sum|v|); counts exact'}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        from oracle import oracle
-        oracle.build()
-        S = min(args.cpu_sample_rows, args.n_fact)
-        nt = oracle.max_threads()
-        t0 = time.perf_counter()
-        res = oracle.evaluate(sch, batch, root_range=(0, S), nthreads=nt)
-        dt = time.perf_counter() - t0
-        line['cpu_baseline'] = {'value': res.join_size * n_agg / dt / 1e9, 'unit': UNIT, 'cores': nt,
-                                'kind': 'oracle',
-                                'sample': f'first {S} fact rows of the same workload, all {n_agg} '
-                                          f'aggregates ({dt:.1f} s)'}
+        line['cpu_baseline'] = cpu_baseline(sch, batch, args.n_fact, args.cpu_sample_rows,
+                                            single_thread=args.workload == 'star')
     eng.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
