@@ -74,3 +74,42 @@ def test_struct_layouts_match_header(tmp_path):
         assert int(want[name]) == ctypes.sizeof(cls), name
         for f, _ in cls._fields_:
             assert int(want[f'{name}.{f}']) == getattr(cls, f).offset, (name, f)
+
+
+def _prototypes():
+    """name -> list of parameter declarations, from include/lmf.h."""
+    with open(os.path.join(ROOT, 'include', 'lmf.h')) as f:
+        text = f.read()
+    text = re.sub(r'/\*.*?\*/', '', text, flags=re.S)
+    text = re.sub(r'//[^\n]*', '', text)
+    out = {}
+    for name, params in re.findall(r'\b(lmf_[a-z_0-9]+)\s*\(([^;{)]*)\)\s*;', text, flags=re.S):
+        params = ' '.join(params.split())
+        out[name] = [] if params in ('', 'void') else [p.strip() for p in params.split(',')]
+    return out
+
+
+def test_binding_argument_types_match_the_prototypes():
+    """Every binding signature has the header's parameter count, a pointer
+    where the header has one, and a scalar of the header's width and kind
+    elsewhere."""
+    from paper_1906_08687_gb300 import lmf
+    scalars = {'int': (4, int), 'int32_t': (4, int), 'uint32_t': (4, int), 'int64_t': (8, int),
+               'uint64_t': (8, int),
+               'size_t': (8, int), 'float': (4, float), 'double': (8, float),
+               'lmf_status': (4, int), 'lmf_dtype': (4, int)}
+    protos = _prototypes()
+    assert set(protos) == set(declared_symbols())
+    for name, params in protos.items():
+        _, argtypes = lmf._SIGNATURES[name]
+        assert len(argtypes) == len(params), (name, params, argtypes)
+        for decl, ct in zip(params, argtypes):
+            if '*' in decl:
+                ok = (ct in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(ct, ctypes._Pointer)
+                      or issubclass(ct, ctypes.Array))
+                assert ok, (name, decl, ct)
+                continue
+            base = decl.replace('const ', '').split()[0]
+            size, kind = scalars[base]
+            assert ctypes.sizeof(ct) == size, (name, decl, ct)
+            assert issubclass(ct, (ctypes.c_float, ctypes.c_double)) == (kind is float), (name, decl, ct)
