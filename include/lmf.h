@@ -23,6 +23,11 @@
  *     pointers on the context's device; everything else is host memory.
  *   - One context per host thread; a context is not thread safe.  There is no
  *     global mutable state.
+ *   - Calls that take (ctx, batch_id) return LMF_ERR_ARG for a null ctx or a
+ *     batch id lmf_declare_batch did not hand out, LMF_ERR_STATE when the
+ *     batch needs a plan and has none; a failing CUDA call gives LMF_ERR_CUDA
+ *     (LMF_ERR_OOM for a failed allocation).  Outputs are meaningful only on
+ *     LMF_OK.
  */
 #ifndef LMF_H_
 #define LMF_H_
@@ -165,7 +170,11 @@ typedef struct {
  */
 lmf_status lmf_create(int device, lmf_ctx** out);
 
-/* Free every device buffer the context owns and the context itself. */
+/*
+ * Wait for the device, then free every device buffer the context owns (plans,
+ * staging copies of host columns, its stream) and the context itself.  Borrowed
+ * column memory stays the caller's.  Errors: LMF_ERR_ARG for a null ctx.
+ */
 lmf_status lmf_destroy(lmf_ctx* ctx);
 
 /*
@@ -219,7 +228,10 @@ lmf_status lmf_declare_batch(lmf_ctx* ctx, const lmf_agg_spec* aggs, int n, int*
  */
 lmf_status lmf_plan(lmf_ctx* ctx, int batch_id, const lmf_plan_opts* opts);
 
-/* Report statistics of a planned batch. */
+/*
+ * Statistics of a planned batch (views and probe groups of Sec. 3.2-3.4, the
+ * root scan's form) into *info (host).  Errors: the common ones.
+ */
 lmf_status lmf_plan_info(lmf_ctx* ctx, int batch_id, lmf_plan_stats* info);
 
 /*
@@ -245,6 +257,7 @@ lmf_status lmf_run(lmf_ctx* ctx, int batch_id, void* cuda_stream);
  * Like lmf_run without graph replay, with a CUDA event recorded on
  * `cuda_stream` at every stage boundary; waits for the run and writes the
  * LMF_STAGES stage durations in milliseconds to stage_ms (host array).
+ * Errors: LMF_ERR_ARG for a null stage_ms, else those of lmf_run.
  */
 lmf_status lmf_run_profiled(lmf_ctx* ctx, int batch_id, void* cuda_stream, float* stage_ms);
 
@@ -256,25 +269,32 @@ lmf_status lmf_run_profiled(lmf_ctx* ctx, int batch_id, void* cuda_stream, float
 lmf_status lmf_sync(lmf_ctx* ctx, int batch_id);
 
 /*
- * Shape of aggregate `agg`'s result: *n_groups cells of *dtype (LMF_I64 or
- * LMF_F64), stored at *offset in the batch's int64 or float64 result array.
+ * Shape of aggregate `agg`'s result (the output of query Q(F; alpha), Eq.
+ * query): *n_groups cells of *dtype (LMF_I64 or LMF_F64), stored at *offset
+ * in the batch's int64 or float64 result array; any of the three outputs may
+ * be NULL.  Errors: LMF_ERR_ARG for agg outside [0, n), else the common ones.
  */
 lmf_status lmf_result_info(lmf_ctx* ctx, int batch_id, int agg, int64_t* n_groups,
                            int32_t* dtype, int64_t* offset);
 
-/* Total cells of the batch's int64 and float64 result arrays. */
+/* Total cells of the batch's int64 and float64 result arrays (either output
+ * may be NULL).  Errors: the common ones. */
 lmf_status lmf_result_sizes(lmf_ctx* ctx, int batch_id, int64_t* n_i64, int64_t* n_f64);
 
 /*
  * Copy all results of the last run: n_i64 int64 cells to dst_i64 and n_f64
  * doubles to dst_f64 (either may be NULL to skip), host or device memory
- * (dst_is_device).  Enqueued on `cuda_stream` after the run; a host copy
- * waits for it.
+ * (dst_is_device).  Enqueued on `cuda_stream` (NULL: the stream of the last
+ * run) after the run; a host copy waits for it.  Results stay owned by the
+ * plan; they are overwritten by the next run.  Errors: the common ones.
  */
 lmf_status lmf_read_results(lmf_ctx* ctx, int batch_id, int64_t* dst_i64, double* dst_f64,
                             int dst_is_device, void* cuda_stream);
 
-/* Copy one aggregate's result (n_groups cells of its dtype) to host memory. */
+/* Copy one aggregate's result (n_groups cells of its dtype, groups row-major
+ * over the group-by values) to host memory dst; waits for the last run.
+ * Errors: LMF_ERR_ARG for a null dst or agg outside [0, n), else the common
+ * ones. */
 lmf_status lmf_read_result(lmf_ctx* ctx, int batch_id, int agg, void* dst);
 
 /* ---------------------------------------------------------------------------
@@ -292,7 +312,7 @@ lmf_status lmf_read_result(lmf_ctx* ctx, int batch_id, int agg, void* dst);
  * the Sec. 3.3 rule's one, the largest relations) x precision x CTAs per SM x
  * view merging, each as explicit plan options derived from *base (NULL: zero
  * options).  Writes min(max, count) entries to out (may be NULL) and the count
- * to *n.
+ * to *n.  Errors: LMF_ERR_ARG (null n), LMF_ERR_STATE before lmf_declare_join.
  */
 lmf_status lmf_plan_candidates(lmf_ctx* ctx, int batch_id, const lmf_plan_opts* base,
                                lmf_plan_opts* out, int max, int* n);
@@ -301,19 +321,31 @@ lmf_status lmf_plan_candidates(lmf_ctx* ctx, int batch_id, const lmf_plan_opts* 
  * Features of the batch's current plan (host array of n >= LMF_PLAN_FEATURES
  * floats): sizes, view and group counts, z length, record bytes, aggregate
  * counts, key multiplicity, precision, CTAs per SM, merging, root position.
+ * Errors: LMF_ERR_ARG (null feat, n too small), LMF_ERR_STATE before a plan.
  */
 lmf_status lmf_plan_features(lmf_ctx* ctx, int batch_id, float* feat, int n);
 
 typedef struct lmf_mlp lmf_mlp;
 
-/* An FP32 MLP in -> hidden -> hidden -> 1 (ReLU), weights drawn from seed. */
+/*
+ * The learned cost model (no counterpart in the paper, which plans by the
+ * Sec. 3.3 rule alone): an FP32 MLP in -> hidden -> hidden -> 1 with ReLU,
+ * predicting the log run time of a plan from its features.  Its parameters,
+ * gradients and Adam moments live on `device`, owned by the model until
+ * lmf_mlp_destroy.  Every call below is synchronous and returns LMF_ERR_ARG for
+ * a null model or pointer argument, a size that does not match the model or a
+ * batch <= 0, LMF_ERR_OOM / LMF_ERR_CUDA on device failures.
+ */
+/* A model with weights drawn from seed; 1 <= in_dim, hidden <= 4096. */
 lmf_status lmf_mlp_create(int device, int in_dim, int hidden, uint64_t seed, lmf_mlp** out);
 lmf_status lmf_mlp_destroy(lmf_mlp* m);
-/* Parameter count and flat copies (layout W1[in][h] b1[h] W2[h][h] b2[h] w3[h] b3). */
+/* Parameter count and flat host copies of n = that count floats (layout
+ * W1[in][h] b1[h] W2[h][h] b2[h] w3[h] b3). */
 lmf_status lmf_mlp_num_params(lmf_mlp* m, int64_t* n);
 lmf_status lmf_mlp_get_params(lmf_mlp* m, float* host, int64_t n);
 lmf_status lmf_mlp_set_params(lmf_mlp* m, const float* host, int64_t n);
-/* Input standardisation (x - mean) / std and output scale y = y_std * out + y_mean. */
+/* Input standardisation (x - mean) / std (host arrays of in_dim floats, std > 0)
+ * and output scale y = y_std * out + y_mean (y_std > 0). */
 lmf_status lmf_mlp_set_norm(lmf_mlp* m, const float* mean, const float* std, float y_mean, float y_std);
 /* Predictions for `batch` feature rows x_dev[batch][in] (device) into y_dev[batch] (device). */
 lmf_status lmf_mlp_forward(lmf_mlp* m, const float* x_dev, int batch, float* y_dev);
@@ -332,14 +364,15 @@ lmf_status lmf_mlp_train_step(lmf_mlp* m, const float* x_dev, const float* y_dev
  * Plan the batch with the candidate the model predicts fastest (every
  * candidate is planned to compute its features).  model == NULL falls back to
  * the Sec. 3.3 root rule with *base.  The chosen options go to *chosen (may be
- * NULL).
+ * NULL).  Errors: LMF_ERR_STATE before lmf_declare_join, those of lmf_plan.
  */
 lmf_status lmf_plan_learned(lmf_ctx* ctx, int batch_id, lmf_mlp* model, const lmf_plan_opts* base,
                             lmf_plan_opts* chosen);
 
 /*
- * The covar Gram of one relation, computed without allocating any device
- * memory.  The paper has no counterpart: this entry point exists for callers
+ * The covar Gram of one relation (the covar matrix of Sec. 2, Eq. lr-sigma,
+ * over a single relation), computed without allocating any device memory.
+ * The allocation-free form has no counterpart in the paper: it exists for callers
  * that cannot call cudaMalloc -- code running under a memory pool or custom
  * allocator that forbids outside allocations, code that must avoid the
  * implicit synchronisation an allocation can cause, or a process whose device
@@ -377,10 +410,11 @@ lmf_status lmf_gram_noalloc(const float* const* dev_cols, int ncols, int64_t nro
  */
 lmf_status lmf_wait_selftest(lmf_ctx* ctx);
 
-/* Static text of a status code. */
+/* Static text of a status code (never NULL; unknown codes give "unknown status"). */
 const char* lmf_status_string(lmf_status s);
 
-/* Detail of the last failure on ctx (empty string when none). */
+/* Detail of the last failure on ctx (empty string when none, or for a null
+ * ctx); owned by the context, valid until its next call. */
 const char* lmf_error_message(lmf_ctx* ctx);
 
 #ifdef __cplusplus
