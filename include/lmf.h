@@ -28,6 +28,9 @@
  *     batch needs a plan and has none; a failing CUDA call gives LMF_ERR_CUDA
  *     (LMF_ERR_OOM for a failed allocation).  Outputs are meaningful only on
  *     LMF_OK.
+ *   - LMF_LOG=1 in the environment prints every plan (root, probe groups,
+ *     record sizes, root-scan form and launch shape) and the stage times of
+ *     lmf_run_profiled to stderr.
  */
 #ifndef LMF_H_
 #define LMF_H_

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -780,6 +781,30 @@ extern "C" lmf_status lmf_plan(lmf_ctx* c, int batch_id, const lmf_plan_opts* op
 }
 
 namespace {
+
+// LMF_LOG=1 in the environment: print every plan, and the stage times of
+// profiled runs, to stderr
+bool log_enabled() {
+  const char* e = std::getenv("LMF_LOG");
+  return e && *e && std::strcmp(e, "0") != 0;
+}
+
+void log_plan(const lmf_ctx* c, int batch_id, const Plan& P) {
+  std::fprintf(stderr,
+               "lmf: batch %d planned at root %s: %d views, %d probe groups, z length %d, "
+               "%d Gram / %d grouped / %d filtered aggregates\n",
+               batch_id, c->rels[P.root].name.c_str(), P.n_views, P.rootp.n_grp, P.rootp.m, P.n_gram,
+               P.n_grouped, P.n_filtered);
+  for (const GroupH& g : P.groups)
+    std::fprintf(stderr, "lmf:   probe group %s.%s: %d keys, %d-byte records (%d counts, %d means, %d categories)\n",
+                 c->rels[g.owner].name.c_str(), g.fk.c_str(), g.K, g.stride * 4, g.n_cnt, g.n_mu, g.n_cat);
+  std::fprintf(stderr,
+               "lmf:   root scan: %s Gram, %s, grid %d, %zu B shared memory per CTA, resident group %d "
+               "(%d cells), %d reverse views, %d category views; plan arena %zu bytes\n",
+               P.tc ? "split-bf16 tcgen05" : "FP32 CUDA-core", (P.jit_plain || P.jit_tc) ? "compiled" : "interpreted",
+               P.grid, P.smem, P.rootp.res_cells > 0 ? P.rootp.res_grp : -1, P.rootp.res_cells, P.rootp.n_rv,
+               P.rootp.n_cv, P.arena.size);
+}
 
 lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, int root) {
   cudaSetDevice(c->device);
@@ -1598,6 +1623,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   }
   P->n_views = (int)P->post.size();
   P->root_scan = !P->maps.empty();
+  if (log_enabled()) log_plan(c, batch_id, *P);
   B.plan = std::move(P);
   return LMF_OK;
 }
@@ -1880,6 +1906,9 @@ lmf_status lmf_run_profiled(lmf_ctx* c, int batch_id, void* cuda_stream, float* 
   if (st == LMF_OK) {
     CUDA_TRY(c, cudaEventSynchronize(ev.e[LMF_STAGES]));
     for (int i = 0; i < LMF_STAGES; ++i) cudaEventElapsedTime(&stage_ms[i], ev.e[i], ev.e[i + 1]);
+    if (log_enabled())
+      std::fprintf(stderr, "lmf: batch %d run: input %.3f, views %.3f, root scan %.3f, tree %.3f, finalize %.3f ms\n",
+                   batch_id, stage_ms[0], stage_ms[1], stage_ms[2], stage_ms[3], stage_ms[4]);
   }
   return st;
 }
