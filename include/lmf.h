@@ -199,11 +199,14 @@ lmf_status lmf_register_relation(lmf_ctx* ctx, const char* name, int64_t nrows,
  * edges must form a tree over all registered relations; its root is the
  * relation that is nobody's child.  Child keys are indexed here (the engine's
  * analogue of load time, Sec. 4 setup: not part of a run): key range and
- * multiplicity are measured on the device.
+ * multiplicity are measured on the device.  Keys index arrays directly; an
+ * attribute whose child keys are too sparse for that (max key >= 4 * rows +
+ * 4096) is renumbered once, in engine-owned device copies of its columns on
+ * both sides of its edges, by each value's rank among the distinct child keys
+ * (values no child holds never join); the borrowed columns are not written.
  * Errors: LMF_ERR_NOT_TREE, LMF_ERR_ARG (unknown attribute), LMF_ERR_DTYPE,
- * LMF_ERR_KEY (negative keys, or keys too sparse for direct addressing:
- * max key >= 4 * rows + 4096), LMF_ERR_UNSUPPORTED (two relations sharing
- * an attribute other than their edge key).
+ * LMF_ERR_KEY (negative child keys), LMF_ERR_UNSUPPORTED (two relations
+ * sharing an attribute other than their edge key), LMF_ERR_OOM.
  */
 lmf_status lmf_declare_join(lmf_ctx* ctx, int n_edges, const int* parent_rel,
                             const int* child_rel, const char* const* key_attr);

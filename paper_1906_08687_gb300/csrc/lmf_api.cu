@@ -14,6 +14,7 @@
 #include "lmf.h"
 #include "lmf_internal.h"
 #include "lmf_jit.h"
+#include "lmf_keymap.h"
 #include "lmf_tree.h"
 #include "lmf_gram_tc.h"
 
@@ -39,7 +40,11 @@ struct ColumnH {
   const void* data;      // user pointer
   void* dev = nullptr;   // device copy of a host column
   const void* mapped = nullptr;  // LMF_HOST_MAPPED: the device's address of the host data
-  const void* dptr() const { return on_host == LMF_HOST_COPY ? dev : on_host == LMF_HOST_MAPPED ? mapped : data; }
+  void* remap = nullptr;  // engine-owned renumbered copy of a sparse join key (lmf_keymap.cu)
+  const void* dptr() const {
+    if (remap) return remap;
+    return on_host == LMF_HOST_COPY ? dev : on_host == LMF_HOST_MAPPED ? mapped : data;
+  }
   size_t esize() const { return dtype == LMF_F64 ? 8 : 4; }
 };
 
@@ -245,6 +250,77 @@ void free_plan(Plan* p) {
   if (p) p->release();
 }
 
+// min and max of an int32 device column (n > 0) through the scratch pair mm
+lmf_status key_range(lmf_ctx* c, const int32_t* col, int64_t n, int* mm, int out[2]) {
+  int h_mm[2] = {0x7fffffff, -0x7fffffff - 1};
+  CUDA_TRY(c, cudaMemcpy(mm, h_mm, sizeof(h_mm), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, launch_key_stats(col, n, nullptr, 0, mm, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(h_mm, mm, sizeof(h_mm), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  out[0] = h_mm[0];
+  out[1] = h_mm[1];
+  return LMF_OK;
+}
+
+// Join attribute `a` has child keys too sparse for direct addressing: every
+// column of that name on either side of an edge keyed on it gets an
+// engine-owned copy holding the rank of its values among the distinct child
+// keys (lmf_keymap.cu), so the key index stays a direct-addressed array.
+lmf_status renumber_attribute(lmf_ctx* c, const std::string& a, int* mm) {
+  std::vector<std::pair<int, int>> cols;  // (relation, column): child sides first
+  auto add = [&](int r, int col) {
+    for (auto& x : cols)
+      if (x.first == r && x.second == col) return;
+    cols.push_back({r, col});
+  };
+  const int nrel = (int)c->rels.size();
+  for (int ch = 0; ch < nrel; ++ch)
+    if (c->rels[ch].parent >= 0 && c->rels[ch].key == a) add(ch, c->rels[ch].find(a));
+  const int n_child = (int)cols.size();
+  for (int ch = 0; ch < nrel; ++ch)
+    if (c->rels[ch].parent >= 0 && c->rels[ch].key == a) {
+      const int p = c->rels[ch].parent;
+      add(p, c->rels[p].find(a));
+    }
+  int max_key = -1;
+  for (int i = 0; i < n_child; ++i) {
+    const RelationH& R = c->rels[cols[i].first];
+    if (R.nrows == 0) continue;
+    int mmv[2];
+    lmf_status st = key_range(c, static_cast<const int32_t*>(R.cols[cols[i].second].dptr()), R.nrows, mm, mmv);
+    if (st) return st;
+    if (mmv[0] < 0) return fail(c, LMF_ERR_KEY, "relation %s: negative key %d", R.name.c_str(), mmv[0]);
+    max_key = std::max(max_key, mmv[1]);
+  }
+  if (max_key < 0) return LMF_OK;  // no child rows
+  std::vector<const int32_t*> in;
+  std::vector<int64_t> rows;
+  std::vector<int32_t*> out;
+  struct Owned {
+    std::vector<int32_t*>* v;
+    bool keep = false;
+    ~Owned() {
+      if (!keep)
+        for (int32_t* p : *v)
+          if (p) cudaFree(p);
+    }
+  } owned{&out};
+  for (auto& [r, col] : cols) {
+    const RelationH& R = c->rels[r];
+    int32_t* d = nullptr;
+    if (R.nrows > 0) CUDA_TRY(c, cudaMalloc(&d, sizeof(int32_t) * (size_t)R.nrows));
+    in.push_back(static_cast<const int32_t*>(R.cols[col].dptr()));
+    rows.push_back(R.nrows);
+    out.push_back(d);
+  }
+  int64_t n_keys = 0;
+  CUDA_TRY(c, keymap_renumber(in.data(), rows.data(), (int)cols.size(), n_child, max_key, out.data(), &n_keys,
+                              c->stream));
+  for (size_t i = 0; i < cols.size(); ++i) c->rels[cols[i].first].cols[cols[i].second].remap = out[i];
+  owned.keep = true;
+  return LMF_OK;
+}
+
 // which relation holds attribute `a` (non-key attributes are unique)
 int owner_of(const lmf_ctx* c, const std::string& a, int* col) {
   for (size_t r = 0; r < c->rels.size(); ++r) {
@@ -311,8 +387,10 @@ lmf_status lmf_destroy(lmf_ctx* c) {
   for (auto& b : c->batches)
     if (b && b->plan) free_plan(b->plan.get());
   for (auto& r : c->rels)
-    for (auto& col : r.cols)
+    for (auto& col : r.cols) {
       if (col.dev) cudaFree(col.dev);
+      if (col.remap) cudaFree(col.remap);
+    }
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return LMF_OK;
@@ -463,6 +541,7 @@ lmf_status lmf_declare_join(lmf_ctx* c, int n_edges, const int* parent_rel, cons
   DevScratch mm_buf;
   CUDA_TRY(c, cudaMalloc(&mm_buf.p, 2 * sizeof(int)));
   int* mm = mm_buf.as<int>();
+  std::set<std::string> renumbered;  // attributes whose keys were renumbered
   for (int ch = 0; ch < n; ++ch) {
     RelationH& R = c->rels[ch];
     if (R.parent < 0) continue;
@@ -478,9 +557,14 @@ lmf_status lmf_declare_join(lmf_ctx* c, int n_edges, const int* parent_rel, cons
     CUDA_TRY(c, cudaMemcpyAsync(h_mm, mm, sizeof(h_mm), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (h_mm[0] < 0) return fail(c, LMF_ERR_KEY, "relation %s: negative key %d", R.name.c_str(), h_mm[0]);
-    if ((int64_t)h_mm[1] >= 4 * R.nrows + 4096) {
-      return fail(c, LMF_ERR_KEY, "relation %s: keys too sparse for direct addressing (max %d, %lld rows)",
-                  R.name.c_str(), h_mm[1], (long long)R.nrows);
+    if ((int64_t)h_mm[1] >= 4 * R.nrows + 4096 && !renumbered.count(R.key)) {
+      // too sparse for direct addressing: renumber the attribute and start
+      // the index again (children indexed so far may share it)
+      lmf_status st = renumber_attribute(c, R.key, mm);
+      if (st) return st;
+      renumbered.insert(R.key);
+      ch = -1;
+      continue;
     }
     R.K = h_mm[1] + 1;
     DevScratch hist_buf;
@@ -1643,7 +1727,7 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
   // host-resident columns are copied in first
   for (auto& r : c->rels)
     for (auto& col : r.cols)
-      if (col.on_host == LMF_HOST_COPY && r.nrows > 0)
+      if (col.on_host == LMF_HOST_COPY && !col.remap && r.nrows > 0)
         CUDA_TRY(c, cudaMemcpyAsync(col.dev, col.data, (size_t)r.nrows * col.esize(), cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemsetAsync(P->arena.base + P->zero_off, 0, P->zero_len, s));
   mark(1);
