@@ -26,7 +26,7 @@ from oracle_pinlib import (assert_close, brute_force, check_against_brute_force,
                            check_compensated_sum, shared_attribute_schema)
 from workloads import (Agg, Column, Relation, Schema, chain_schema, config1, config2,
                        config3, config4, covar_batch, cube_batch, pair_count_batch,
-                       tiny_schema)
+                       spread_keys, tiny_schema)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), 'golden')
 
@@ -58,6 +58,21 @@ def test_join_on_two_shared_attributes(seed):
     _, size, _ = brute_force(sch, [Agg()])
     _, size_key_only, _ = brute_force(key_only, [Agg()])
     assert size_key_only > size > 0
+
+
+@pytest.mark.parametrize('seed', list(range(8)))
+def test_sparse_keys_same_results(seed):
+    """An injective relabelling of the join keys (values ~1e6 apart) changes
+    no aggregate: the join depends on key equality only (Sec. 1.1)."""
+    sch, batch = tiny_schema(1000 + seed)
+    sp = spread_keys(sch)
+    assert all(c.data.max() > 1_000_000 for r in sp.relations for c in r.columns
+               if c.role == 'key' and r.nrows and c.data.max() > 0)
+    check_against_brute_force(sp, batch, nthreads=1 + seed % 3)
+    a, b = oracle.evaluate(sch, batch), oracle.evaluate(sp, batch)
+    assert a.join_size == b.join_size
+    for x, y in zip(a.values, b.values):
+        assert np.array_equal(x, y)
 
 
 @pytest.mark.parametrize('nthreads', [1, 3])

@@ -428,6 +428,27 @@ def config5_schema(index: int, n_scale: float = 1.0, seed: Optional[int] = None
     return sch, batch
 
 
+def spread_keys(sch: Schema, mult: int = 1_000_003, offset: int = 7) -> Schema:
+    """The same database with every join-key value k >= 0 replaced by
+    k * mult + offset (negative values kept): an injective relabelling, so
+    every aggregate keeps its value, but keys far too sparse to index an array
+    directly (int32 range permitting)."""
+    keys = {k for _, _, k in sch.edges}
+    rels = []
+    for r in sch.relations:
+        cols = []
+        for c in r.columns:
+            if c.name in keys:
+                v = c.data.astype(np.int64)
+                v = np.where(v >= 0, v * mult + offset, v)
+                if v.size and v.max() > np.iinfo(np.int32).max:
+                    raise ValueError(f'{r.name}.{c.name}: spread keys overflow int32')
+                c = dataclasses.replace(c, data=v.astype(np.int32))
+            cols.append(c)
+        rels.append(Relation(r.name, cols))
+    return Schema(rels, list(sch.edges), sch.root, meta=dict(sch.meta))
+
+
 # ----------------------------------------------------------------------------
 # tiny schemas for brute-force tests
 # ----------------------------------------------------------------------------
