@@ -228,3 +228,39 @@ def test_planted_mistake_is_caught(what, old, new):
         for k, v in saved.items():
             setattr(consumers, k, v)
     assert failed, what
+
+
+def test_chow_liu_over_the_oracle_batch_of_config4():
+    """The whole Chow-Liu application of Sec. 2 on a small config-4 instance:
+    MI of all 435 category pairs from the oracle's count batch, then the tree;
+    the same tree as from a library MI of the materialised join's columns and
+    a library maximum spanning tree."""
+    metrics = pytest.importorskip('sklearn.metrics')
+    nx = pytest.importorskip('networkx')
+    sch, batch = config4(5000)
+    cats = sch.meta['cats']
+    res = oracle.evaluate(sch, batch)
+    by_gb = {agg.group_by: (res.values[i], res.shapes[i]) for i, agg in enumerate(batch)}
+    alpha = float(sch.rel('F').nrows)
+    mi = {}
+    for i in range(len(cats)):
+        for j in range(i + 1, len(cats)):
+            beta, gamma = by_gb[(cats[i],)][0], by_gb[(cats[j],)][0]
+            vals, shape = by_gb[(cats[i], cats[j])]
+            delta = vals.reshape(shape)
+            kb, kg = beta > 0, gamma > 0
+            mi[(i, j)] = consumers.mutual_information(alpha, beta[kb], gamma[kg], delta[kb][:, kg])
+    tree = consumers.chow_liu_tree(len(cats), mi)
+    F = sch.rel('F')
+    cols = []
+    for c in cats:
+        d = next(r for r in sch.relations if c in r.names())
+        key = d.columns[0].name
+        cols.append(d.col(c).data[F.col(key).data])
+    G = nx.Graph()
+    for (i, j) in mi:
+        w = metrics.mutual_info_score(cols[i], cols[j])
+        assert abs(w - mi[(i, j)]) < 1e-12
+        G.add_edge(i, j, weight=w)
+    want = sorted(tuple(sorted(e)) for e in nx.maximum_spanning_tree(G).edges())
+    assert sorted(tree) == want
