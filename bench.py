@@ -77,6 +77,9 @@ def parse():
     ap.add_argument('--check-aggs', type=int, default=None,
                     help='aggregates re-evaluated by the oracle over the full join (0: skip, -1: all)')
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--shard', action='store_true',
+                    help='one instance sharded over the ranks by root row ranges, partial results combined '
+                         'by one all-reduce per result array (strong scaling); default: one instance per rank')
     args = ap.parse_args()
     gen, idx, n, cpu_rows, ref_rows, check, prof = WORKLOADS[args.workload]
     args.gen, args.cfg_index = gen, idx
@@ -295,10 +298,79 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
+def run_sharded(args):
+    """One instance of the workload sharded over the ranks: rank r registers the
+    root rows row_range(N, r, world) with the dimensions whole, runs the batch
+    and exports its packed results to device buffers, and one all-reduce (sum)
+    per result array combines them (paper_1906_08687_gb300.shard).  A step is
+    run + export + all-reduce; the step time is the maximum over ranks."""
+    ws, rank, local = dist_env()
+    import torch
+    import torch.distributed as dist
+    if ws > 1:
+        dist.init_process_group('nccl')
+    torch.cuda.set_device(local)
+    from paper_1906_08687_gb300 import build as engine_build
+    engine_build.build()
+    from paper_1906_08687_gb300 import Engine, register_schema, shard
+    from workloads import to_device
+    sch, batch = make_workload(args, 0)            # the same instance on every rank
+    n = sch.rel(sch.root).nrows
+    b, e = shard.row_range(n, rank, ws)
+    dev = to_device(sch, f'cuda:{local}')
+    eng = Engine(local)
+    register_schema(eng, shard.shard_schema(sch, b, e), shard.shard_tensors(sch, dev, b, e))
+    bid = eng.declare_batch(batch)
+    eng.plan(bid, precision=0, batching=1)
+    info = eng.plan_info(bid)
+    n_i, n_f = eng.result_sizes(bid)
+    i64 = torch.zeros(max(1, n_i), dtype=torch.int64, device=f'cuda:{local}')
+    f64 = torch.zeros(max(1, n_f), dtype=torch.float64, device=f'cuda:{local}')
+    stream = torch.cuda.Stream()
+    reduce = dist.all_reduce if ws > 1 else (lambda t: t)
+
+    def step():
+        eng.run(bid, stream.cuda_stream)
+        eng.read_results(bid, i64.data_ptr(), f64.data_ptr(), True, stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            shard.allreduce_packed(i64[:n_i], f64[:n_f], reduce)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ws, e0.elapsed_time(e1) / args.steps)
+    eng.sync(bid)
+    value = n * len(batch) / (ms * 1e-3) / 1e9
+    line = {'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': ws, 'steps': args.steps,
+            'warmup': args.warmup, 'ms_per_step': ms, 'higher_is_better': True, 'scaling': 'strong',
+            'vs_baseline': None, 'dtype': 'f32', 'data': 'synthetic',
+            'config': {'workload': WORKLOAD_TEXT.get(args.workload, '{name}').format(name=sch.meta['name']),
+                       'n_aggregates': len(batch), 'join_rows': n, 'rows_per_rank': e - b,
+                       'key_level': info['key_level'],
+                       'parallelism': f'root row ranges x{ws}, one all-reduce per result array '
+                                      f'({n_i} int64 + {n_f} float64 cells)'},
+            'gpu_launches': info['n_kernels_per_run'] * args.steps}
+    eng.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == 'reference':
         return run_reference(args)
+    if args.shard:
+        return run_sharded(args)
     ws, rank, local = dist_env()
     import numpy as np
     import torch
@@ -306,12 +378,11 @@ def main():
         import torch.distributed as dist
         dist.init_process_group('nccl')
     torch.cuda.set_device(local)
-    sys.path.insert(0, os.path.join(ROOT, 'tests'))
     from paper_1906_08687_gb300 import build as engine_build
     engine_build.build()
     from paper_1906_08687_gb300 import Engine, register_schema
     from paper_1906_08687_gb300.lmf import STAGE_NAMES
-    from lmf_testlib import compare, to_device, to_pinned
+    from workloads import to_device, to_pinned
 
     sch, batch = make_workload(args, rank)
     n_agg = len(batch)
@@ -474,10 +545,12 @@ def main():
             pick = list(range(n_agg))
         else:
             pick = sorted(set([0] + list(rng.choice(n_agg, size=args.check_aggs, replace=False))))
+        from oracle.compare import compare, compare_by_kind
         want = oracle.evaluate(sch, [batch[i] for i in pick])
         fails, stats = compare([got[i] for i in pick], want)
         line['accuracy'] = {'checked_aggregates': len(pick), 'failures': len(fails), **stats,
-                            'rule': '|g-r| <= 1e-6*max(|r|, 1e-3*sum|v|); counts exact'}
+                            'rule': '|g-r| <= 1e-6*max(|r|, 1e-3*sum|v|); counts exact',
+                            'by_kind': compare_by_kind([batch[i] for i in pick], [got[i] for i in pick], want)}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line['cpu_baseline'] = cpu_baseline(sch, batch, args.n_fact, args.cpu_sample_rows,

@@ -135,6 +135,16 @@ typedef struct {
    with NVRTC) unless this bit is set or NVRTC cannot be loaded; the
    interpreted kernel (same arithmetic, same results) runs otherwise. */
 #define LMF_PLAN_NO_JIT 1
+/* lmf_plan_opts.flags: keep every Gram block of the plain-precision root scan at
+   the row level (FP32 products of the whole z = [1, x_root, view means]).  By
+   default a plan whose child keys are all unique takes the key-level form: the
+   scan sums only the products of two root features row by row and builds, per
+   probe group, the reverse view (count and sums of the features the group's
+   Gram blocks and grouped outputs need); every block with a view mean is then
+   sum_k m(k) R[k][.] over the group's keys (the aggregate at the group's own
+   root, Sec. 3.3).  Same results within the error rule; needs the plan-time
+   compiler. */
+#define LMF_PLAN_ROW_GRAM 2
 
 /* Statistics of a plan, for reporting (lmf_plan_info). */
 typedef struct {
@@ -163,7 +173,7 @@ typedef struct {
                                  that foreign key), -1: none */
   int32_t resident_cells;     /* shared-memory counters of the resident-key tables */
   int32_t jit;                /* 1: the root scan runs a kernel compiled for this plan */
-  int32_t reserved_stats;
+  int32_t key_level;          /* 1: key-level Gram blocks (see LMF_PLAN_ROW_GRAM) */
 } lmf_plan_stats;
 
 /*
@@ -204,6 +214,11 @@ lmf_status lmf_register_relation(lmf_ctx* ctx, const char* name, int64_t nrows,
  * 4096) is renumbered once, in engine-owned device copies of its columns on
  * both sides of its edges, by each value's rank among the distinct child keys
  * (values no child holds never join); the borrowed columns are not written.
+ * Those copies are a snapshot: later runs read the renumbered copies, so
+ * changes the caller makes to the key columns of a renumbered attribute after
+ * this call are not seen (declare the join again on a new context instead).
+ * Columns of dense-key attributes and all other columns are read live by every
+ * run.
  * Errors: LMF_ERR_NOT_TREE, LMF_ERR_ARG (unknown attribute), LMF_ERR_DTYPE,
  * LMF_ERR_KEY (negative child keys), LMF_ERR_UNSUPPORTED (two relations
  * sharing an attribute other than their edge key), LMF_ERR_OOM.

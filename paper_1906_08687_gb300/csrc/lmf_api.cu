@@ -153,6 +153,24 @@ struct Plan {
   std::vector<GroupGram> ggram;
   size_t ggram_off = 0, ggram_part_off = 0;
   static constexpr int kGgChunks = 2048;  // key ranges (one warp each) of the key-level Gram
+  // key-level plan (lmf_root_lean.cuh): the row Gram covers the root's
+  // features only, every block with a view mean comes from CrossGram /
+  // GroupGram over the reverse views
+  bool lean = false;
+  int lean_mpx = 4;
+  std::vector<CrossGram> cgram;
+  std::vector<CrossPair> cpairs;
+  std::vector<FixMeans> fixm;    // per root group with fixed-point mean images
+  // work items of the key-level tasks and the final placement, in `aux`
+  std::vector<RvItem> rv_items;
+  std::vector<CvPairItem> cv_pair_items;
+  std::vector<CvMeanItem> cv_mean_items;
+  std::vector<OutItem> out_items;
+  int rv_item_cells = 0, cv_pair_cells = 0;
+  bool rv_wide = false;          // some reverse-view task is too wide for a block's table
+  void* aux = nullptr;
+  size_t aux_rv = 0, aux_cvp = 0, aux_cvm = 0, aux_out = 0;
+  size_t cgram_off = 0, cpair_off = 0, cgram_part_off = 0;
   size_t cvtask_off = 0;
   int64_t cv_max_cells = 0;
   std::vector<DirectAgg> direct;
@@ -165,7 +183,7 @@ struct Plan {
   // tensor-core Gram
   std::unique_ptr<GramTcPlan> tc;
   // root scan compiled for this plan (null: the interpreted kernel)
-  cudaKernel_t jit_plain = nullptr, jit_tc = nullptr;
+  cudaKernel_t jit_plain = nullptr, jit_tc = nullptr, jit_lean = nullptr;
   // results
   int64_t n_i64 = 0, n_f64 = 0;
   size_t res_i64_off = 0, res_f64_off = 0;
@@ -194,6 +212,8 @@ struct Plan {
     if (graph) cudaGraphDestroy(graph);
     if (graph_stream) cudaStreamDestroy(graph_stream);
     if (arena.base) cudaFree(arena.base);
+    if (aux) cudaFree(aux);
+    aux = nullptr;
     exec = nullptr;
     graph = nullptr;
     graph_stream = nullptr;
@@ -885,7 +905,8 @@ void log_plan(const lmf_ctx* c, int batch_id, const Plan& P) {
   std::fprintf(stderr,
                "lmf:   root scan: %s Gram, %s, grid %d, %zu B shared memory per CTA, resident group %d "
                "(%d cells), %d reverse views, %d category views; plan arena %zu bytes\n",
-               P.tc ? "split-bf16 tcgen05" : "FP32 CUDA-core", (P.jit_plain || P.jit_tc) ? "compiled" : "interpreted",
+               P.tc ? "split-bf16 tcgen05" : P.lean ? "key-level, root-feature FP32" : "FP32 CUDA-core",
+               (P.jit_plain || P.jit_tc || P.jit_lean) ? "compiled" : "interpreted",
                P.grid, P.smem, P.rootp.res_cells > 0 ? P.rootp.res_grp : -1, P.rootp.res_cells, P.rootp.n_rv,
                P.rootp.n_cv, P.arena.size);
 }
@@ -1064,6 +1085,13 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     }
   }
 
+  // ---- key-level form (lmf_root_lean.cuh): every child key unique, plain
+  // precision, a compiled scan, at least one probe group and one feature
+  P->lean = P->unique_all && rp.n_grp >= 1 && m > 1 && Root.nrows > 0 &&
+            P->opts.precision == LMF_PREC_PLAIN_FP32 && !(P->opts.flags & (LMF_PLAN_NO_JIT | LMF_PLAN_ROW_GRAM)) &&
+            jit_available();
+  std::vector<size_t> deferred;   // grouped sums of another group's mean, placed with the carriers
+
   // ---- grouped aggregates
   std::vector<size_t> rv_hist_off(rp.n_grp, 0), rv_R_off(rp.n_grp, 0);
   std::vector<std::vector<int>> rv_slots(rp.n_grp);     // z index per slot
@@ -1072,6 +1100,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     int mode; int grp; int slot; int mu_word; int direct; double scale; int64_t cells; size_t out_off; int cache_off;
     int res_off, res_q, res_word, res_n, res_lanes;
     int cv, cv_aword, cv_afirst, cv_doma;  // COUNT table read off category view cv (-1: none)
+    int cv_mode, cv_muword;                // 1: SUM of a mean of the view's keying group grouped by b
   };
   // category views: (keying group, row category of b) -> view
   struct CvPlan { int grp, bcat, bgrp, dom; size_t off; int res_off; };
@@ -1093,6 +1122,8 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     gp.cache_off = -1;
     gp.res_off = -1;
     gp.cv = -1;
+    gp.cv_mode = 0;
+    gp.cv_muword = -1;
     gp.cells = cells;
     gp.direct = (gsrc < 0) ? 1 : 0;   // root categories or several keys: per-row table
     if (gp.direct && cls[a].mono.empty() && ag.gb.size() == 2 && P->unique_all) {
@@ -1149,6 +1180,10 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
         gp.mode = 2;
         GroupH& g = P->groups[RR.groups[gsrc]];
         gp.mu_word = g.n_cnt + (P->zidx.at(f) - rp.grp_zoff[gsrc]);
+      } else if (P->lean && P->feat_group.at(f) >= 0) {
+        gp.mode = 1;  // a mean of another group: a slot of this view, or a category view (below)
+        gp.slot = -1;
+        deferred.push_back(a);
       } else {
         gp.mode = 1;
         auto& sl = rv_slots[gsrc];
@@ -1167,11 +1202,139 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   // add the same products over and over)
   for (int q = 0; q < rp.n_grp; ++q)
     if (P->groups[RR.groups[q]].n_mu > 0 && has_runs[q]) rv_used[q] = 1;
+
+  // ---- key-level form: where every Gram block with a view mean comes from.
+  // (x, m_g): the root feature x as a slot of g's reverse view; (m_g, m_h):
+  // the carrier's view holds the other group's mean (the carrier is the
+  // resident key, else the key with fewer changes, else with fewer keys);
+  // (1, x): the root feature's sum from the view with the fewest keys; (m_g,
+  // m_g) and (1, m_g): GroupGram over g's key counts; (x, x): the row Gram.
+  struct LeanPair {
+    int q, z_slot, mean_i, za, zb;
+  };
+  std::vector<LeanPair> lean_pairs;
+  std::vector<int> rv_mode(rp.n_grp, kRvRuns);
+  if (P->lean) {
+    auto n_mu_of = [&](int q) { return P->groups[RR.groups[q]].n_mu; };
+    auto zgroup = [&](int z) -> int {
+      for (int q = 0; q < rp.n_grp; ++q)
+        if (z >= rp.grp_zoff[q] && z < rp.grp_zoff[q] + n_mu_of(q)) return q;
+      return -1;  // the constant or a root feature
+    };
+    auto rank = [&](int q) {
+      return std::make_tuple(q == res_grp ? 0 : 1, changes[q], P->groups[RR.groups[q]].K, q);
+    };
+    auto carrier = [&](int g, int h) { return rank(g) < rank(h) ? g : h; };
+    auto add_slot = [&](int q, int z) {
+      auto& sl = rv_slots[q];
+      auto it = std::find(sl.begin(), sl.end(), z);
+      if (it == sl.end()) sl.push_back(z);
+    };
+    std::set<std::pair<int, int>> need;
+    for (size_t a = 0; a < B.aggs.size(); ++a) {
+      if (cls[a].kind != 0 || cls[a].mono.empty()) continue;
+      int i = cls[a].mono.size() == 2 ? P->zidx.at(cls[a].mono[0]) : 0;
+      int j = P->zidx.at(cls[a].mono.back());
+      if (i > j) std::swap(i, j);
+      need.insert({i, j});
+    }
+    int sum_q = 0;
+    for (int q = 1; q < rp.n_grp; ++q)
+      if (P->groups[RR.groups[q]].K < P->groups[RR.groups[sum_q]].K) sum_q = q;
+    for (auto& ij : need) {
+      const int i = ij.first, j = ij.second, gi = zgroup(i), gj = zgroup(j);
+      if (i == 0) {
+        if (gj < 0) lean_pairs.push_back({sum_q, j, -1, 0, j});
+        continue;  // (1, m_g): GroupGram
+      }
+      if (gi < 0 && gj < 0) continue;  // row Gram
+      if (gi < 0) {
+        lean_pairs.push_back({gj, i, j - rp.grp_zoff[gj], i, j});
+        continue;
+      }
+      if (gi == gj) continue;  // GroupGram
+      const int cq = carrier(gi, gj);
+      const int carried = cq == gi ? j : i, own = cq == gi ? i : j;
+      lean_pairs.push_back({cq, carried, own - rp.grp_zoff[cq], i, j});
+    }
+    // root features first in every view, then carried means
+    for (auto& lp : lean_pairs)
+      if (zgroup(lp.z_slot) < 0) add_slot(lp.q, lp.z_slot);
+    for (auto& lp : lean_pairs)
+      if (zgroup(lp.z_slot) >= 0) add_slot(lp.q, lp.z_slot);
+    // grouped sums of another group h's mean, grouped by a category of g: a
+    // slot g's view already holds, else a category view keyed by h keeping
+    // the category (count x mean over h's keys), else a new slot
+    for (size_t a : deferred) {
+      GPlan& gp = gplan[a];
+      const std::string& f = cls[a].mono[0];
+      const int h = P->feat_group.at(f), z = P->zidx.at(f);
+      auto& sl = rv_slots[gp.grp];
+      auto it = std::find(sl.begin(), sl.end(), z);
+      if (it != sl.end()) {
+        gp.slot = (int)(it - sl.begin());
+        continue;
+      }
+      auto cv = cv_index.find({h, P->rowcat.at(B.aggs[a].gb[0])});
+      if (B.aggs[a].gb.size() == 1 && cv != cv_index.end()) {
+        gp.cv = cv->second;
+        gp.cv_mode = 1;
+        gp.cv_muword = P->groups[RR.groups[h]].n_cnt + (z - rp.grp_zoff[h]);
+        continue;
+      }
+      gp.slot = (int)sl.size();
+      sl.push_back(z);
+    }
+    // every group with means keeps its key counts (GroupGram); update modes:
+    // the resident key in registers, keys in runs summed per run, the rest one
+    // bulk reduction per row while the staging fits (16 words a row)
+    int stage_words = 0;
+    for (int q = 0; q < rp.n_grp; ++q) {
+      if (n_mu_of(q) > 0 || !rv_slots[q].empty()) rv_used[q] = 1;
+      if (!rv_used[q]) continue;
+      const int stride = (int)(1 + rv_slots[q].size() + 1) & ~1;
+      if (q == res_grp) {
+        rv_mode[q] = kRvResident;
+      } else if (has_runs[q] || stage_words + stride > 16) {
+        rv_mode[q] = kRvRuns;
+      } else {
+        rv_mode[q] = kRvBulk;
+        stage_words += stride;
+      }
+    }
+  }
   for (int q = 0; q < rp.n_grp; ++q) {
     if (!rv_used[q]) continue;
     GroupH& g = P->groups[RR.groups[q]];
+    if (P->lean) {  // one record per key: [count, slots], an even number of int64 words
+      const size_t stride = (1 + rv_slots[q].size() + 1) & ~(size_t)1;
+      rv_hist_off[q] = A.take((size_t)g.K * stride * 8);
+      rv_R_off[q] = rv_hist_off[q] + 8;
+      continue;
+    }
     rv_hist_off[q] = A.take((size_t)g.K * 8);
     rv_R_off[q] = A.take((size_t)g.K * rv_slots[q].size() * 8 + 8);
+  }
+  // key-level form: the exact fixed-point image of every mean a view sums,
+  // once per key (k_fix_means), so that the scan does not convert it per row
+  std::vector<std::vector<int>> fix_z(rp.n_grp);
+  std::vector<size_t> fix_off(rp.n_grp, 0);
+  for (int i = 0; i < kMaxZ; ++i) rp.fix_of_z[i] = -1;
+  if (P->lean) {
+    // (a count times a mean's image would multiply the image's rounding by the
+    // count: key-level tasks round the exact product instead)
+    std::set<int> slot_z;
+    for (int q = 0; q < rp.n_grp; ++q)
+      for (int z : rv_slots[q]) slot_z.insert(z);
+    for (int q = 0; q < rp.n_grp; ++q) {
+      const GroupH& g = P->groups[RR.groups[q]];
+      for (int z : slot_z)
+        if (z >= rp.grp_zoff[q] && z < rp.grp_zoff[q] + g.n_mu) {
+          rp.fix_of_z[z] = (int16_t)fix_z[q].size();
+          fix_z[q].push_back(z);
+        }
+      if (!fix_z[q].empty()) fix_off[q] = A.take((size_t)g.K * ((fix_z[q].size() + 1) & ~(size_t)1) * 8 + 16);
+    }
   }
   for (size_t a = 0; a < B.aggs.size(); ++a)
     if (cls[a].kind == 1) gplan[a].out_off = A.take((size_t)gplan[a].cells * 8);
@@ -1234,8 +1397,63 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   int mp0 = 16;
   while (mp0 < m) mp0 += 16;
   const bool tc_planned = P->opts.precision == LMF_PREC_SPLIT_BF16 && gram_tc_supported(m) && P->unique_all;
-  const size_t base_smem = tc_planned ? gram_tc_smem(ncat, 0, 0) : root_plain_smem(mp0, ncat, 0, 0, P->unique_all);
-  const int64_t cell_budget = std::max<int64_t>(0, ((int64_t)108 * 1024 - (int64_t)base_smem) / 4);
+  size_t base_smem = tc_planned ? gram_tc_smem(ncat, 0, 0) : root_plain_smem(mp0, ncat, 0, 0, P->unique_all);
+  int64_t smem_cap = 108 * 1024;
+  // reverse-view descriptors (device pointers are valid once the arena is allocated)
+  std::vector<int> rv_index(rp.n_grp, -1);
+  auto fill_rvs = [&](RootParams& t) -> lmf_status {
+    t.n_rv = 0;
+    t.res_rv = -1;
+    for (int q = 0; q < rp.n_grp; ++q) {
+      if (!rv_used[q]) continue;
+      if ((int)rv_slots[q].size() > kMaxZ - 1) return fail(c, LMF_ERR_UNSUPPORTED, "too many reverse-view slots");
+      RevView& R = t.rv[t.n_rv];
+      R.hist = P->at<unsigned long long>(rv_hist_off[q]);
+      R.R = P->at<long long>(rv_R_off[q]);
+      R.grp = q;
+      R.n_slot = (int)rv_slots[q].size();
+      for (int s2 = 0; s2 < R.n_slot; ++s2) {
+        R.slot_z[s2] = (int16_t)rv_slots[q][s2];
+        std::string fname;
+        for (auto& kv : P->zidx)
+          if (kv.second == rv_slots[q][s2]) fname = kv.first;
+        R.slot_scale[s2] = (float)std::ldexp(1.0, fixp_exp(W * bound[fname]));
+      }
+      if (P->lean) {
+        R.stride = (1 + R.n_slot + 1) & ~1;
+        R.hstride = R.rstride = R.stride;
+        R.mode = rv_mode[q];
+        if (R.mode == kRvResident) t.res_rv = t.n_rv;
+      } else {
+        R.stride = R.n_slot;
+        R.hstride = 1;
+        R.rstride = R.n_slot;
+        R.mode = kRvRuns;
+      }
+      rv_index[q] = t.n_rv++;
+    }
+    return LMF_OK;
+  };
+  int n_direct_planned = 0;
+  bool direct_z = false;
+  for (size_t a = 0; a < B.aggs.size(); ++a)
+    if (cls[a].kind == 1 && gplan[a].direct) {
+      ++n_direct_planned;
+      direct_z = direct_z || !cls[a].mono.empty();
+    }
+  if (P->lean) {  // three CTAs per SM: what the z tile and the bulk staging leave of 74 KB
+    rp.lean = 1;
+    rp.gram_off = 1;
+    rp.gram_n = rp.n_x;
+    RootParams t = rp;
+    t.cache_cells = t.res_cells = 0;
+    t.n_direct = n_direct_planned;
+    lmf_status st = fill_rvs(t);
+    if (st) return st;
+    base_smem = lean_shape(t, direct_z).cache_off;
+    smem_cap = 74 * 1024;
+  }
+  const int64_t cell_budget = std::max<int64_t>(0, (smem_cap - (int64_t)base_smem) / 4);
   const int64_t kResBudget = cell_budget * 3 / 4;
   int res_cells = 0;
   int cv_res_cells = 0;
@@ -1287,7 +1505,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       gplan[a].res_off = res_cells;
       res_cells += gplan[a].res_n * (gplan[a].res_lanes ? 32 : 1);
     }
-    if (res_cells == 0) res_grp = -1;
+    if (res_cells == 0 && !P->lean) res_grp = -1;
   }
 
   // ---- hot-cell cache: per CTA, the hottest (value, value) cells of every
@@ -1375,8 +1593,25 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     CUDA_TRY(c, gram_tc_configure(P->tc.get(), ncat, P->opts.ctas_per_sm, cache_cells, res_cells));
     P->grid = P->tc->grid;
   }
+  if (P->lean) {
+    RootParams t = rp;
+    t.cache_cells = cache_cells;
+    t.res_cells = res_cells;
+    t.n_direct = n_direct_planned;
+    lmf_status st = fill_rvs(t);
+    if (st) return st;
+    const LeanShape L = lean_shape(t, direct_z);
+    P->lean_mpx = L.mpx;
+    P->smem = L.smem;
+    // two CTAs per SM by default: the generated row pass keeps its z values in
+    // registers (128 a thread without spills); three when asked and the shared
+    // memory allows
+    const int lcps = P->opts.ctas_per_sm > 0 ? std::min(P->opts.ctas_per_sm, L.smem <= 74 * 1024 ? 3 : 2)
+                                              : (L.smem <= 110 * 1024 ? 2 : 1);
+    P->grid = (int)std::max<int64_t>(1, std::min<int64_t>(P->n_tiles, (int64_t)c->num_sms * lcps));
+  }
   const int grid_max = std::max(P->grid, grid_jit);
-  P->part_off = A.take((size_t)grid_max * mp * mp * 8);
+  P->part_off = A.take((size_t)grid_max * std::max(mp, P->lean_mpx) * std::max(mp, P->lean_mpx) * 8);
   P->cntp_off = A.take((size_t)grid_max * 8);
   P->G_off = A.take((size_t)m * m * 8);
   P->count_off = A.take(8);
@@ -1414,6 +1649,9 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     }
     P->ggram_off = A.take(sizeof(GroupGram) * (rp.n_grp + 1));
     P->ggram_part_off = A.take(sizeof(double) * (npart * Plan::kGgChunks + 1));
+    P->cgram_off = A.take(sizeof(CrossGram) * (rp.n_grp + 1));
+    P->cpair_off = A.take(sizeof(CrossPair) * (lean_pairs.size() + 1));
+    P->cgram_part_off = A.take(sizeof(double) * (lean_pairs.size() * Plan::kGgChunks + 1));
   }
   P->direct_off = A.take(sizeof(DirectAgg) * n_rvt_est);
   P->corr_off = A.take(sizeof(CorrTask) * (omega.size() + 1));
@@ -1440,30 +1678,34 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     d.n_cnt = g.n_cnt;
     d.n_mu = g.n_mu;
     d.n_cat = g.n_cat;
+    d.fix = nullptr;
+    d.fix_stride = 0;
     return d;
   };
-  for (int q = 0; q < rp.n_grp; ++q) rp.grp[q] = gdesc(RR.groups[q]);
+  for (int q = 0; q < rp.n_grp; ++q) {
+    rp.grp[q] = gdesc(RR.groups[q]);
+    if (fix_z[q].empty()) continue;
+    rp.grp[q].fix = P->at<long long>(fix_off[q]);
+    rp.grp[q].fix_stride = (int)((fix_z[q].size() + 1) & ~(size_t)1);
+    FixMeans f{};
+    f.g = rp.grp[q];
+    f.n = (int)fix_z[q].size();
+    for (int j = 0; j < f.n; ++j) {
+      const int z = fix_z[q][j];
+      f.mu_word[j] = (int16_t)(rp.grp[q].n_cnt + (z - rp.grp_zoff[q]));
+      std::string fname;
+      for (auto& kv : P->zidx)
+        if (kv.second == z) fname = kv.first;
+      f.scale[j] = (float)std::ldexp(1.0, fixp_exp(W * bound[fname]));
+    }
+    P->fixm.push_back(f);
+  }
   rp.gram_part = P->at<double>(P->part_off);
   rp.cnt_part = P->at<long long>(P->cntp_off);
   rp.status = P->at<uint32_t>(P->status_off);
-  rp.n_rv = 0;
-  std::vector<int> rv_index(rp.n_grp, -1);
-  for (int q = 0; q < rp.n_grp; ++q) {
-    if (!rv_used[q]) continue;
-    if ((int)rv_slots[q].size() > kMaxZ) return fail(c, LMF_ERR_UNSUPPORTED, "too many reverse-view slots");
-    RevView& R = rp.rv[rp.n_rv];
-    R.hist = P->at<unsigned long long>(rv_hist_off[q]);
-    R.R = P->at<long long>(rv_R_off[q]);
-    R.grp = q;
-    R.n_slot = (int)rv_slots[q].size();
-    for (int s = 0; s < R.n_slot; ++s) {
-      R.slot_z[s] = (int16_t)rv_slots[q][s];
-      std::string fname;
-      for (auto& kv : P->zidx)
-        if (kv.second == rv_slots[q][s]) fname = kv.first;
-      R.slot_scale[s] = (float)std::ldexp(1.0, fixp_exp(W * bound[fname]));
-    }
-    rv_index[q] = rp.n_rv++;
+  {
+    lmf_status st = fill_rvs(rp);
+    if (st) return st;
   }
   {
     int part = 0;
@@ -1480,6 +1722,27 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       g.part_off = part;
       part += g.npair;
       P->ggram.push_back(g);
+    }
+  }
+  if (P->lean) {  // key-level Gram entries, one CrossGram per view that holds slots for them
+    int part = 0;
+    for (int q = 0; q < rp.n_grp; ++q) {
+      CrossGram g{};
+      g.rv = rv_index[q];
+      g.grp = q;
+      g.mu_word = P->groups[RR.groups[q]].n_cnt;
+      g.pair_off = (int)P->cpairs.size();
+      g.part_off = part;
+      for (auto& lp : lean_pairs) {
+        if (lp.q != q) continue;
+        const auto& sl = rv_slots[q];
+        const int slot = (int)(std::find(sl.begin(), sl.end(), lp.z_slot) - sl.begin());
+        P->cpairs.push_back(CrossPair{(int16_t)slot, (int16_t)lp.mean_i, (int16_t)lp.za, (int16_t)lp.zb});
+      }
+      g.npair = (int)P->cpairs.size() - g.pair_off;
+      if (g.npair == 0) continue;
+      part += g.npair;
+      P->cgram.push_back(g);
     }
   }
   // hot-cell tables: category value -> hot index, and the global cell every
@@ -1521,6 +1784,10 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       t.dom_a = gp.cv_doma;
       t.a_first = gp.cv_afirst;
       t.out = P->at<long long>(gp.out_off);
+      t.mode = gp.cv_mode;
+      t.mu_word = gp.cv_muword;
+      t.scale = (float)gp.scale;
+      t.fix_idx = -1;  // count x mean: one rounding of the exact product per cell (FP64)
       P->cv_tasks.push_back(t);
       const CvPlan& v = cvs[gp.cv];
       P->cv_max_cells = std::max<int64_t>(P->cv_max_cells, (int64_t)P->groups[RR.groups[v.grp]].K * v.dom);
@@ -1566,6 +1833,9 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       t.mu_word = gp.mu_word;
       t.scale = (float)gp.scale;
       t.out = P->at<long long>(gp.out_off);
+      t.fix_idx = -1;  // hist x mean: one rounding of the exact product per key (FP64)
+      t.soff = -1;
+      t.cells = gp.cells;
       tasks.push_back(t);
       P->max_group_K = std::max(P->max_group_K, P->groups[RR.groups[gp.grp]].K);
     }
@@ -1584,7 +1854,73 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     }
   };
   group_by_view(tasks, rp.n_rv, [](const RvTask& t) { return t.rv; }, &P->rv_ranges);
+  std::stable_sort(P->cv_tasks.begin(), P->cv_tasks.end(),
+                   [](const CatViewTask& a, const CatViewTask& b) { return a.mode < b.mode; });
   group_by_view(P->cv_tasks, (int)cvs.size(), [](const CatViewTask& t) { return t.view; }, &P->cv_ranges);
+  // work items of the key-level tasks: reverse-view tasks in groups that share
+  // one shared-memory table per block (kRvTabCells int64), over key chunks;
+  // COUNT tables by blocks of rows (kCvTabCells counters); SUM(m) by b tables
+  // over key chunks
+  constexpr int kRvTabCells = 5120, kCvTabCells = 12288;
+  {
+    for (int r = 0; r < rp.n_rv; ++r) {
+      const int t0 = P->rv_ranges.begin[r], t1 = P->rv_ranges.begin[r + 1];
+      const int64_t K = rp.grp[rp.rv[r].grp].K;
+      int g0 = t0, cells = 0;
+      auto close = [&](int g1) {
+        if (g1 <= g0) return;
+        const int64_t ch = 512;  // keys per block; the block's table is added to the outputs once
+        for (int64_t k0 = 0; k0 < K; k0 += ch) P->rv_items.push_back(RvItem{r, g0, g1, cells, k0, std::min(K, k0 + ch)});
+        P->rv_item_cells = std::max(P->rv_item_cells, cells);
+      };
+      for (int t = t0; t < t1; ++t) {
+        if (tasks[t].cells > kRvTabCells) {  // wide: straight to its output (k_rv_tasks)
+          close(t);
+          g0 = t + 1;
+          cells = 0;
+          P->rv_wide = true;
+          continue;
+        }
+        if (cells + tasks[t].cells > kRvTabCells || t - g0 >= 64) {
+          close(t);
+          g0 = t;
+          cells = 0;
+        }
+        tasks[t].soff = cells;
+        cells += (int)tasks[t].cells;
+      }
+      close(t1);
+    }
+    for (size_t t = 0; t < P->cv_tasks.size(); ++t) {
+      const CatViewTask& T = P->cv_tasks[t];
+      if (T.mode != 0) continue;
+      const int db = cvs[T.view].dom;
+      const int rows = std::max(1, std::min(T.dom_a, kCvTabCells / db));
+      const int64_t K = rp.grp[cvs[T.view].grp].K;
+      // about 16 blocks per table: row ranges, then key ranges while there are few rows
+      const int n_rr = (T.dom_a + rows - 1) / rows;
+      const int64_t n_kc = std::max<int64_t>(1, std::min<int64_t>((16 + n_rr - 1) / n_rr, (K + 255) / 256));
+      const int64_t ch = (K + n_kc - 1) / n_kc;
+      for (int a0 = 0; a0 < T.dom_a; a0 += rows)
+        for (int64_t k0 = 0; k0 < K; k0 += ch)
+          P->cv_pair_items.push_back(CvPairItem{(int)t, a0, std::min(rows, T.dom_a - a0), 0, k0, std::min(K, k0 + ch)});
+      P->cv_pair_cells = std::max(P->cv_pair_cells, rows * db);
+    }
+    for (int v = 0; v < (int)cvs.size(); ++v) {
+      int m0 = -1, m1 = -1;
+      for (int t = P->cv_ranges.begin[v]; t < P->cv_ranges.begin[v + 1]; ++t)
+        if (P->cv_tasks[t].mode == 1) {
+          if (m0 < 0) m0 = t;
+          m1 = t + 1;
+        }
+      if (m0 < 0) continue;
+      const int64_t K = rp.grp[cvs[v].grp].K;
+      const int64_t ch = 256;  // keys per block, 32 per warp
+      for (int t = m0; t < m1; ++t)
+        for (int64_t k0 = 0; k0 < K; k0 += ch)
+          P->cv_mean_items.push_back(CvMeanItem{v, t, t + 1, 0, k0, std::min(K, k0 + ch)});
+    }
+  }
   P->rv_tasks = tasks;
   P->direct = direct;
   rp.n_cv = (int)cvs.size();
@@ -1647,11 +1983,36 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     maps.push_back(o);
   }
   P->maps = maps;
+  for (size_t i = 0; i < maps.size(); ++i)
+    for (int64_t c0 = 0; c0 < std::max<int64_t>(1, maps[i].n); c0 += 4096)
+      P->out_items.push_back(OutItem{(int)i, 0, c0, std::min<int64_t>(std::max<int64_t>(1, maps[i].n), c0 + 4096)});
+  {  // one device buffer for the work-item lists
+    auto bytes = [](size_t n, size_t sz) { return (n * sz + 255) & ~(size_t)255; };
+    P->aux_rv = 0;
+    P->aux_cvp = P->aux_rv + bytes(P->rv_items.size(), sizeof(RvItem));
+    P->aux_cvm = P->aux_cvp + bytes(P->cv_pair_items.size(), sizeof(CvPairItem));
+    P->aux_out = P->aux_cvm + bytes(P->cv_mean_items.size(), sizeof(CvMeanItem));
+    const size_t total = P->aux_out + bytes(P->out_items.size(), sizeof(OutItem)) + 256;
+    cudaError_t e = cudaMalloc(&P->aux, total);
+    if (e != cudaSuccess) return fail(c, LMF_ERR_OOM, "plan work lists of %zu bytes", total);
+    char* a = static_cast<char*>(P->aux);
+    CUDA_TRY(c, cudaMemcpy(a + P->aux_rv, P->rv_items.data(), sizeof(RvItem) * P->rv_items.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(a + P->aux_cvp, P->cv_pair_items.data(), sizeof(CvPairItem) * P->cv_pair_items.size(),
+                           cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(a + P->aux_cvm, P->cv_mean_items.data(), sizeof(CvMeanItem) * P->cv_mean_items.size(),
+                           cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(a + P->aux_out, P->out_items.data(), sizeof(OutItem) * P->out_items.size(),
+                           cudaMemcpyHostToDevice));
+  }
   P->corr = corr;
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->rvtask_off, tasks.data(), sizeof(RvTask) * tasks.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->cvtask_off, P->cv_tasks.data(), sizeof(CatViewTask) * P->cv_tasks.size(),
                          cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->ggram_off, P->ggram.data(), sizeof(GroupGram) * P->ggram.size(),
+                         cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(P->arena.base + P->cgram_off, P->cgram.data(), sizeof(CrossGram) * P->cgram.size(),
+                         cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(P->arena.base + P->cpair_off, P->cpairs.data(), sizeof(CrossPair) * P->cpairs.size(),
                          cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->direct_off, direct.data(), sizeof(DirectAgg) * direct.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->corr_off, corr.data(), sizeof(CorrTask) * corr.size(), cudaMemcpyHostToDevice));
@@ -1693,7 +2054,23 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       std::fprintf(stderr, "lmf: plan-time compile failed, interpreted root scan kept: %.400s\n", log.c_str());
     }
   }
-  if (!use_tc && !(P->opts.flags & LMF_PLAN_NO_JIT) && Root.nrows > 0 && jit_available()) {
+  if (P->lean) {  // the key-level scan exists only compiled: without it, plan the row-level form
+    std::string log;
+    cudaKernel_t k = nullptr;
+    const int lcps = (int)std::min<int64_t>(3, std::max<int64_t>(1, (int64_t)P->grid / std::max(1, c->num_sms)));
+    if (!jit_kernel(jit_lean_source(rp, direct, lcps), "lmf_root_lean_jit", &k, &log)) {
+      std::fprintf(stderr, "lmf: plan-time compile of the key-level scan failed, row-level form planned: %.400s\n",
+                   log.c_str());
+      lmf_plan_opts o2 = opts;
+      o2.flags |= LMF_PLAN_ROW_GRAM;
+      P.reset();
+      return plan_with_root(c, batch_id, o2, root);
+    }
+    CUDA_TRY(c, cudaFuncSetAttribute(reinterpret_cast<const void*>(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(P->smem)));
+    P->jit_lean = k;
+  }
+  if (!use_tc && !P->lean && !(P->opts.flags & LMF_PLAN_NO_JIT) && Root.nrows > 0 && jit_available()) {
     std::string log;
     cudaKernel_t k = nullptr;
     if (jit_kernel(jit_plain_source(rp, P->mp, direct, jit3 ? 3 : 1), "lmf_root_plain_jit", &k, &log)) {
@@ -1764,6 +2141,8 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
       d.n_cnt = cg.n_cnt;
       d.n_mu = cg.n_mu;
       d.n_cat = cg.n_cat;
+      d.fix = nullptr;
+      d.fix_stride = 0;
       a.grp[q] = d;
     }
     a.status = P->at<uint32_t>(P->status_off);
@@ -1815,6 +2194,10 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
     CUDA_TRY(c, launch_view_finalize(f, s));
     nk += 2;
   }
+  for (const FixMeans& f : P->fixm) {
+    CUDA_TRY(c, launch_fix_means(f, s));
+    ++nk;
+  }
   mark(2);
   // root scan: Gram, counts, reverse views, per-row grouped tables (skipped when
   // the batch has only threshold-filtered aggregates)
@@ -1825,6 +2208,10 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
                                    P->tc->smem, s));
     } else if (P->tc) {
       CUDA_TRY(c, gram_tc_launch(P->tc.get(), P->rootp, s));
+    } else if (P->lean) {
+      void* args[] = {&P->rootp, &P->n_tiles};
+      CUDA_TRY(c, cudaLaunchKernel(reinterpret_cast<const void*>(P->jit_lean), dim3(P->grid), dim3(kLeanT), args,
+                                   P->smem, s));
     } else {
       if (P->jit_plain) {
         void* args[] = {&P->rootp, &P->n_tiles};
@@ -1844,12 +2231,22 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
   if (P->root_scan) {
     if (P->tc) {
       CUDA_TRY(c, gram_tc_combine(P->tc.get(), P->rootp, P->at<double>(P->G_off), P->at<long long>(P->count_off), s));
+    } else if (P->lean) {  // the row Gram covers the root's features z[1, 1 + n_x)
+      CUDA_TRY(c, launch_combine(P->at<double>(P->part_off), P->grid, P->lean_mpx, P->rootp.m,
+                                 P->at<long long>(P->cntp_off), P->at<double>(P->G_off),
+                                 P->at<long long>(P->count_off), s, P->rootp.gram_off, P->rootp.gram_n));
     } else {
       CUDA_TRY(c, launch_combine(P->at<double>(P->part_off), P->grid, P->mp, P->rootp.m,
                                  P->at<long long>(P->cntp_off), P->at<double>(P->G_off),
                                  P->at<long long>(P->count_off), s));
     }
     ++nk;
+    if (!P->cgram.empty()) {
+      CUDA_TRY(c, launch_cross_gram(P->at<CrossGram>(P->cgram_off), (int)P->cgram.size(), P->at<CrossPair>(P->cpair_off),
+                                    Plan::kGgChunks, P->rootp, P->at<double>(P->cgram_part_off),
+                                    P->at<double>(P->G_off), s));
+      nk += 2;
+    }
     if (!P->ggram.empty()) {
       CUDA_TRY(c, launch_group_gram(P->at<GroupGram>(P->ggram_off), (int)P->ggram.size(), Plan::kGgChunks, P->rootp,
                                     P->at<double>(P->ggram_part_off), P->at<double>(P->G_off), s));
@@ -1860,18 +2257,29 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
     CUDA_TRY(c, launch_corr(P->arena.base + P->corr_off, (int)P->corr.size(), P->at<double>(P->G_off), P->rootp.m, s));
     ++nk;
   }
-  if (!P->rv_tasks.empty()) {
+  char* aux = static_cast<char*>(P->aux);
+  if (!P->rv_items.empty()) {
+    CUDA_TRY(c, launch_rv_items(P->at<RvTask>(P->rvtask_off), reinterpret_cast<const RvItem*>(aux + P->aux_rv),
+                                (int)P->rv_items.size(), P->rv_item_cells, P->rootp, s));
+    ++nk;
+  }
+  if (P->rv_wide) {
     CUDA_TRY(c, launch_rv_tasks(P->at<RvTask>(P->rvtask_off), P->rv_ranges, P->rootp, P->max_group_K, s));
     ++nk;
   }
-  if (!P->cv_tasks.empty()) {
-    CUDA_TRY(c, launch_cv_tasks(P->at<CatViewTask>(P->cvtask_off), P->cv_ranges, P->rootp, P->cv_max_cells, s));
+  if (!P->cv_pair_items.empty()) {
+    CUDA_TRY(c, launch_cv_pairs(P->at<CatViewTask>(P->cvtask_off), reinterpret_cast<const CvPairItem*>(aux + P->aux_cvp),
+                                (int)P->cv_pair_items.size(), P->cv_pair_cells, P->rootp, s));
     ++nk;
   }
-  if (!P->maps.empty()) {
-    int64_t max_cells = 1;
-    for (auto& o : P->maps) max_cells = std::max<int64_t>(max_cells, o.n);
-    CUDA_TRY(c, launch_out_map(P->at<OutMap>(P->maps_off), (int)P->maps.size(), max_cells, P->at<double>(P->G_off), P->rootp.m,
+  if (!P->cv_mean_items.empty()) {
+    CUDA_TRY(c, launch_cv_means(P->at<CatViewTask>(P->cvtask_off), reinterpret_cast<const CvMeanItem*>(aux + P->aux_cvm),
+                                (int)P->cv_mean_items.size(), P->rootp, s));
+    ++nk;
+  }
+  if (!P->out_items.empty()) {
+    CUDA_TRY(c, launch_out_map(P->at<OutMap>(P->maps_off), reinterpret_cast<const OutItem*>(aux + P->aux_out),
+                               (int)P->out_items.size(), P->at<double>(P->G_off), P->rootp.m,
                                P->at<long long>(P->count_off), P->at<long long>(P->res_i64_off),
                                P->at<double>(P->res_f64_off), s));
     ++nk;
@@ -1929,7 +2337,8 @@ lmf_status lmf_plan_info(lmf_ctx* c, int batch_id, lmf_plan_stats* info) {
   info->scratch_bytes = (int64_t)P->arena.size;
   info->resident_group = P->rootp.res_cells > 0 ? P->rootp.res_grp : -1;
   info->resident_cells = P->rootp.res_cells;
-  info->jit = (P->jit_plain || P->jit_tc) ? 1 : 0;
+  info->jit = (P->jit_plain || P->jit_tc || P->jit_lean) ? 1 : 0;
+  info->key_level = P->lean ? 1 : 0;
   return LMF_OK;
 }
 

@@ -31,6 +31,7 @@ constexpr int kMaxCat = 32;          // categorical words of one record / root r
 constexpr int kMaxQ = kMaxZ * (kMaxZ + 1) / 2;
 constexpr int kDirInline = 96;        // per-row tables whose descriptors ride in the kernel parameters
 constexpr int kMaxCatViews = 64;      // category views of one root scan
+constexpr int kLeanT = 256;           // key-level root scan: rows per tile, one per thread
 
 // device status bits (OR-ed by kernels, read by lmf_sync)
 constexpr uint32_t kStatusCatRange = 1u;      // category outside [0, domain)
@@ -54,6 +55,19 @@ struct GroupDesc {
   int32_t K;                         // keys 0..K-1 (direct addressing)
   int32_t stride;                    // words per record
   int32_t n_cnt, n_mu, n_cat;
+  // key-level plans: exact fixed-point images of the means the reverse views
+  // sum, [K][fix_stride] int64 (fix_stride even: 16-byte records), written
+  // once per run from the records by k_fix_means; null when none
+  long long* fix;
+  int32_t fix_stride;
+};
+
+// fixed-point images of a probe group's means (key-level plans)
+struct FixMeans {
+  GroupDesc g;
+  int32_t n;                         // images per key
+  int16_t mu_word[kMaxZ];            // record word of each mean
+  float scale[kMaxZ];                // fixed-point scale (power of 2) of each
 };
 
 // Build of one child relation's section of its parent's group record (A2).
@@ -109,13 +123,29 @@ struct ViewFinalizeArgs {
 // SUM(w) and SUM(w * z_s) for the slots s (the view from the root towards a
 // dimension, Sec. 3.2 directional views; used for grouped outputs).
 struct RevView {
-  unsigned long long* hist;          // [K]
-  long long* R;                      // [K][n_slot]
+  unsigned long long* hist;          // count of key k at hist[k * hstride]
+  long long* R;                      // slot s of key k at R[k * rstride + s]
   int32_t grp;                       // root probe group
   int32_t n_slot;
   int16_t slot_z[kMaxZ];             // z index of each slot
   float slot_scale[kMaxZ];           // fixed-point scale per slot (power of 2)
+  // Layout.  Row-level Gram plans: hist [K] and R [K][n_slot] (hstride 1,
+  // rstride n_slot).  Key-level plans (RootParams::lean): one record of
+  // `stride` int64 words per key, word 0 the count and words 1..n_slot the
+  // slots (hist points at word 0, R at word 1, both strides = stride); stride
+  // is even so that a record is a whole number of 16-byte units.
+  int32_t hstride, rstride;
+  int32_t stride;                    // key-level plans: int64 words per key
+  int32_t mode;                      // key-level plans: how the scan updates it (kRv*)
 };
+
+// update modes of a reverse view in the key-level root scan
+constexpr int kRvRuns = 0;           // FP32 sum of every run of equal keys in a warp, one reduction per run
+constexpr int kRvResident = 1;       // the CTA's resident key: per-lane sums in registers until the key changes
+constexpr int kRvBulk = 2;           // every row's record added by one bulk reduction (cp.reduce.async.bulk)
+
+__host__ __device__ inline unsigned long long rv_hist(const RevView& R, int64_t k) { return R.hist[k * R.hstride]; }
+__host__ __device__ inline long long rv_slot(const RevView& R, int64_t k, int s) { return R.R[k * R.rstride + s]; }
 
 // one grouped aggregate accumulated row by row (group-by categories that are
 // not all functions of one foreign key)
@@ -164,6 +194,32 @@ struct CatViewTask {
   int32_t dom_a;
   int32_t a_first;                   // 1: cells a * dom_b + b, 0: b * dom_a + a
   long long* out;
+  // mode 1: SUM of a mean m of the keying group grouped by b alone,
+  // T[vb] += V[k][vb] * m(k) (fixed-point, one rounding per cell): the mean
+  // is constant over key k, so the view's counts weight it exactly
+  int32_t mode;                      // 0: COUNT table (a, b), 1: SUM(m) grouped by b
+  int32_t mu_word;                   // mode 1: m's word in the keying group's record
+  float scale;                       // mode 1: fixed-point scale of the output
+  int32_t fix_idx;                   // mode 1: m's fixed-point image in the keying group's fix records
+                                     // (count * image, exact integers), -1: rounded in FP64 per cell
+};
+
+// Gram entries taken at the key level from a reverse view R keyed by probe
+// group g (the aggregate at the root of g, Sec. 3.3):
+//   G[za][zb] = sum over keys k of R[k][s] / scale_s * m_i(k)
+// where slot s holds sum w z_a over the root rows with key k and m_i is mean i
+// of group g (constant over key k; i = -1: the constant 1, giving SUM(z_a)).
+struct CrossPair {
+  int16_t s, i;                      // reverse-view slot, mean index (-1: 1)
+  int16_t za, zb;                    // Gram entry
+};
+struct CrossGram {
+  int32_t rv;                        // index into RootParams::rv
+  int32_t grp;                       // probe group (the view's key)
+  int32_t mu_word;                   // record word of mean 0
+  int32_t npair;
+  int32_t pair_off;                  // first pair in the pair table
+  int32_t part_off;                  // first partial: [npair][n_parts]
 };
 
 // Gram block of one probe group's view means, taken at the key level: for z
@@ -231,6 +287,14 @@ struct RootParams {
   int32_t unit_w;                    // 1: every w is 0 or 1 (unique child keys)
   int32_t fold;                      // rows per FP32 chain of the plain Gram before it is
                                      // folded into the two-float accumulator (0: once per tile)
+  // key-level plans (lmf_root_lean.cuh): the row-level Gram covers only
+  // z[gram_off, gram_off + gram_n) (the root's own features); every block
+  // with a view mean is taken at the key level from the reverse views
+  int32_t lean;
+  int32_t gram_off, gram_n;
+  int32_t res_rv;                    // reverse view of the resident key (kRvResident), -1: none
+  int16_t fix_of_z[kMaxZ];           // key-level plans: index of z's fixed-point image in its group's
+                                     // fix records, -1: none (the row pass converts the value itself)
 };
 
 // answering a grouped aggregate from a reverse view: loop over the group's keys
@@ -244,6 +308,33 @@ struct RvTask {
   int32_t mu_word;                   // mode 2
   float scale;                       // modes 1, 2
   long long* out;                    // [cells]
+  int32_t fix_idx;                   // mode 2: the mean's fixed-point image in the group's fix records
+                                     // (hist * image, exact integers), -1: rounded in FP64 per key
+  int32_t soff;                      // first cell of its output in the block's shared table (grouped
+                                     // launch), -1: accumulated straight into `out`
+  int64_t cells;
+};
+
+// one block of the grouped launch of the reverse-view tasks: tasks [t0, t1)
+// of view rv (sharing one shared-memory table of `cells` int64) over the
+// keys [k0, k1)
+struct RvItem {
+  int32_t rv, t0, t1, cells;
+  int64_t k0, k1;
+};
+
+// one block of the COUNT tables read off category views: rows [a0, a0 +
+// rows) of task `task`'s table, counted in shared memory over all keys
+struct CvPairItem {
+  int32_t task, a0, rows, pad;
+  int64_t k0, k1;                    // keys of the view this block counts
+};
+
+// one block of the SUM(m) grouped by b tables of a category view: the view's
+// mean tasks [t0, t1) over its keys [k0, k1)
+struct CvMeanItem {
+  int32_t view, t0, t1, pad;
+  int64_t k0, k1;
 };
 
 // within-key scatter of a fanning-out root child e:  G[e's block] += sum_k omega[k] Sc_e[k]
@@ -276,7 +367,17 @@ size_t root_plain_smem(int mp, int n_rowcat, int cache_cells = 0, int res_cells 
 cudaError_t root_plain_prepare(int mp, size_t smem);
 int root_plain_tile_rows();
 cudaError_t launch_combine(const double* part, int grid, int mp, int m, const long long* cnt_part,
-                           double* G, long long* count, cudaStream_t s);
+                           double* G, long long* count, cudaStream_t s, int off = 0, int n = -1);
+cudaError_t launch_cross_gram(const CrossGram* cg, int n_cg, const CrossPair* pairs, int n_parts,
+                              const RootParams& p, double* part, double* G, cudaStream_t s);
+cudaError_t launch_fix_means(const FixMeans& f, cudaStream_t s);
+// grouped launches of the key-level tasks (shared-memory tables per block)
+cudaError_t launch_rv_items(const RvTask* tasks, const RvItem* items, int n_items, int max_cells,
+                            const RootParams& p, cudaStream_t s);
+cudaError_t launch_cv_pairs(const CatViewTask* tasks, const CvPairItem* items, int n_items, int max_cells,
+                            const RootParams& p, cudaStream_t s);
+cudaError_t launch_cv_means(const CatViewTask* tasks, const CvMeanItem* items, int n_items, const RootParams& p,
+                            cudaStream_t s);
 cudaError_t launch_corr(const void* tasks_dev, int n, double* G, int m, cudaStream_t s);
 // tasks sorted by their view; view v owns tasks [begin[v], begin[v + 1])
 struct TaskRanges {
@@ -289,9 +390,13 @@ cudaError_t launch_cv_tasks(const CatViewTask* tasks, const TaskRanges& rg, cons
                             cudaStream_t s);
 cudaError_t launch_group_gram(const GroupGram* gg, int n_gg, int n_parts, const RootParams& p, double* part,
                               double* G, cudaStream_t s);
-cudaError_t launch_out_map(const OutMap* maps, int n_maps, int64_t max_cells, const double* G, int m,
-                           const long long* count, long long* res_i64, double* res_f64,
-                           cudaStream_t s);
+// a range of one map's cells placed by one block
+struct OutItem {
+  int32_t map, pad;
+  int64_t c0, c1;
+};
+cudaError_t launch_out_map(const OutMap* maps, const OutItem* items, int n_items, const double* G, int m,
+                           const long long* count, long long* res_i64, double* res_f64, cudaStream_t s);
 cudaError_t launch_colmaxabs(const Col* cols, int n, int64_t nrows, double* out, cudaStream_t s);
 cudaError_t launch_key_stats(const int32_t* key, int64_t n, unsigned int* hist, int K,
                              int* minmax, cudaStream_t s);

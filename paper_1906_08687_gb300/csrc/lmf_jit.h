@@ -30,6 +30,34 @@ std::string jit_plain_source(const RootParams& rp, int mp, const std::vector<Dir
 std::string jit_tc_source(const RootParams& rp, const std::vector<DirectAgg>& direct);
 std::string jit_source(const RootParams& rp, int mp, const std::vector<DirectAgg>& direct, int min_ctas, bool tc);
 
+// Shared-memory layout of the key-level root scan (lmf_root_lean.cuh) for a
+// plan: the generated row pass carries it as constants, the planner sizes the
+// launch with it.  Per CTA, 256 rows: the fixed-point tile [256][zi_ld] int64
+// (column 0 the row's count, then every value a reverse view sums, exact
+// integers at the value's fixed-point scale), the root features of the row
+// Gram [256][mpx] floats, the z rows of per-row tables that sum a feature
+// [256][zf_ld] floats, staging for bulk reductions [256][stage_w] int64, the
+// row categories of per-row tables [256][cat_w] int32, then the hot-cell and
+// resident-key counters.
+struct LeanShape {
+  int mpx = 4;                  // width of the row-level Gram block (multiple of 4)
+  int ncol = 1;                 // columns of the fixed-point tile
+  int zi_ld = 2;                // int64 words per fixed-point row (even: 16-byte rows)
+  int col_of_z[kMaxZ];          // column of a z index in the fixed-point tile, -1: none
+  float col_scale[kMaxZ];       // fixed-point scale of each column (1 for the count)
+  int zf_ld = 0;                // floats per z row of per-row tables (0: none staged)
+  int stage_w = 0;              // int64 words staged per row for bulk reductions (even)
+  int stage_at[kMaxGroups];     // per reverse view: -1 not bulk, -2 bulk straight from the
+                                // fixed-point row (its slots are columns 1..n), else first staged word
+  int cat_w = 0;                // row categories staged per row
+  int racc = 1;                 // 32-word chunks of the resident view's record
+  uint32_t xg_off = 0, zf_off = 0, stage_off = 0, cat_off = 0, cache_off = 0;
+  size_t smem = 0;              // dynamic shared memory of one CTA, counters included
+};
+LeanShape lean_shape(const RootParams& rp, bool direct_z);
+// CUDA source of the key-level root scan of a plan (kernel lmf_root_lean_jit)
+std::string jit_lean_source(const RootParams& rp, const std::vector<DirectAgg>& direct, int min_ctas);
+
 // compiles src for sm_103a, or finds it in the process-wide cache of compiled
 // sources; on failure returns false with NVRTC's log in *log
 bool jit_kernel(const std::string& src, const char* name, cudaKernel_t* k, std::string* log);

@@ -307,28 +307,37 @@ cudaError_t launch_root_plain(const RootParams& p, int mp, int grid, int64_t n_t
 
 // ---------------------------------------------------------------------------
 // A9: ordered FP64 combine of the per-CTA partials (deterministic)
+// the partials cover z[off, off + n): entry (i, j) of a CTA's block lands at
+// G[off + i][off + j]
+// one warp per entry (i <= j), lanes striding over the CTAs, a fixed shuffle
+// tree: the same order on every run
 __global__ void k_combine(const double* part, int grid, int mp, int m, const long long* cnt_part,
-                          double* G, long long* count) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < m * m) {
-    const int i = e / m, j = e % m;
+                          double* G, long long* count, int off, int n) {
+  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (e < n * n) {
+    const int i = e / n, j = e % n;
     if (i <= j) {
       double s = 0.0;
-      for (int c = 0; c < grid; ++c) s += part[(int64_t)c * mp * mp + i * mp + j];
-      G[i * m + j] = s;
-      G[j * m + i] = s;
+      for (int c = lane; c < grid; c += 32) s += part[(int64_t)c * mp * mp + i * mp + j];
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) {
+        G[(off + i) * m + off + j] = s;
+        G[(off + j) * m + off + i] = s;
+      }
     }
-  }
-  if (e == 0) {
+  } else if (e == n * n) {
     long long s = 0;
-    for (int c = 0; c < grid; ++c) s += cnt_part[c];
-    *count = s;
+    for (int c = lane; c < grid; c += 32) s += cnt_part[c];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) *count = s;
   }
 }
 
 cudaError_t launch_combine(const double* part, int grid, int mp, int m, const long long* cnt_part,
-                           double* G, long long* count, cudaStream_t s) {
-  k_combine<<<(m * m + 127) / 128, 128, 0, s>>>(part, grid, mp, m, cnt_part, G, count);
+                           double* G, long long* count, cudaStream_t s, int off, int n) {
+  if (n < 0) n = m;
+  const int warps = n * n + 1;  // the last one sums the counts
+  k_combine<<<(warps + 3) / 4, 128, 0, s>>>(part, grid, mp, m, cnt_part, G, count, off, n);
   return cudaGetLastError();
 }
 
@@ -358,6 +367,35 @@ cudaError_t launch_corr(const void* tasks_dev, int n, double* G, int m, cudaStre
 
 // grouped aggregates answered from a reverse view: one pass over the group's
 // keys, every task of the view served from the key's record and slots
+// round(c * m * scale) for a count c < 2^40, an FP32 value m and a power-of-two
+// scale, exactly, in integer arithmetic: m = M 2^(e - 150) with the 24-bit
+// integer M, so c m scale = (c M) 2^sh, c M exact in 64 bits, then one
+// rounding (half away from zero) by the shift.  The plan's scale keeps the
+// result below 2^62.
+__device__ __forceinline__ long long cnt_times(unsigned long long c, float m, float scale) {
+  const uint32_t b = __float_as_uint(m);
+  const int e = static_cast<int>((b >> 23) & 0xffu);
+  if (e == 0 || c == 0) return 0;  // zero, or a subnormal far below the fixed-point grid
+  const unsigned long long p = c * static_cast<unsigned long long>((b & 0x7fffffu) | 0x800000u);
+  const int sh = e - 150 + (static_cast<int>((__float_as_uint(scale) >> 23) & 0xffu) - 127);
+  unsigned long long v;
+  if (sh >= 0) v = p << (sh < 63 ? sh : 63);
+  else if (sh > -64) v = (p >> -sh) + ((p >> (-sh - 1)) & 1ull);
+  else v = 0;
+  return (b >> 31) ? -static_cast<long long>(v) : static_cast<long long>(v);
+}
+
+// value of reverse-view task t at key k with count h
+__device__ __forceinline__ long long rv_task_value(const RvTask& t, const RevView& R, const GroupDesc& G, int64_t k,
+                                                   unsigned long long h, const uint32_t* rec) {
+  if (t.mode == 0) return static_cast<long long>(h);
+  if (t.mode == 1) return rv_slot(R, k, t.slot);
+  // hist * mean * scale, one exact rounding per key
+  return cnt_times(h, __uint_as_float(rec[t.mu_word]), t.scale);
+}
+
+// the reverse-view tasks too wide for a block's shared table: straight into
+// their global outputs
 __global__ void k_rv_tasks(const RvTask* tasks, const TaskRanges rg, const __grid_constant__ RootParams p) {
   const int r = blockIdx.y;
   const int t0 = rg.begin[r], t1 = rg.begin[r + 1];
@@ -365,22 +403,169 @@ __global__ void k_rv_tasks(const RvTask* tasks, const TaskRanges rg, const __gri
   const RevView& R = p.rv[r];
   const GroupDesc& G = p.grp[R.grp];
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G.K; k += gridDim.x * blockDim.x) {
-    const unsigned long long h = R.hist[k];
+    const unsigned long long h = rv_hist(R, k);
     if (h == 0) continue;
     const uint32_t* rec = G.rec + (int64_t)k * G.stride;
     for (int ti = t0; ti < t1; ++ti) {
       const RvTask& t = tasks[ti];
+      if (t.soff >= 0) continue;  // served by the grouped launch
       int64_t cell = 0;
       for (int q = 0; q < t.n_gb; ++q) cell = cell * t.dom[q] + static_cast<int32_t>(rec[t.cat_word[q]]);
-      long long v;
-      if (t.mode == 0) v = static_cast<long long>(h);
-      else if (t.mode == 1) v = R.R[(int64_t)k * R.n_slot + t.slot];
-      else  // hist * mean * scale is exact in FP64 (49 bits): one rounding per key
-        v = __double2ll_rn(static_cast<double>(h) * static_cast<double>(__uint_as_float(rec[t.mu_word])) *
-                           static_cast<double>(t.scale));
-      add_ll(t.out + cell, v);
+      add_ll(t.out + cell, rv_task_value(t, R, G, k, h, rec));
     }
   }
+}
+
+// Grouped reverse-view tasks: a block sums tasks [t0, t1) of one view over
+// its key range in a shared-memory table (Zipf-hot categories then collide in
+// shared memory instead of serialising global atomics) and adds the table to
+// the outputs once.  Integer sums: the result does not depend on the order.
+constexpr int kRvItemTasks = 64;  // tasks of one grouped launch block, staged in shared memory
+__global__ void __launch_bounds__(256) k_rv_items(const RvTask* tasks, const RvItem* items,
+                                                  const __grid_constant__ RootParams p) {
+  extern __shared__ unsigned long long tab[];
+  __shared__ RvTask ts[kRvItemTasks];
+  const RvItem it = items[blockIdx.x];
+  const RevView& R = p.rv[it.rv];
+  const GroupDesc& G = p.grp[R.grp];
+  for (int i = threadIdx.x; i < it.cells; i += blockDim.x) tab[i] = 0ull;
+  for (int i = threadIdx.x; i < it.t1 - it.t0; i += blockDim.x) ts[i] = tasks[it.t0 + i];
+  __syncthreads();
+  for (int64_t k = it.k0 + threadIdx.x; k < it.k1; k += blockDim.x) {
+    const unsigned long long h = rv_hist(R, k);
+    if (h == 0) continue;
+    const uint32_t* rec = G.rec + k * G.stride;
+    for (int ti = 0; ti < it.t1 - it.t0; ++ti) {
+      const RvTask& t = ts[ti];
+      int64_t cell = 0;
+      for (int q = 0; q < t.n_gb; ++q) cell = cell * t.dom[q] + static_cast<int32_t>(rec[t.cat_word[q]]);
+      const long long v = rv_task_value(t, R, G, k, h, rec);
+      if (v != 0) atomicAdd(&tab[t.soff + cell], static_cast<unsigned long long>(v));
+    }
+  }
+  __syncthreads();
+  for (int ti = 0; ti < it.t1 - it.t0; ++ti) {
+    const RvTask& t = ts[ti];
+    for (int64_t c = threadIdx.x; c < t.cells; c += blockDim.x) {
+      const unsigned long long v = tab[t.soff + c];
+      if (v) atomicAdd(reinterpret_cast<unsigned long long*>(t.out + c), v);
+    }
+  }
+}
+
+cudaError_t launch_rv_items(const RvTask* tasks, const RvItem* items, int n_items, int max_cells,
+                            const RootParams& p, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  const int sm = max_cells * 8;
+  cudaError_t e = cudaFuncSetAttribute(k_rv_items, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e != cudaSuccess) return e;
+  k_rv_items<<<n_items, 256, sm, s>>>(tasks, items, p);
+  return cudaGetLastError();
+}
+
+// COUNT tables (a, b) read off category views, one block per range of rows a
+// of one table and range of the view's keys: the block lists the keys whose
+// a falls in its rows, adds their view rows V[k][.] into shared counters (a
+// warp per key, lanes over b) and adds its counters to the table
+__global__ void __launch_bounds__(256) k_cv_pairs(const CatViewTask* tasks, const CvPairItem* items,
+                                                  const __grid_constant__ RootParams p) {
+  extern __shared__ uint32_t cnt[];  // [rows][dom_b]
+  __shared__ int32_t keys[256];
+  __shared__ int32_t nk;
+  const CvPairItem it = items[blockIdx.x];
+  const CatViewTask T = tasks[it.task];
+  const CatView& C = p.cv[T.view];
+  const GroupDesc& G = p.grp[C.grp];
+  const int db = C.dom;
+  const int n = it.rows * db;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) cnt[i] = 0u;
+  for (int64_t k0 = it.k0; k0 < it.k1; k0 += blockDim.x) {
+    if (threadIdx.x == 0) nk = 0;
+    __syncthreads();
+    const int64_t k = k0 + threadIdx.x;
+    if (k < it.k1) {
+      const int a = static_cast<int32_t>(G.rec[k * G.stride + T.a_word]) - it.a0;
+      if (a >= 0 && a < it.rows) keys[atomicAdd(&nk, 1)] = static_cast<int32_t>(k);
+    }
+    __syncthreads();
+    const int m = nk;
+    for (int j = warp; j < m; j += nwarp) {  // one listed key per warp, lanes over b
+      const int64_t kk = keys[j];
+      const int a = static_cast<int32_t>(G.rec[kk * G.stride + T.a_word]) - it.a0;
+      const uint32_t* v = C.V + kk * db;
+      for (int b = lane; b < db; b += 32) {
+        const uint32_t x = v[b];
+        if (x) atomicAdd(&cnt[a * db + b], x);
+      }
+    }
+    __syncthreads();  // the list is read by every warp before it is refilled
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint32_t x = cnt[i];
+    if (!x) continue;
+    const int a = it.a0 + i / db, b = i % db;
+    const int64_t cell = T.a_first ? static_cast<int64_t>(a) * db + b : static_cast<int64_t>(b) * T.dom_a + a;
+    atomicAdd(reinterpret_cast<unsigned long long*>(T.out + cell), static_cast<unsigned long long>(x));
+  }
+}
+
+cudaError_t launch_cv_pairs(const CatViewTask* tasks, const CvPairItem* items, int n_items, int max_cells,
+                            const RootParams& p, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  const int sm = max_cells * 4;
+  cudaError_t e = cudaFuncSetAttribute(k_cv_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e != cudaSuccess) return e;
+  k_cv_pairs<<<n_items, 256, sm, s>>>(tasks, items, p);
+  return cudaGetLastError();
+}
+
+// SUM of a keying-group mean grouped by b, read off a category view: one block
+// per (task, range of keys); a warp takes a key at a time, its lanes the
+// cells b of the key's view row (coalesced), each lane keeping its cells'
+// sums in registers; the warps' sums meet in shared memory and one value per
+// (block, b) goes to the output.  Every cell's count x mean is one exact
+// integer rounding (cnt_times).
+constexpr int kCvMeanRegs = 16;  // cells b per lane held in registers: db <= 512 per pass
+__global__ void __launch_bounds__(256) k_cv_means(const CatViewTask* tasks, const CvMeanItem* items,
+                                                  const __grid_constant__ RootParams p) {
+  __shared__ long long part[8][32 * kCvMeanRegs];
+  const CvMeanItem it = items[blockIdx.x];
+  const CatViewTask T = tasks[it.t0];
+  const CatView& C = p.cv[it.view];
+  const GroupDesc& G = p.grp[C.grp];
+  const int db = C.dom;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int b0 = 0; b0 < db; b0 += 32 * kCvMeanRegs) {
+    long long acc[kCvMeanRegs];
+#pragma unroll
+    for (int r = 0; r < kCvMeanRegs; ++r) acc[r] = 0;
+    for (int64_t k = it.k0 + warp; k < it.k1; k += 8) {
+      const float m = __uint_as_float(G.rec[k * G.stride + T.mu_word]);
+      const uint32_t* v = C.V + k * db + b0;
+#pragma unroll
+      for (int r = 0; r < kCvMeanRegs; ++r) {
+        const int b = lane + 32 * r;
+        if (b0 + b < db) acc[r] += cnt_times(v[b], m, T.scale);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kCvMeanRegs; ++r) part[warp][lane + 32 * r] = acc[r];
+    __syncthreads();
+    for (int b = threadIdx.x; b < 32 * kCvMeanRegs && b0 + b < db; b += blockDim.x) {
+      long long s = 0;
+      for (int w = 0; w < 8; ++w) s += part[w][b];
+      if (s) atomicAdd(reinterpret_cast<unsigned long long*>(T.out + b0 + b), static_cast<unsigned long long>(s));
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_cv_means(const CatViewTask* tasks, const CvMeanItem* items, int n_items, const RootParams& p,
+                            cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  k_cv_means<<<n_items, 256, 0, s>>>(tasks, items, p);
+  return cudaGetLastError();
 }
 
 // COUNT tables read off category views: one pass over each view's cells,
@@ -400,6 +585,10 @@ __global__ void k_cv_tasks(const CatViewTask* tasks, const TaskRanges rg, const 
     const uint32_t* rec = G.rec + k * G.stride;
     for (int t = t0; t < t1; ++t) {
       const CatViewTask& T = tasks[t];
+      if (T.mode == 1) {  // count x mean: one exact rounding per cell
+        add_ll(T.out + b, cnt_times(static_cast<unsigned long long>(val), __uint_as_float(rec[T.mu_word]), T.scale));
+        continue;
+      }
       const int a = static_cast<int32_t>(rec[T.a_word]);
       add_ll(T.out + (T.a_first ? static_cast<int64_t>(a) * C.dom + b : static_cast<int64_t>(b) * T.dom_a + a),
              val);
@@ -428,43 +617,79 @@ __device__ __forceinline__ void gg_pair(int p, int n, int& i, int& j) {
   j = (i < 0 ? 0 : i) + p;
 }
 
-// partial sums over one range of the keys per warp; lane l takes the pairs
-// l, l + 32, .. (up to kGgLane of them per sweep over the keys)
+// Key-level sums: one warp per range of the keys.  For every key the warp
+// stages the key's values in shared memory -- an integer (a count, or a
+// reverse view's fixed-point slot) as two floats hi + lo (equal to it within
+// 2^-48), the group's means as the FP32 values they are -- then lane l forms
+// the products of its pairs l, l + 32, .. in compensated FP32 (the rounding
+// error of each product recovered with an FMA) and adds them to a two-float
+// (TwoSum) accumulator: each key's term carries a relative error near 2^-48,
+// so a few heavy keys (Zipf-hot) cannot dominate the error.  Partials go out
+// in FP64 and are summed in a fixed order.
 constexpr int kGgLane = 4;
+constexpr int kKeyVals = 3 * kMaxZ + 4;  // staged values of one key
+
+__device__ __forceinline__ void ks_two_sum(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
+// an int64 as hi + lo (two floats), times a power-of-two scale
+__device__ __forceinline__ void ks_split(long long v, float scale, float& hi, float& lo) {
+  const float h = __ll2float_rn(v);
+  hi = h * scale;
+  lo = __ll2float_rn(v - __float2ll_rn(h)) * scale;
+}
+// acc += (ah + al) * b with the product's rounding error kept (b exact)
+__device__ __forceinline__ void ks_mad(float& acc_hi, float& acc_lo, float ah, float al, float b) {
+  const float p = ah * b;
+  const float e = fmaf(ah, b, -p);
+  ks_two_sum(acc_hi, acc_lo, p);
+  acc_lo += fmaf(al, b, e);
+}
+
 __global__ void k_group_gram_part(const GroupGram* gg, int n_parts, const __grid_constant__ RootParams p,
                                   double* part) {
+  __shared__ float vals[8][kKeyVals];  // per warp: [count hi, count lo, means]
   const GroupGram g = gg[blockIdx.y];
   const GroupDesc& G = p.grp[g.grp];
-  const unsigned long long* hist = p.rv[g.rv].hist;
-  const int lane = threadIdx.x & 31;
-  const int64_t part_id = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const RevView& RV = p.rv[g.rv];
+  const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+  float* sv = vals[wv];
+  const int64_t part_id = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + wv;
   const int64_t k0 = part_id * G.K / n_parts, k1 = (part_id + 1) * G.K / n_parts;
   for (int q0 = 0; q0 < g.npair; q0 += 32 * kGgLane) {
     int pi[kGgLane], pj[kGgLane];
-    double s[kGgLane];
+    float hi[kGgLane], lo[kGgLane];
 #pragma unroll
     for (int u = 0; u < kGgLane; ++u) {
       const int q = q0 + lane + 32 * u;
       pi[u] = -1;
       pj[u] = 0;
       if (q < g.npair) gg_pair(q, g.n, pi[u], pj[u]);
-      s[u] = 0.0;
+      hi[u] = lo[u] = 0.f;
     }
-#pragma unroll 4
     for (int64_t k = k0; k < k1; ++k) {
-      const double h = static_cast<double>(hist[k]);
       const uint32_t* rec = G.rec + k * G.stride + g.mu_word;
+      if (lane == 0) ks_split(static_cast<long long>(rv_hist(RV, k)), 1.f, sv[0], sv[1]);
+      for (int i = lane; i < g.n; i += 32) sv[2 + i] = __uint_as_float(rec[i]);
+      __syncwarp();
 #pragma unroll
       for (int u = 0; u < kGgLane; ++u) {
-        const double mj = static_cast<double>(__uint_as_float(rec[pj[u]]));
-        const double mi = pi[u] < 0 ? 1.0 : static_cast<double>(__uint_as_float(rec[pi[u]]));
-        s[u] += h * (mi * mj);
+        // m_i m_j exactly as qh + ql, then (count) x (qh + ql)
+        const float mj = sv[2 + pj[u]];
+        const float mi = pi[u] < 0 ? 1.f : sv[2 + pi[u]];
+        const float qh = mi * mj, ql = fmaf(mi, mj, -qh);
+        ks_mad(hi[u], lo[u], sv[0], sv[1], qh);
+        lo[u] = fmaf(sv[0], ql, lo[u]);
       }
+      __syncwarp();
     }
 #pragma unroll
     for (int u = 0; u < kGgLane; ++u) {
       const int q = q0 + lane + 32 * u;
-      if (q < g.npair) part[static_cast<int64_t>(g.part_off + q) * n_parts + part_id] = s[u];
+      if (q < g.npair) part[static_cast<int64_t>(g.part_off + q) * n_parts + part_id] = (double)hi[u] + (double)lo[u];
     }
   }
 }
@@ -497,6 +722,98 @@ cudaError_t launch_group_gram(const GroupGram* gg, int n_gg, int n_parts, const 
   return cudaGetLastError();
 }
 
+// Gram entries at the key level from the reverse views (CrossGram), in the
+// form of k_group_gram_part: per key the warp stages the view's slots (exact
+// fixed-point integers, scaled back to FP32) and the group's means, lane l
+// forms the products of its pairs and adds them to two-float accumulators
+constexpr int kCgLane = 4;
+__global__ void k_cross_gram_part(const CrossGram* cg, const CrossPair* pairs, int n_parts,
+                                  const __grid_constant__ RootParams p, double* part) {
+  __shared__ float vals[8][kKeyVals];  // per warp: [slots hi][slots lo][means]
+  const CrossGram g = cg[blockIdx.y];
+  const GroupDesc& G = p.grp[g.grp];
+  const RevView& R = p.rv[g.rv];
+  const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+  float* sv = vals[wv];
+  const int ns = R.n_slot;
+  const int64_t part_id = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + wv;
+  const int64_t k0 = part_id * G.K / n_parts, k1 = (part_id + 1) * G.K / n_parts;
+  for (int q0 = 0; q0 < g.npair; q0 += 32 * kCgLane) {
+    int ps[kCgLane], pm[kCgLane];
+    float hi[kCgLane], lo[kCgLane];
+#pragma unroll
+    for (int u = 0; u < kCgLane; ++u) {
+      const int q = q0 + lane + 32 * u;
+      const CrossPair cp = q < g.npair ? pairs[g.pair_off + q] : CrossPair{0, -1, 0, 0};
+      ps[u] = cp.s;
+      pm[u] = cp.i;
+      hi[u] = lo[u] = 0.f;
+    }
+    for (int64_t k = k0; k < k1; ++k) {
+      const uint32_t* rec = G.rec + k * G.stride + g.mu_word;
+      for (int i = lane; i < ns; i += 32) ks_split(rv_slot(R, k, i), 1.0f / R.slot_scale[i], sv[i], sv[ns + i]);
+      for (int i = lane; i < G.n_mu; i += 32) sv[2 * ns + i] = __uint_as_float(rec[i]);
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < kCgLane; ++u) {
+        const float m = pm[u] < 0 ? 1.f : sv[2 * ns + pm[u]];
+        ks_mad(hi[u], lo[u], sv[ps[u]], sv[ns + ps[u]], m);
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int u = 0; u < kCgLane; ++u) {
+      const int q = q0 + lane + 32 * u;
+      if (q < g.npair) part[static_cast<int64_t>(g.part_off + q) * n_parts + part_id] = (double)hi[u] + (double)lo[u];
+    }
+  }
+}
+
+// the partials of each pair summed in a fixed order (one warp per pair)
+__global__ void k_cross_gram_fin(const CrossGram* cg, const CrossPair* pairs, int n_parts, const double* part,
+                                 double* G, int m) {
+  const CrossGram g = cg[blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  for (int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < g.npair; q += gridDim.x * (blockDim.x >> 5)) {
+    const double* src = part + static_cast<int64_t>(g.part_off + q) * n_parts;
+    double s = 0.0;
+    for (int c = lane; c < n_parts; c += 32) s += src[c];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      const CrossPair cp = pairs[g.pair_off + q];
+      G[cp.za * m + cp.zb] = s;
+      G[cp.zb * m + cp.za] = s;
+    }
+  }
+}
+
+cudaError_t launch_cross_gram(const CrossGram* cg, int n_cg, const CrossPair* pairs, int n_parts,
+                              const RootParams& p, double* part, double* G, cudaStream_t s) {
+  if (n_cg <= 0) return cudaSuccess;
+  k_cross_gram_part<<<dim3(n_parts / 8, n_cg), 256, 0, s>>>(cg, pairs, n_parts, p, part);
+  k_cross_gram_fin<<<dim3(16, n_cg), 256, 0, s>>>(cg, pairs, n_parts, part, G, p.m);
+  return cudaGetLastError();
+}
+
+// key-level plans: the exact fixed-point image of every mean a reverse view
+// sums, once per key (the root scan then sums integers without converting
+// the same value on every row)
+__global__ void k_fix_means(const __grid_constant__ FixMeans f) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= static_cast<int64_t>(f.g.K) * f.n) return;
+  const int64_t k = i / f.n;
+  const int j = static_cast<int>(i - k * f.n);
+  const float m = __uint_as_float(f.g.rec[k * f.g.stride + f.mu_word[j]]);
+  f.g.fix[k * f.g.fix_stride + j] = __float2ll_rn(m * f.scale[j]);
+}
+
+cudaError_t launch_fix_means(const FixMeans& f, cudaStream_t s) {
+  const int64_t n = static_cast<int64_t>(f.g.K) * f.n;
+  if (n <= 0) return cudaSuccess;
+  k_fix_means<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rv_tasks(const RvTask* tasks, const TaskRanges& rg, const RootParams& p, int max_K,
                             cudaStream_t s) {
   if (rg.n_views <= 0) return cudaSuccess;
@@ -505,12 +822,17 @@ cudaError_t launch_rv_tasks(const RvTask* tasks, const TaskRanges& rg, const Roo
   return cudaGetLastError();
 }
 
-// final placement of every aggregate: blockIdx.y = map, blocks of x stride the cells
-__global__ void k_out_map(const OutMap* maps, const double* G, int m, const long long* count,
+// final placement of every aggregate: one block per item (a map and a range
+// of its cells)
+__global__ void k_out_map(const OutMap* maps, const OutItem* items, const double* G, int m, const long long* count,
                           long long* res_i64, double* res_f64) {
-  const OutMap o = maps[blockIdx.y];
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const OutItem it = items[blockIdx.x];
+  OutMap o = maps[it.map];
+  o.dst += it.c0;
+  o.n = it.c1 - it.c0;
+  if (o.kind >= 2) o.src += it.c0;
+  const int64_t t0 = threadIdx.x;
+  const int64_t step = blockDim.x;
   switch (o.kind) {
     case 0:
       if (t0 == 0) res_i64[o.dst] = *count;
@@ -528,12 +850,10 @@ __global__ void k_out_map(const OutMap* maps, const double* G, int m, const long
   }
 }
 
-cudaError_t launch_out_map(const OutMap* maps, int n_maps, int64_t max_cells, const double* G, int m,
+cudaError_t launch_out_map(const OutMap* maps, const OutItem* items, int n_items, const double* G, int m,
                            const long long* count, long long* res_i64, double* res_f64, cudaStream_t s) {
-  if (n_maps <= 0) return cudaSuccess;
-  int64_t bx = (max_cells + 255) / 256;
-  dim3 grid((unsigned)(bx < 64 ? (bx > 0 ? bx : 1) : 64), (unsigned)n_maps);
-  k_out_map<<<grid, 256, 0, s>>>(maps, G, m, count, res_i64, res_f64);
+  if (n_items <= 0) return cudaSuccess;
+  k_out_map<<<n_items, 256, 0, s>>>(maps, items, G, m, count, res_i64, res_f64);
   return cudaGetLastError();
 }
 

@@ -127,20 +127,27 @@ __global__ void k_affine(const float* y, int B, float scale, float shift, float*
 
 inline int nb(int64_t n) { return (int)((n + 255) / 256); }
 
+// activation buffers for batches of up to B rows; on failure every buffer is
+// freed and nulled and the capacity is 0, so a later call starts clean
 lmf_status ensure_cap(lmf_mlp* m, int B) {
   if (B <= m->cap) return LMF_OK;
-  cudaFree(m->xn);
-  cudaFree(m->h1);
-  cudaFree(m->h2);
-  cudaFree(m->yh);
-  cudaFree(m->dy);
-  cudaFree(m->dh1);
-  cudaFree(m->dh2);
+  float** bufs[7] = {&m->xn, &m->h1, &m->h2, &m->yh, &m->dy, &m->dh1, &m->dh2};
   const size_t b = (size_t)B;
-  if (cudaMalloc(&m->xn, b * m->in * 4) || cudaMalloc(&m->h1, b * m->hid * 4) || cudaMalloc(&m->h2, b * m->hid * 4) ||
-      cudaMalloc(&m->yh, b * 4) || cudaMalloc(&m->dy, b * 4) || cudaMalloc(&m->dh1, b * m->hid * 4) ||
-      cudaMalloc(&m->dh2, b * m->hid * 4))
-    return LMF_ERR_OOM;
+  const size_t bytes[7] = {b * m->in * 4, b * m->hid * 4, b * m->hid * 4, b * 4, b * 4, b * m->hid * 4,
+                           b * m->hid * 4};
+  for (float** p : bufs) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  m->cap = 0;
+  for (int i = 0; i < 7; ++i)
+    if (cudaMalloc(bufs[i], bytes[i]) != cudaSuccess) {
+      for (float** p : bufs) {
+        cudaFree(*p);
+        *p = nullptr;
+      }
+      return LMF_ERR_OOM;
+    }
   m->cap = B;
   return LMF_OK;
 }

@@ -15,13 +15,18 @@
 // keeps x <= t exact for FP32 data.
 //
 // Kernels:
-//   k_tree_rows  one pass over the root rows: z from the views, the row's node
-//                in every group of mutually exclusive nodes, its bucket for
-//                every split attribute, its fixed-point moment values.
-//   k_tree_hist  persistent: CTAs own a slice (node range x split range) of the
-//                histogram in shared memory, pull row chunks from a per-slice
-//                work queue, accumulate exact 64-bit sums as two 32-bit atomics
-//                with carry, and flush once to global int64.
+//   k_tree_fused persistent: CTAs own a slice (node range x split range) of the
+//                histogram in shared memory and pull row chunks from a
+//                per-slice work queue; for every row they build z from the
+//                views, find the row's node in every group of mutually
+//                exclusive nodes by descending a decision tree over the nodes'
+//                predicates, and -- only for a node of the slice -- compute its
+//                fixed-point moments and its bucket for every split attribute
+//                of the slice (binary search over the thresholds, held in
+//                shared memory), accumulating exact 64-bit sums as two 32-bit
+//                shared-memory atomics with carry; one flush to global int64.
+//                Nothing per row leaves the CTA: a slice recomputes the row
+//                pass instead of reading it back from memory.
 //   k_tree_out   every aggregate as a prefix / suffix sum over the buckets.
 #include "lmf_tree.h"
 #include "lmf_rowpass.cuh"
@@ -60,13 +65,23 @@ struct TreeDev {
   const float* thr;
   int16_t mom_a[kTreeMaxMom], mom_b[kTreeMaxMom];  // z indices, -1: absent
   double mom_scale[kTreeMaxMom];                   // 0: the count moment (w itself)
-  uint16_t* node;              // [n_groups][N]
-  uint8_t* bucket;             // [n_split][N]
-  long long* momv;             // [n_mom][N]
+  // decision tree over the nodes' predicates, per group: internal entries
+  // send a row left when z[dz] <= dthr; a leaf lists candidate nodes
+  // [dleft, dleft + dright) of dcand, each checked on all of its predicates
+  const int32_t* droot;        // [n_groups]
+  const struct TreeDt* dt;
+  const int32_t* dcand;
   long long* H;                // [n_nodes][n_split][max_bins][n_mom]
   uint32_t* queue;             // [n_slices]
   int64_t N;
   uint32_t* status;
+};
+
+struct TreeDt {
+  int16_t z;
+  int16_t leaf;                // 1: left/right are the candidate range [left, left + right)
+  float thr;
+  int32_t left, right;
 };
 
 struct TreeShape {
@@ -86,10 +101,13 @@ struct TreePlanImpl {
     int node, split, j, op, mom;
   };
   std::vector<OutH> outs;
+  std::vector<int32_t> droot;    // decision tree per group (host copy)
+  std::vector<TreeDt> dt;
+  std::vector<int32_t> dcand;
   int max_bins = 1;
   int mp = 16;
   // device
-  size_t H_off = 0, queue_off = 0, node_off = 0, bucket_off = 0, momv_off = 0;
+  size_t H_off = 0, queue_off = 0;
   size_t tab_off = 0, tab_bytes = 0, outs_off = 0;
   TreeDev dev{};
   const TreeOut* d_outs = nullptr;
@@ -121,6 +139,54 @@ bool disjoint(const std::vector<TreePred>& a, const std::vector<TreePred>& b) {
       if (gt.thr >= le.thr) return true;  // x <= t1 and x > t2 >= t1 cannot both hold
     }
   return false;
+}
+
+// Decision tree over a set of mutually exclusive nodes: an internal entry
+// splits on one predicate (z, thr) of the nodes; a node that requires z <= thr
+// goes only left, one that requires z > thr only right, the others both ways.
+// The predicate that leaves the smaller side largest is taken; a set that no
+// predicate splits is a leaf (its nodes are checked in full).
+int build_dt(const std::vector<std::vector<TreePred>>& nodes, const std::vector<int>& set, int depth,
+             std::vector<TreeDt>* dt, std::vector<int32_t>* cand) {
+  const int at = (int)dt->size();
+  dt->push_back(TreeDt{});
+  auto leaf = [&]() {
+    (*dt)[at] = TreeDt{0, 1, 0.f, (int32_t)cand->size(), (int32_t)set.size()};
+    cand->insert(cand->end(), set.begin(), set.end());
+    return at;
+  };
+  if (set.size() <= 1 || depth >= 24) return leaf();
+  std::map<std::pair<int, float>, std::pair<int, int>> cnt;  // (z, thr) -> (nodes only left, only right)
+  for (int n : set)
+    for (const TreePred& p : nodes[n]) {
+      auto& c = cnt[{p.z, p.thr}];
+      (p.op == 0 ? c.first : c.second)++;
+    }
+  int best_min = 0;
+  std::pair<int, float> best{-1, 0.f};
+  for (auto& kv : cnt) {
+    const int n = (int)set.size();
+    const int l = n - kv.second.second, r = n - kv.second.first;  // sizes of the two sides
+    if (l >= n || r >= n) continue;
+    const int mn = std::min(l, r);
+    if (mn > best_min) {
+      best_min = mn;
+      best = kv.first;
+    }
+  }
+  if (best.first < 0) return leaf();
+  std::vector<int> L, R;
+  for (int n : set) {
+    bool le = false, gt = false;
+    for (const TreePred& p : nodes[n])
+      if (p.z == best.first && p.thr == best.second) (p.op == 0 ? le : gt) = true;
+    if (!gt) L.push_back(n);
+    if (!le) R.push_back(n);
+  }
+  const int l = build_dt(nodes, L, depth + 1, dt, cand);
+  const int r = build_dt(nodes, R, depth + 1, dt, cand);
+  (*dt)[at] = TreeDt{(int16_t)best.first, 0, best.second, l, r};
+  return at;
 }
 
 size_t slice_bytes(const TreePlanImpl& T, int node_w, int split_w) {
@@ -292,6 +358,7 @@ lmf_status tree_plan(const std::vector<TreeAggIn>& in, const std::map<std::strin
     }
     if (!placed) T.groups.push_back({n});
   }
+  for (auto& g : T.groups) T.droot.push_back(build_dt(T.nodes, g, 0, &T.dt, &T.dcand));
   int mz = 0;
   for (auto& kv : zidx) mz = std::max(mz, kv.second + 1);
   T.mp = 16;
@@ -323,18 +390,15 @@ void tree_alloc_zeroed(TreePlan* tp, int64_t /*N*/, const std::function<size_t(s
   T.queue_off = take(static_cast<size_t>(T.max_slices) * 4 + 4);
 }
 
-void tree_alloc(TreePlan* tp, int64_t N, const std::function<size_t(size_t)>& take) {
+void tree_alloc(TreePlan* tp, int64_t /*N*/, const std::function<size_t(size_t)>& take) {
   TreePlanImpl& T = *tp->impl;
-  const size_t n = static_cast<size_t>(N > 0 ? N : 1);
-  T.node_off = take(n * 2 * T.dev.n_groups);
-  T.bucket_off = take(n * T.dev.n_split);
-  T.momv_off = take(n * 8 * T.dev.n_mom);
   size_t npred = 0, nthr = 0;
   for (auto& v : T.nodes) npred += v.size();
   for (auto& v : T.thr) nthr += v.size();
   T.tab_bytes = (T.nodes.size() + 1) * 4 + (npred + 1) * sizeof(TreePred) + (T.groups.size() + 1) * 4 +
                 (T.nodes.size() + 1) * 4 + (T.split_z.size() + 1) * 2 + (T.split_z.size() + 1) * 4 +
-                (nthr + 1) * 4 + 64;
+                (nthr + 1) * 4 + (T.droot.size() + 1) * 4 + (T.dt.size() + 1) * sizeof(TreeDt) +
+                (T.dcand.size() + 1) * 4 + 128;
   T.tab_off = take(T.tab_bytes);
   T.outs_off = take(sizeof(TreeOut) * (T.outs.size() + 1));
 }
@@ -348,9 +412,6 @@ lmf_status tree_finish(TreePlan* tp, char* base, long long* res_i64, double* res
   TreeDev& D = T.dev;
   D.N = N;
   D.status = status;
-  D.node = reinterpret_cast<uint16_t*>(base + T.node_off);
-  D.bucket = reinterpret_cast<uint8_t*>(base + T.bucket_off);
-  D.momv = reinterpret_cast<long long*>(base + T.momv_off);
   D.H = reinterpret_cast<long long*>(base + T.H_off);
   D.queue = reinterpret_cast<uint32_t*>(base + T.queue_off);
   // moments: fixed-point scale from the value bounds, 0 for the count
@@ -404,6 +465,9 @@ lmf_status tree_finish(TreePlan* tp, char* base, long long* res_i64, double* res
   const size_t o_split_z = put(T.split_z.data(), T.split_z.size() * 2, 8);
   const size_t o_thr_off = put(thr_off.data(), thr_off.size() * 4, 8);
   const size_t o_thr = put(thr.data(), thr.size() * 4, 8);
+  const size_t o_droot = put(T.droot.data(), T.droot.size() * 4, 8);
+  const size_t o_dt = put(T.dt.data(), T.dt.size() * sizeof(TreeDt), 8);
+  const size_t o_dcand = put(T.dcand.data(), T.dcand.size() * 4, 8);
   if (off > T.tab_bytes) return LMF_ERR_ARG;
   char* dtab = base + T.tab_off;
   D.pred_off = reinterpret_cast<const int32_t*>(dtab + o_pred_off);
@@ -413,6 +477,9 @@ lmf_status tree_finish(TreePlan* tp, char* base, long long* res_i64, double* res
   D.split_z = reinterpret_cast<const int16_t*>(dtab + o_split_z);
   D.thr_off = reinterpret_cast<const int32_t*>(dtab + o_thr_off);
   D.thr = reinterpret_cast<const float*>(dtab + o_thr);
+  D.droot = reinterpret_cast<const int32_t*>(dtab + o_droot);
+  D.dt = reinterpret_cast<const TreeDt*>(dtab + o_dt);
+  D.dcand = reinterpret_cast<const int32_t*>(dtab + o_dcand);
   if (cudaMemcpy(dtab, tab.data(), T.tab_bytes, cudaMemcpyHostToDevice) != cudaSuccess) return LMF_ERR_CUDA;
   // outputs
   std::vector<TreeOut> outs;
@@ -444,60 +511,6 @@ lmf_status tree_finish(TreePlan* tp, char* base, long long* res_i64, double* res
 // ---------------------------------------------------------------------------
 // kernels
 
-template <int MP>
-__global__ void __launch_bounds__(128) k_tree_rows(const __grid_constant__ RootParams p, const __grid_constant__ TreeDev d) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  float* zrow = reinterpret_cast<float*>(smem) + threadIdx.x * (MP + 4);
-  int32_t* crow = reinterpret_cast<int32_t*>(reinterpret_cast<float*>(smem) + blockDim.x * (MP + 4)) +
-                  threadIdx.x * (p.n_rowcat > 0 ? p.n_rowcat : 1);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < d.N; row += stride) {
-    const long long w = root_row_z<MP>(p, row, zrow, crow);
-    for (int g = 0; g < d.n_groups; ++g) {
-      uint16_t hit = kNoNode;
-      if (w != 0) {
-        for (int q = d.group_off[g]; q < d.group_off[g + 1]; ++q) {
-          const int n = d.group_nodes[q];
-          bool ok = true;
-          for (int k = d.pred_off[n]; k < d.pred_off[n + 1] && ok; ++k) {
-            const TreePred pr = d.preds[k];
-            const float x = zrow[pr.z];
-            ok = pr.op == 0 ? (x <= pr.thr) : (x > pr.thr);
-          }
-          if (ok) {
-            hit = static_cast<uint16_t>(n);
-            break;
-          }
-        }
-      }
-      d.node[(int64_t)g * d.N + row] = hit;
-    }
-    for (int f = 0; f < d.n_split; ++f) {
-      const float x = zrow[d.split_z[f]];
-      int lo = d.thr_off[f], hi = d.thr_off[f + 1];
-      const int base = lo;
-      while (lo < hi) {  // first threshold >= x: number of thresholds < x
-        const int mid = (lo + hi) >> 1;
-        if (d.thr[mid] < x) lo = mid + 1;
-        else hi = mid;
-      }
-      d.bucket[(int64_t)f * d.N + row] = static_cast<uint8_t>(lo - base);
-    }
-    for (int m = 0; m < d.n_mom; ++m) {
-      long long v = w;
-      if (d.mom_scale[m] > 0.0 && w != 0) {
-        double x = static_cast<double>(w);
-        if (d.mom_a[m] >= 0) x *= static_cast<double>(zrow[d.mom_a[m]]);
-        if (d.mom_b[m] >= 0) x *= static_cast<double>(zrow[d.mom_b[m]]);
-        v = llrint(x * d.mom_scale[m]);
-      } else if (d.mom_scale[m] > 0.0) {
-        v = 0;
-      }
-      d.momv[(int64_t)m * d.N + row] = v;
-    }
-  }
-}
-
 // exact 64-bit accumulation in two 32-bit shared-memory words (low word with
 // carry detection through the returned old value, high word plain)
 __device__ __forceinline__ void acc64(uint32_t* lo, uint32_t* hi, long long v) {
@@ -508,8 +521,35 @@ __device__ __forceinline__ void acc64(uint32_t* lo, uint32_t* hi, long long v) {
   if (up) atomicAdd(hi, up);
 }
 
-__global__ void __launch_bounds__(256) k_tree_hist(const __grid_constant__ TreeDev d, TreeShape sh, int n_slices) {
-  extern __shared__ __align__(16) uint32_t bins[];  // [cells] lo, then [cells] hi
+// the row's node in group g: descend the decision tree, then check the
+// candidates of the leaf on all of their predicates; kNoNode when none holds
+__device__ __forceinline__ int tree_node_of(const TreeDev& d, int g, const float* zrow) {
+  int i = d.droot[g];
+  TreeDt e = d.dt[i];
+  while (!e.leaf) {
+    i = zrow[e.z] <= e.thr ? e.left : e.right;
+    e = d.dt[i];
+  }
+  for (int c = e.left; c < e.left + e.right; ++c) {
+    const int n = d.dcand[c];
+    bool ok = true;
+    for (int k = d.pred_off[n]; k < d.pred_off[n + 1] && ok; ++k) {
+      const TreePred pr = d.preds[k];
+      const float x = zrow[pr.z];
+      ok = pr.op == 0 ? (x <= pr.thr) : (x > pr.thr);
+    }
+    if (ok) return n;
+  }
+  return kNoNode;
+}
+
+constexpr int kTreeThreads = 128;
+
+template <int MP>
+__global__ void __launch_bounds__(kTreeThreads) k_tree_fused(const __grid_constant__ RootParams p,
+                                                             const __grid_constant__ TreeDev d, TreeShape sh,
+                                                             int n_slices) {
+  extern __shared__ __align__(16) uint32_t sm[];
   const int slice = blockIdx.x % n_slices;
   const int n_split_slices = (d.n_split + sh.split_w - 1) / sh.split_w;
   const int n0 = (slice / n_split_slices) * sh.node_w;
@@ -517,10 +557,22 @@ __global__ void __launch_bounds__(256) k_tree_hist(const __grid_constant__ TreeD
   const int nw = min(sh.node_w, d.n_nodes - n0);
   const int fw = min(sh.split_w, d.n_split - f0);
   const int cells = nw * fw * d.max_bins * d.n_mom;
-  uint32_t* lo = bins;
-  uint32_t* hi = bins + cells;
-  for (int i = threadIdx.x; i < 2 * cells; i += blockDim.x) bins[i] = 0u;
+  uint32_t* lo = sm;
+  uint32_t* hi = sm + cells;
+  float* thr = reinterpret_cast<float*>(sm + 2 * cells);     // [fw][max_bins]: the slice's sorted thresholds
+  int32_t* thr_n = reinterpret_cast<int32_t*>(thr + fw * d.max_bins);
+  float* Z = reinterpret_cast<float*>(thr_n + ((fw + 3) & ~3));
+  int32_t* C = reinterpret_cast<int32_t*>(Z + kTreeThreads * (MP + 4));
+  const int ncat = p.n_rowcat > 0 ? p.n_rowcat : 1;
+  for (int i = threadIdx.x; i < 2 * cells; i += blockDim.x) sm[i] = 0u;
+  for (int f = 0; f < fw; ++f) {
+    const int t0 = d.thr_off[f0 + f], nt = d.thr_off[f0 + f + 1] - t0;
+    for (int j = threadIdx.x; j < nt; j += blockDim.x) thr[f * d.max_bins + j] = d.thr[t0 + j];
+    if (threadIdx.x == 0) thr_n[f] = nt;
+  }
   __shared__ uint32_t chunk_s;
+  float* zrow = Z + threadIdx.x * (MP + 4);
+  int32_t* crow = C + threadIdx.x * ncat;
   __syncthreads();
   const int64_t n_chunks = (d.N + sh.chunk - 1) / sh.chunk;
   for (;;) {
@@ -531,18 +583,36 @@ __global__ void __launch_bounds__(256) k_tree_hist(const __grid_constant__ TreeD
     if (c >= n_chunks) break;
     const int64_t r1 = d.N < (c + 1) * sh.chunk ? d.N : (c + 1) * sh.chunk;
     for (int64_t row = c * sh.chunk + threadIdx.x; row < r1; row += blockDim.x) {
+      const long long w = root_row_z<MP>(p, row, zrow, crow);
+      if (w == 0) continue;
       long long mv[kTreeMaxMom];
-      bool loaded = false;
+      bool have = false;
       for (int g = 0; g < d.n_groups; ++g) {
-        const int n = d.node[(int64_t)g * d.N + row];
+        const int n = tree_node_of(d, g, zrow);
         if (n == kNoNode || n < n0 || n >= n0 + nw) continue;
-        if (!loaded) {
-          for (int m = 0; m < d.n_mom; ++m) mv[m] = d.momv[(int64_t)m * d.N + row];
-          loaded = true;
+        if (!have) {  // the row's fixed-point moments, once
+          for (int m = 0; m < d.n_mom; ++m) {
+            long long v = w;
+            if (d.mom_scale[m] > 0.0) {
+              double x = static_cast<double>(w);
+              if (d.mom_a[m] >= 0) x *= static_cast<double>(zrow[d.mom_a[m]]);
+              if (d.mom_b[m] >= 0) x *= static_cast<double>(zrow[d.mom_b[m]]);
+              v = llrint(x * d.mom_scale[m]);
+            }
+            mv[m] = v;
+          }
+          have = true;
         }
         for (int f = 0; f < fw; ++f) {
-          const int b = d.bucket[(int64_t)(f0 + f) * d.N + row];
-          const int cell = (((n - n0) * fw + f) * d.max_bins + b) * d.n_mom;
+          const float x = zrow[d.split_z[f0 + f]];
+          const float* t = thr + f * d.max_bins;
+          int l = 0, h = thr_n[f];
+          while (l < h) {  // number of thresholds < x
+            const int mid = (l + h) >> 1;
+            if (t[mid] < x) l = mid + 1;
+            else h = mid;
+          }
+          const int cell = (((n - n0) * fw + f) * d.max_bins + l) * d.n_mom;
           for (int m = 0; m < d.n_mom; ++m)
             if (mv[m] != 0) acc64(lo + cell + m, hi + cell + m, mv[m]);
         }
@@ -581,60 +651,45 @@ __global__ void k_tree_out(const __grid_constant__ TreeDev d, const TreeOut* out
 
 namespace {
 
-size_t rows_smem(const TreePlanImpl& T, const RootParams& rp) {
-  return static_cast<size_t>(128) * (T.mp + 4) * 4 + static_cast<size_t>(128) * (rp.n_rowcat > 0 ? rp.n_rowcat : 1) * 4;
+size_t fused_smem(const TreePlanImpl& T, const RootParams& rp, const TreeShape& sh) {
+  const size_t bins = slice_bytes(T, sh.node_w, sh.split_w);
+  const size_t thr = static_cast<size_t>(sh.split_w) * T.max_bins * 4 + ((sh.split_w + 3) & ~3) * 4;
+  const size_t z = static_cast<size_t>(kTreeThreads) * (T.mp + 4) * 4;
+  const size_t cat = static_cast<size_t>(kTreeThreads) * (rp.n_rowcat > 0 ? rp.n_rowcat : 1) * 4;
+  return bins + thr + z + cat;
 }
 
-cudaError_t launch_rows(const TreePlanImpl& T, const RootParams& rp, cudaStream_t s) {
-  const size_t sm = rows_smem(T, rp);
-  const int grid = T.num_sms * 8;
-  cudaError_t e = cudaSuccess;
-  switch (T.mp) {
-    case 16:
-      e = cudaFuncSetAttribute(k_tree_rows<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e == cudaSuccess) k_tree_rows<16><<<grid, 128, sm, s>>>(rp, T.dev);
-      break;
-    case 32:
-      e = cudaFuncSetAttribute(k_tree_rows<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e == cudaSuccess) k_tree_rows<32><<<grid, 128, sm, s>>>(rp, T.dev);
-      break;
-    case 48:
-      e = cudaFuncSetAttribute(k_tree_rows<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e == cudaSuccess) k_tree_rows<48><<<grid, 128, sm, s>>>(rp, T.dev);
-      break;
-    default:
-      e = cudaFuncSetAttribute(k_tree_rows<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e == cudaSuccess) k_tree_rows<64><<<grid, 128, sm, s>>>(rp, T.dev);
-      break;
-  }
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_hist(const TreePlanImpl& T, const TreeShape& sh, cudaStream_t s) {
+template <int MP>
+cudaError_t launch_fused_mp(const TreePlanImpl& T, const RootParams& rp, const TreeShape& sh, cudaStream_t s) {
   const int ns = n_slices(T, sh);
-  const size_t sm = slice_bytes(T, sh.node_w, sh.split_w);
+  const size_t sm = fused_smem(T, rp, sh);
   int per = (int)((static_cast<int64_t>(T.num_sms) * sh.cps + ns - 1) / ns);
   if (per < 1) per = 1;
-  const int grid = ns * per;
-  cudaError_t e = cudaFuncSetAttribute(k_tree_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(k_tree_fused<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_tree_hist<<<grid, 256, sm, s>>>(T.dev, sh, ns);
+  k_tree_fused<MP><<<ns * per, kTreeThreads, sm, s>>>(rp, T.dev, sh, ns);
   return cudaGetLastError();
+}
+
+cudaError_t launch_fused(const TreePlanImpl& T, const RootParams& rp, const TreeShape& sh, cudaStream_t s) {
+  switch (T.mp) {
+    case 16: return launch_fused_mp<16>(T, rp, sh, s);
+    case 32: return launch_fused_mp<32>(T, rp, sh, s);
+    case 48: return launch_fused_mp<48>(T, rp, sh, s);
+    default: return launch_fused_mp<64>(T, rp, sh, s);
+  }
 }
 
 }  // namespace
 
 cudaError_t tree_launch(TreePlan* tp, const RootParams& rp, cudaStream_t s, int* nk) {
   TreePlanImpl& T = *tp->impl;
-  cudaError_t e = launch_rows(T, rp, s);
-  if (e != cudaSuccess) return e;
-  e = launch_hist(T, T.shape, s);
+  cudaError_t e = launch_fused(T, rp, T.shape, s);
   if (e != cudaSuccess) return e;
   if (T.n_outs > 0) {
     k_tree_out<<<(T.n_outs + 255) / 256, 256, 0, s>>>(T.dev, T.d_outs, T.n_outs, T.res_i64, T.res_f64);
   }
-  *nk += 3;
+  *nk += 2;
   return cudaGetLastError();
 }
 
@@ -643,17 +698,25 @@ bool tree_needs_tuning(const TreePlan* tp) { return tp && tp->impl && !tp->impl-
 cudaError_t tree_autotune(TreePlan* tp, const RootParams& rp, cudaStream_t s) {
   TreePlanImpl& T = *tp->impl;
   (void)rp;
+  // every slice recomputes the row pass: the fewest slices that fit, with some
+  // variants of the node / split cut, CTAs per SM and chunk size
   std::vector<TreeShape> cand;
-  for (int node_w : {T.dev.n_nodes, (T.dev.n_nodes + 1) / 2, (T.dev.n_nodes + 3) / 4})
-    for (int split_w : {1, 2, 4, 8})
+  const int NS = std::max(1, T.dev.n_split), NN = std::max(1, T.dev.n_nodes);
+  constexpr size_t kCap = 220 * 1024;
+  for (int sd : {1, 2, 4}) {
+    const int split_w = (NS + sd - 1) / sd;
+    int nd = 1;
+    while (nd < NN && fused_smem(T, rp, {split_w, (NN + nd - 1) / nd, 1, 4096}) > kCap) nd *= 2;
+    const int node_w = (NN + nd - 1) / nd;
+    for (int nw : {node_w, (node_w + 1) / 2})
       for (int cps : {1, 2})
         for (int chunk : {4096, 16384}) {
-          if (node_w < 1 || split_w > std::max(1, T.dev.n_split)) continue;
-          const size_t b = slice_bytes(T, node_w, split_w);
-          if (b * cps > 200 * 1024 || b > 200 * 1024) continue;
-          if (n_slices(T, {split_w, node_w, cps, chunk}) > T.max_slices) continue;
-          cand.push_back({split_w, node_w, cps, chunk});
+          const TreeShape c{split_w, nw, cps, chunk};
+          if (nw < 1 || fused_smem(T, rp, c) * cps > kCap) continue;
+          if (n_slices(T, c) > T.max_slices) continue;
+          cand.push_back(c);
         }
+  }
   if (cand.empty()) cand.push_back(T.shape);
   cudaEvent_t a, b;
   cudaEventCreate(&a);
@@ -665,7 +728,7 @@ cudaError_t tree_autotune(TreePlan* tp, const RootParams& rp, cudaStream_t s) {
     cudaMemsetAsync(T.dev.queue, 0, static_cast<size_t>(T.max_slices) * 4, s);
     cudaMemsetAsync(T.dev.H, 0, hbytes, s);
     cudaEventRecord(a, s);
-    cudaError_t e = launch_hist(T, c, s);
+    cudaError_t e = launch_fused(T, rp, c, s);
     cudaEventRecord(b, s);
     if (e != cudaSuccess) continue;
     if (cudaEventSynchronize(b) != cudaSuccess) break;

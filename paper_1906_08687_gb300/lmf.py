@@ -28,6 +28,7 @@ LMF_MAX_GROUP_BY = 3
 LMF_STAGES = 5
 LMF_PLAN_FEATURES = 24
 LMF_PLAN_NO_JIT = 1
+LMF_PLAN_ROW_GRAM = 2
 LMF_DEVICE, LMF_HOST_COPY, LMF_HOST_MAPPED = 0, 1, 2
 STAGE_NAMES = ['input', 'views', 'root_scan', 'tree', 'finalize']
 
@@ -71,7 +72,7 @@ class lmf_plan_stats(ctypes.Structure):
                 ('tree_chunk', ctypes.c_int32),
                 ('root_rows', ctypes.c_int64), ('scratch_bytes', ctypes.c_int64),
                 ('resident_group', ctypes.c_int32), ('resident_cells', ctypes.c_int32),
-                ('jit', ctypes.c_int32), ('reserved_stats', ctypes.c_int32)]
+                ('jit', ctypes.c_int32), ('key_level', ctypes.c_int32)]
 
 
 # every symbol include/lmf.h declares, with its ctypes signature
@@ -228,9 +229,9 @@ class Engine:
 
     def plan(self, batch: int, precision: int = LMF_PREC_SPLIT_BF16, batching: int = LMF_BATCH_GRAPH,
              tile_rows: int = 0, ctas_per_sm: int = 0, root_mode: int = 0, root_rel: int = 0,
-             no_merge: int = 0, jit: bool = True):
-        o = lmf_plan_opts(precision, batching, tile_rows, ctas_per_sm, root_mode, root_rel, no_merge,
-                          0 if jit else LMF_PLAN_NO_JIT)
+             no_merge: int = 0, jit: bool = True, key_level: bool = True):
+        flags = (0 if jit else LMF_PLAN_NO_JIT) | (0 if key_level else LMF_PLAN_ROW_GRAM)
+        o = lmf_plan_opts(precision, batching, tile_rows, ctas_per_sm, root_mode, root_rel, no_merge, flags)
         self._check(self.lib.lmf_plan(self.ctx, batch, ctypes.byref(o)), 'lmf_plan')
 
     def plan_info(self, batch: int) -> dict:

@@ -183,6 +183,59 @@ int main() {
       for (int s = 0; s < rp.rv[r].n_slot; ++s) rp.rv[r].slot_z[s] = static_cast<int16_t>((s * 3) % rp.m);
     check(rp, 64, {}, "wide", false);
   }
+  {  // key-level form of the sorted snowflake: a bulk, a runs and a resident reverse view
+    RootParams rp = base(true);
+    rp.lean = 1;
+    rp.gram_off = 1;
+    rp.gram_n = rp.n_x;
+    rp.res_grp = 2;
+    rp.res_cells = 1800;
+    const int nslot[3] = {8, 20, 25}, mode[3] = {kRvBulk, kRvRuns, kRvResident};
+    for (int r = 0; r < 3; ++r) {
+      RevView& R = rp.rv[r];
+      R.n_slot = nslot[r];
+      for (int s = 0; s < R.n_slot; ++s) R.slot_z[s] = static_cast<int16_t>(1 + s);
+      R.stride = (1 + R.n_slot + 1) & ~1;
+      R.hstride = R.rstride = R.stride;
+      R.mode = mode[r];
+    }
+    rp.res_rv = 2;
+    // the means of groups 0 and 1 come as fixed-point images from their fix records
+    for (int z = 0; z < kMaxZ; ++z) rp.fix_of_z[z] = -1;
+    for (int g = 0; g < 2; ++g)
+      for (int j = 0; j < rp.grp[g].n_mu; ++j) rp.fix_of_z[rp.grp_zoff[g] + j] = static_cast<int16_t>(j);
+    rp.n_cv = 4;
+    for (int v = 0; v < 4; ++v) {
+      CatView& C = rp.cv[v];
+      C.grp = v < 2 ? 1 : 2;
+      C.bcat = v;
+      C.dom = 50 + v;
+      C.res_off = v < 2 ? -1 : 400 * v;
+    }
+    bad += !compile(jit_lean_source(rp, {}, 3), "key-level snowflake");
+    // random order: every view summed per run, root categories and per-row tables with features,
+    // every value converted in the row pass
+    for (int z = 0; z < kMaxZ; ++z) rp.fix_of_z[z] = -1;
+    rp.res_cells = 0;
+    rp.res_rv = -1;
+    for (int r = 0; r < 3; ++r) rp.rv[r].mode = kRvRuns;
+    rp.n_cv = 0;
+    rp.n_rcat = 1;
+    rp.rcat_dom[0] = 9;
+    rp.n_rowcat += 1;
+    std::vector<DirectAgg> dir = {pair(0, rp.n_rowcat - 1, 11, 9)};
+    DirectAgg s{};
+    s.n_gb = 1;
+    s.cat[0] = rp.n_rowcat - 1;
+    s.dom[0] = 9;
+    s.z = 4;
+    s.scale = 1024.f;
+    s.cache_off = -1;
+    s.res_off = -1;
+    dir.push_back(s);
+    rp.n_direct = static_cast<int>(dir.size());
+    bad += !compile(jit_lean_source(rp, dir, 2), "key-level random");
+  }
   {  // a root without probe groups: features only
     RootParams rp{};
     rp.N = 1000;

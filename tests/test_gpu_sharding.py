@@ -1,49 +1,59 @@
-"""Sharding of the root by row ranges, emulated on one GPU: every shard runs
-the whole batch over its rows (dimensions replicated), the partial results
-are summed on the host (int64 counts exactly, FP64 sums), and the sum equals
-the unsharded run -- counts bit for bit, sums within the error rule against
-the oracle.  This is the exchange a multi-GPU run would do with one
-all-reduce, emulated on one GPU."""
-import dataclasses
-
+"""Sharding of the root by row ranges (paper_1906_08687_gb300.shard), emulated
+on one GPU: every shard registers its slice of the root's device columns (the
+same memory, offset pointers) with the dimensions whole, runs the whole batch,
+and exports its packed results to device buffers; the exchange a multi-GPU
+run does with one all-reduce per array is emulated by summing the shards'
+device buffers.  The sum equals the unsharded run -- counts bit for bit, sums
+within the error rule against the oracle -- and the host-side result layout
+equals the engine's."""
 import numpy as np
 import pytest
 
 from oracle import oracle
-from workloads import Relation, Schema, config2, config4
+from workloads import config2, config4, to_device
 
-from lmf_testlib import ARITH_FLOOR, compare, run_engine
+from lmf_testlib import ARITH_FLOOR, compare
 
 pytestmark = pytest.mark.gpu
 
 
-def _shard(sch, lo, hi):
-    root = sch.rel(sch.root)
-    part = Relation(root.name, [dataclasses.replace(c, data=np.ascontiguousarray(c.data[lo:hi]))
-                                for c in root.columns])
-    rels = [part if r.name == sch.root else r for r in sch.relations]
-    return Schema(rels, sch.edges, sch.root, dict(sch.meta))
+def _packed_run(sch, batch, tensors):
+    import torch
+    from paper_1906_08687_gb300 import Engine, register_schema
+    eng = Engine(0)
+    register_schema(eng, sch, tensors)
+    bid = eng.declare_batch(batch)
+    eng.plan(bid, precision=0, batching=1)
+    eng.run(bid)
+    eng.sync(bid)
+    n_i, n_f = eng.result_sizes(bid)
+    i64 = torch.zeros(max(1, n_i), dtype=torch.int64, device='cuda')
+    f64 = torch.zeros(max(1, n_f), dtype=torch.float64, device='cuda')
+    eng.read_results(bid, i64.data_ptr(), f64.data_ptr(), True)
+    torch.cuda.synchronize()
+    layout = eng.result_layout(bid, len(batch))
+    eng.close()
+    return i64[:n_i], f64[:n_f], layout
 
 
-@pytest.mark.parametrize('make,bounds', [
-    (lambda: config2(300_007), [0, 100_000, 200_003, 300_007]),
-    (lambda: config4(200_001), [0, 1, 77_777, 200_001]),
-])
-def test_root_partition_sums_to_whole(make, bounds):
+@pytest.mark.parametrize('make,world', [(lambda: config2(300_007), 3), (lambda: config4(200_001), 4)])
+def test_root_partition_sums_to_whole(make, world):
+    from paper_1906_08687_gb300 import shard
     sch, batch = make()
-    whole, _, e0 = run_engine(sch, batch, precision=0, batching=1)
-    e0.close()
-    parts = []
-    for lo, hi in zip(bounds[:-1], bounds[1:]):
-        got, _, e = run_engine(_shard(sch, lo, hi), batch, precision=0, batching=1)
-        parts.append(got)
-        e.close()
+    dev = to_device(sch)
+    n = sch.rel(sch.root).nrows
+    wi, wf, layout = _packed_run(sch, batch, dev)
+    mine, n_i, n_f = shard.result_layout(sch, batch)
+    assert n_i == wi.numel() and n_f == wf.numel()
+    assert [(n, off) for _, n, off in mine] == [(n, off) for n, _, off in layout]
+    si, sf = None, None
+    for r in range(world):
+        b, e = shard.row_range(n, r, world)
+        pi, pf, _ = _packed_run(shard.shard_schema(sch, b, e), batch, shard.shard_tensors(sch, dev, b, e))
+        si = pi if si is None else si + pi         # the all-reduce (sum), emulated
+        sf = pf if sf is None else sf + pf
+    assert np.array_equal(si.cpu().numpy(), wi.cpu().numpy())      # counts bit for bit
+    got = shard.unpack(si.cpu().numpy(), sf.cpu().numpy(), sch, batch)
     want = oracle.evaluate(sch, batch)
-    summed = []
-    for i in range(len(batch)):
-        s = sum(np.asarray(p[i]) for p in parts)
-        if want.kinds[i] == 'count':
-            assert np.array_equal(s.astype(np.int64), np.asarray(whole[i]).astype(np.int64)), batch[i]
-        summed.append(s)
-    fails, stats = compare(summed, want, arith_floor=ARITH_FLOOR)
+    fails, stats = compare(got, want, arith_floor=ARITH_FLOOR)
     assert not fails, (fails[:3], stats)

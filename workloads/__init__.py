@@ -10,3 +10,4 @@ from .schemas import (  # noqa: F401
     config1, config2, config3, config4, config5_schema, tiny_schema, chain_schema, spread_keys,
     SEED_BASE,
 )
+from .tensors import to_device, to_pinned  # noqa: F401
