@@ -7,7 +7,7 @@
 // that has handed all device memory to another framework.  For them this entry
 // point runs the plain root-scan kernel (one row per thread, FP32 register
 // blocks, per-CTA FP64 partial Grams combined in a fixed order) with its
-// scratch -- the per-CTA partials, counts and status word -- in the file-scope
+// scratch -- the per-CTA partials and counts -- in the file-scope
 // array below instead of a plan arena.  The caller passes the input columns and
 // the output buffer.
 //
@@ -36,6 +36,9 @@ double* g_scratch_ptr[kMaxDevices] = {};       // device address of g_scratch, p
 
 // the reason is for a reader of this file; callers get the status code
 lmf_status reject(lmf_status s, const char* /*why*/) { return s; }
+
+// G[0][0] is COUNT: the exact int64 row count, not the FP32 sum of ones
+__global__ void k_put_count(double* G, const long long* count) { G[0] = static_cast<double>(*count); }
 
 }  // namespace
 
@@ -89,17 +92,20 @@ extern "C" lmf_status lmf_gram_noalloc(const float* const* dev_cols, int ncols, 
   p.n_direct = 0;
   p.direct = nullptr;
   p.n_om = 0;
-  uint32_t* status = reinterpret_cast<uint32_t*>(scratch + kPartDoubles + kMaxGrid);
+  // the kernel reports out-of-range categories through the status word; this
+  // input has no categorical column, so nothing is ever written there and
+  // nothing reads it (it only has to be a valid address)
+  p.status = reinterpret_cast<uint32_t*>(scratch + kPartDoubles + kMaxGrid);
   long long* count = reinterpret_cast<long long*>(scratch + kPartDoubles + kMaxGrid + 1);
-  p.status = status;
 
-  // the status word must start at zero; the partials and counts are written in full
-  if (cudaMemsetAsync(status, 0, sizeof(uint32_t), s) != cudaSuccess) return reject(LMF_ERR_CUDA, "memset failed");
+  // the partials and counts are written in full by every call: nothing to clear
   const size_t smem = root_plain_smem(kMP, 0);
   if (root_plain_prepare(kMP, smem) != cudaSuccess) return reject(LMF_ERR_CUDA, "kernel attribute failed");
   if (launch_root_plain(p, kMP, static_cast<int>(grid), n_tiles, smem, s) != cudaSuccess)
     return reject(LMF_ERR_CUDA, "root-scan launch failed");
   if (launch_combine(scratch, static_cast<int>(grid), kMP, p.m, p.cnt_part, dev_gram, count, s) != cudaSuccess)
     return reject(LMF_ERR_CUDA, "combine launch failed");
+  k_put_count<<<1, 1, 0, s>>>(dev_gram, count);
+  if (cudaGetLastError() != cudaSuccess) return reject(LMF_ERR_CUDA, "count placement failed");
   return LMF_OK;
 }

@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 def _columns(n=300_007, k=7, seed=42):
     rng = np.random.default_rng(seed)
     cols = [rng.standard_normal(n).astype(np.float32) for _ in range(k)]
-    cols[1] = (np.abs(cols[1]) * 40 + 3).astype(np.float32)       # a positive, large column
+    if k > 1:
+        cols[1] = (np.abs(cols[1]) * 40 + 3).astype(np.float32)   # a positive, large column
     return cols
 
 
@@ -66,6 +67,34 @@ def test_noalloc_matches_regular_entry_point_twice():
         allow = 1e-6 * np.maximum(np.abs(want), 1e-3 * scale)
         assert np.all(err <= allow), (call, float(np.max(err / allow)))
         assert got[0, 0] == n
+
+
+@pytest.mark.parametrize('n,k', [(0, 3), (100, 1), (257, 31), (300_007, 0)])
+def test_noalloc_edge_shapes(n, k):
+    """No rows, one column, the full 31-column block with a ragged tile, no
+    columns; on a stream of its own.  Against NumPy's FP64 Gram of the same
+    FP32 columns (plus the small-input arithmetic floor 2^-21 * sum|v|), and
+    G[0][0] exactly the row count."""
+    import torch
+    from paper_1906_08687_gb300 import lmf
+    lib = lmf.load()
+    cols = _columns(n, k, seed=7 + n + k) if k else []
+    m = k + 1
+    Z = np.stack([np.ones(n)] + [c.astype(np.float64) for c in cols]) if n else np.zeros((m, 0))
+    want = Z @ Z.T
+    scale = np.abs(Z) @ np.abs(Z).T
+    dev = [torch.from_numpy(c).cuda() for c in cols]
+    stream = torch.cuda.Stream()
+    out = torch.full((m, m), float('nan'), dtype=torch.float64, device='cuda')
+    arr = (ctypes.c_void_p * k)(*[c.data_ptr() for c in dev]) if k else None
+    with torch.cuda.stream(stream):
+        assert lib.lmf_gram_noalloc(arr, k, n, ctypes.c_void_p(out.data_ptr()),
+                                    ctypes.c_void_p(stream.cuda_stream)) == lmf.LMF_OK
+    stream.synchronize()
+    got = out.cpu().numpy()
+    allow = np.maximum(1e-6 * np.maximum(np.abs(want), 1e-3 * scale), 2.0 ** -21 * scale)
+    assert np.all(np.abs(got - want) <= allow), float(np.max(np.abs(got - want) - allow))
+    assert got[0, 0] == n
 
 
 def test_noalloc_refuses_oversized_and_null():
