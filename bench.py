@@ -54,6 +54,8 @@ KERNEL_SOURCES = ['paper_1906_08687_gb300/csrc/lmf_tree.cu',
                   'paper_1906_08687_gb300/csrc/lmf_gram_tc.cu',
                   'paper_1906_08687_gb300/csrc/lmf_rowpass.cuh',
                   'paper_1906_08687_gb300/csrc/lmf_root_plain.cuh',
+                  'paper_1906_08687_gb300/csrc/lmf_root_lean.cuh',
+                  'paper_1906_08687_gb300/csrc/lmf_root_tc.cuh',
                   'paper_1906_08687_gb300/csrc/lmf_jit.cu',
                   'paper_1906_08687_gb300/csrc/lmf_internal.h']
 
@@ -67,8 +69,9 @@ def parse():
     ap.add_argument('--workload', default='snowflake', choices=sorted(WORKLOADS))
     ap.add_argument('--n-fact', type=int, default=None, help='fact rows (default: the workload\'s)')
     ap.add_argument('--precision', default='auto', choices=['auto', 'split', 'plain'],
-                    help='Gram precision of the chosen plan; auto times both candidates '
-                         '(split-bf16 tensor cores, FP32 CUDA cores) and keeps the faster')
+                    help='Gram precision of the chosen plan; auto lets the learned plan choice '
+                         '(shipped cost-model checkpoint, the Sec. 3.3 rule without one) pick the '
+                         'root, the Gram form and view merging')
     ap.add_argument('--fact-order', default='sorted', choices=['sorted', 'random'],
                     help='fact rows sorted by their join attributes (the input order of the '
                          "paper's experiments) or in generation order")
@@ -389,11 +392,14 @@ def main():
     dev = to_device(sch, f'cuda:{local}')
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
-    def make(precision, batching, tensors, on_host=False, jit=True):
+    def make(precision, batching, tensors, on_host=False, jit=True, opts=None):
         eng = Engine(local)
         register_schema(eng, sch, tensors, on_host=on_host)
         bid = eng.declare_batch(batch)
-        eng.plan(bid, precision=precision, batching=batching, jit=jit)
+        if opts is not None:
+            eng.plan_opts(bid, opts)
+        else:
+            eng.plan(bid, precision=precision, batching=batching, jit=jit)
         return eng, bid
 
     def timed(eng, bid, steps, warmup, sampler=None):
@@ -415,27 +421,34 @@ def main():
         eng.sync(bid)
         return max_over_ranks(ws, e0.elapsed_time(e1) / steps), clocks
 
-    # chosen form: one CUDA graph per run, the root scan compiled for the plan;
-    # the Gram precision is the faster of the two candidates (auto) or fixed
+    # chosen form: the learned plan choice (lmf_plan_learned with the cost-model
+    # checkpoint shipped in the package; the Sec. 3.3 root rule when there is
+    # no usable checkpoint), one CUDA graph per run; --precision fixes the Gram
+    # form instead
+    from paper_1906_08687_gb300 import costmodel
+    from paper_1906_08687_gb300.lmf import (LMF_BATCH_GRAPH, LMF_PLAN_ROW_GRAM, LMF_PREC_SPLIT_BF16,
+                                            LMF_ROOT_HEURISTIC, lmf_plan_opts)
+    base = lmf_plan_opts(LMF_PREC_SPLIT_BF16, LMF_BATCH_GRAPH, 0, 0, 0, 0, 0, 0)
     names = {'split': 1, 'plain': 0}
-    cands = ['split', 'plain'] if args.precision == 'auto' else [args.precision]
-    cand_ms = {}
-    best = None
-    for cname in cands:
-        e_c, b_c = make(names[cname], 1, dev)
-        if e_c.plan_info(b_c)['precision'] != names[cname]:   # not plannable in this form
-            e_c.close()
-            continue
-        cand_ms[cname], _ = timed(e_c, b_c, max(3, args.steps // 2), args.warmup)
-        if best is None or cand_ms[cname] < cand_ms[best[0]]:
-            if best is not None:
-                best[1].close()
-            best = (cname, e_c, b_c)
-        else:
-            e_c.close()
-    chosen, eng, bid = best
-    prec = names[chosen]
+    eng = Engine(local)
+    register_schema(eng, sch, dev)
+    bid = eng.declare_batch(batch)
+    if args.precision == 'auto':
+        model, origin = costmodel.load_shipped(local)
+        chosen_opts = eng.plan_learned(bid, model, base)
+    else:
+        origin = f'fixed by --precision {args.precision}'
+        eng.plan(bid, precision=names[args.precision], batching=1)
+        chosen_opts = lmf_plan_opts(names[args.precision], LMF_BATCH_GRAPH, 0, 0, 1,
+                                    eng.plan_info(bid)['root_rel'], 0, 0)
+    # the rule's plan (Sec. 3.3 root, default options) for comparison
+    e_r, b_r = make(None, None, dev, opts=lmf_plan_opts(LMF_PREC_SPLIT_BF16, LMF_BATCH_GRAPH, 0, 0,
+                                                        LMF_ROOT_HEURISTIC, 0, 0, 0))
+    rule_ms, _ = timed(e_r, b_r, max(3, args.steps // 2), args.warmup)
+    rule_info = e_r.plan_info(b_r)
+    e_r.close()
     info = eng.plan_info(bid)
+    prec = info['precision']
     join_rows = info['root_rows']   # unique dimension keys: |join| = fact rows
     sampler = ClockSampler(local)
     ms, clocks = timed(eng, bid, args.steps, args.warmup, sampler)
@@ -468,7 +481,7 @@ def main():
     host = to_pinned(sch)
 
     def e2e(modes):
-        eng_e, bid_e = make(prec, 1, host, on_host=modes)
+        eng_e, bid_e = make(None, None, host, on_host=modes, opts=chosen_opts)
         n_i64, n_f64 = eng_e.result_sizes(bid_e)
         out_i = torch.empty(max(1, n_i64), dtype=torch.int64).pin_memory()
         out_f = torch.empty(max(1, n_f64), dtype=torch.float64).pin_memory()
@@ -503,7 +516,9 @@ def main():
     peaks = measured_peaks()
     achieved = algo / (root_ms * 1e-3) / 1e9
     roof = {'bound': 'hbm', 'achieved': achieved, 'peak': peaks['hbm_gbs'], 'unit': 'GB/s',
-            'frac': achieved / peaks['hbm_gbs'], 'traffic': profiled_traffic(chosen, args.profile),
+            'frac': achieved / peaks['hbm_gbs'],
+            'traffic': profiled_traffic('split' if prec == 1 else ('keylevel' if info['key_level'] else 'plain'),
+                                        args.profile),
             'peak_source': peaks['source'], 'kernel': f'{dom_stage} stage',
             'algorithmic_bytes_per_launch': algo, 'launch_ms': root_ms,
             'stage_ms': {n: float(v) for n, v in zip(STAGE_NAMES, stage)}}
@@ -516,10 +531,17 @@ def main():
         'data': 'synthetic',
         'config': {'workload': WORKLOAD_TEXT.get(args.workload, '{name}').format(name=sch.meta['name']),
                    'n_aggregates': n_agg, 'join_rows': join_rows, 'precision': info['precision'],
-                   'plan': {'gram': 'split-bf16 tcgen05' if prec == 1 else 'FP32 CUDA cores (TwoSum)',
+                   'plan': {'origin': origin,
+                            'root': sch.relations[info['root_rel']].name,
+                            'gram': ('split-bf16 tcgen05' if prec == 1 else
+                                     'FP32 root features + key-level blocks' if info['key_level'] else
+                                     'FP32 CUDA cores, all blocks per row'),
+                            'no_merge': int(chosen_opts.no_merge),
                             'root_scan_compiled': bool(info['jit']),
                             'resident_group': info['resident_group'],
-                            'candidates_ms_per_step': cand_ms},
+                            'rule_plan': {'root': sch.relations[rule_info['root_rel']].name,
+                                          'precision': rule_info['precision'],
+                                          'key_level': rule_info['key_level'], 'ms_per_step': rule_ms}},
                    'fact_order': fact_order_text(sch, args.fact_order),
                    'batching': 'cuda-graph', 'kernels_per_step': info['n_kernels_per_run'],
                    'l2': f'inputs larger than L2 ({fact_bytes / 1e6:.0f} MB fact table per step)',

@@ -31,6 +31,8 @@
  *   - LMF_LOG=1 in the environment prints every plan (root, probe groups,
  *     record sizes, root-scan form and launch shape) and the stage times of
  *     lmf_run_profiled to stderr.
+ *   - LMF_JIT_DUMP=<directory> writes the CUDA source of every root scan the
+ *     planner compiles there (<kernel>_<hash of the source>.cu).
  */
 #ifndef LMF_H_
 #define LMF_H_
@@ -325,18 +327,37 @@ lmf_status lmf_read_result(lmf_ctx* ctx, int batch_id, int agg, void* dst);
  * and the reference its regret is measured against.
  * ------------------------------------------------------------------------- */
 
-/* Number of features lmf_plan_features writes. */
-#define LMF_PLAN_FEATURES 24
+/* Number of features lmf_plan_features writes: sizes of the relations and of
+   the root, counts of views, probe groups, aggregates of each kind, record
+   bytes, z length, key multiplicities, the Gram form (tensor core, key-level),
+   the grid, view merging, root position, general-view work, reverse-view
+   slots, per-row tables, tree batches, and the mean log2 run length of equal
+   foreign keys in the root's order. */
+#define LMF_PLAN_FEATURES 26
 
 /*
- * Candidate plans for a declared batch: up to four roots (the declared one,
- * the Sec. 3.3 rule's one, the largest relations) x precision x CTAs per SM x
- * view merging, each as explicit plan options derived from *base (NULL: zero
- * options).  Writes min(max, count) entries to out (may be NULL) and the count
- * to *n.  Errors: LMF_ERR_ARG (null n), LMF_ERR_STATE before lmf_declare_join.
+ * Candidate plans for a declared batch: up to three roots (the declared one,
+ * the Sec. 3.3 rule's one, the largest relations) x Gram form (plain FP32 with
+ * key-level blocks, plain FP32 all at the row level, split bf16) x view
+ * merging, each as explicit plan options derived from *base (NULL: zero
+ * options; its CTAs per SM and compile flag carry over).  Writes
+ * min(max, count) entries to out (may be NULL) and the count to *n.
+ * Errors: LMF_ERR_ARG (null n), LMF_ERR_STATE before lmf_declare_join.
  */
 lmf_status lmf_plan_candidates(lmf_ctx* ctx, int batch_id, const lmf_plan_opts* base,
                                lmf_plan_opts* out, int max, int* n);
+
+/*
+ * Compile, on up to `threads` host threads (0: 8), the plan-time root scans of
+ * every candidate of lmf_plan_candidates(base) into the process-wide cache of
+ * compiled sources, so that planning those candidates afterwards finds them
+ * compiled.  The candidates are planned without compiling (the batch is left
+ * without a plan: plan it again before running).  *n_compiled (may be NULL)
+ * gets the number of sources compiled.  Errors: LMF_ERR_ARG, LMF_ERR_STATE
+ * before lmf_declare_join.
+ */
+lmf_status lmf_plan_precompile(lmf_ctx* ctx, int batch_id, const lmf_plan_opts* base, int threads,
+                               int* n_compiled);
 
 /*
  * Features of the batch's current plan (host array of n >= LMF_PLAN_FEATURES
@@ -383,7 +404,8 @@ lmf_status lmf_mlp_train_step(lmf_mlp* m, const float* x_dev, const float* y_dev
 
 /*
  * Plan the batch with the candidate the model predicts fastest (every
- * candidate is planned to compute its features).  model == NULL falls back to
+ * candidate is planned without compiling to compute its features; only the
+ * chosen one is compiled).  model == NULL falls back to
  * the Sec. 3.3 root rule with *base.  The chosen options go to *chosen (may be
  * NULL).  Errors: LMF_ERR_STATE before lmf_declare_join, those of lmf_plan.
  */

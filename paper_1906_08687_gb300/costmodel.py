@@ -1,13 +1,13 @@
 """Learned plan choice for the engine: timing corpus, training, regret.
 
-The planner's candidates for a batch (lmf_plan_candidates: roots x precision x
-CTAs per SM x view merging) are each planned and timed on the GPU; the cost
+The planner's candidates for a batch (lmf_plan_candidates: roots x Gram form x
+view merging) are each planned, compiled and timed on the GPU; the cost
 model (lmf_mlp, trained here with the engine's own forward/backward/Adam
 kernels) learns log run time from the plan features; on held-out schemas its
 choice is compared with the exhaustive best and with the paper's root rule
 (Sec. 3.3), which stays the fallback.
 
-    python -m paper_1906_08687_gb300.costmodel --schemas 500 --train 400
+    python -m paper_1906_08687_gb300.costmodel --schemas 500 --train 400 --scale 0.1
 """
 from __future__ import annotations
 
@@ -27,7 +27,7 @@ from .lmf import (LMF_BATCH_GRAPH, LMF_PLAN_FEATURES, LMF_PLAN_NO_JIT, LMF_PREC_
 
 
 def _opts_tuple(o) -> tuple:
-    return (o.precision, o.batching, o.tile_rows, o.ctas_per_sm, o.root_mode, o.root_rel, o.no_merge)
+    return (o.precision, o.batching, o.tile_rows, o.ctas_per_sm, o.root_mode, o.root_rel, o.no_merge, o.flags)
 
 
 def time_run(eng: Engine, bid: int, runs: int, max_ms: float) -> float:
@@ -51,12 +51,15 @@ def time_run(eng: Engine, bid: int, runs: int, max_ms: float) -> float:
     return float(statistics.median(out))
 
 
-def collect(schemas, runs: int = 3, max_ms: float = 200.0, device: int = 0, log=None, jit: bool = False
-            ) -> List[Dict]:
+def collect(schemas, runs: int = 3, max_ms: float = 200.0, device: int = 0, log=None, jit: bool = True,
+            threads: int = 16) -> List[Dict]:
     """schemas: iterable of (schema, batch).  One record per schema with every
-    candidate's features and time, and the root rule's plan time.  Candidates
-    run the interpreted root scan unless jit (plan-time compilation of every
-    candidate would dominate a study of thousands of plans)."""
+    distinct candidate's features and time, and the root rule's plan and time.
+    Candidates run the root scan compiled for their plan (the product path):
+    the sources of all candidates of a schema are compiled first on `threads`
+    host threads (lmf_plan_precompile), then each candidate is planned and
+    timed.  Candidates that plan to the same thing (a key-level request that
+    falls back to the row-level form, say) are timed once."""
     import torch
     recs = []
     for si, (sch, batch) in enumerate(schemas):
@@ -65,29 +68,41 @@ def collect(schemas, runs: int = 3, max_ms: float = 200.0, device: int = 0, log=
         eng = Engine(device)
         register_schema(eng, sch, tensors)
         bid = eng.declare_batch(batch)
-        cands, feats, ms = [], [], []
+        cands, feats, ms, seen = [], [], [], set()
         flags = 0 if jit else LMF_PLAN_NO_JIT
         base = lmf_plan_opts(LMF_PREC_SPLIT_BF16, LMF_BATCH_GRAPH, 0, 0, 0, 0, 0, flags)
+        t0 = time.time()
+        if jit:
+            eng.plan_precompile(bid, base, threads)
+        t_compile = time.time() - t0
         for o in eng.plan_candidates(bid, base):
             try:
                 eng.plan_opts(bid, o)
             except LmfError:
                 continue
+            info = eng.plan_info(bid)
+            key = (info['root_rel'], info['precision'], info['key_level'], o.no_merge)
+            if key in seen:
+                continue
+            seen.add(key)
             feats.append(eng.plan_features(bid))
             ms.append(time_run(eng, bid, runs, max_ms))
             cands.append(_opts_tuple(o))
         h = lmf_plan_opts(LMF_PREC_SPLIT_BF16, LMF_BATCH_GRAPH, 0, 0, LMF_ROOT_HEURISTIC, 0, 0, flags)
         eng.plan_opts(bid, h)
         heur_ms = time_run(eng, bid, runs, max_ms)
-        heur_root = eng.plan_info(bid)['root_rel']
+        hi = eng.plan_info(bid)
         eng.close()
         del tensors
+        best = int(np.argmin(ms))
         rec = {'name': sch.meta.get('name', str(si)), 'cand': cands, 'feat': np.array(feats, np.float32),
-               'ms': np.array(ms, np.float64), 'heur_ms': heur_ms, 'heur_root': heur_root,
-               'n_aggs': len(batch)}
+               'ms': np.array(ms, np.float64), 'heur_ms': heur_ms, 'heur_root': hi['root_rel'],
+               'heur_key_level': hi['key_level'], 'n_aggs': len(batch), 'compile_s': t_compile,
+               'rows': [r.nrows for r in sch.relations], 'best': cands[best]}
         recs.append(rec)
         if log:
-            log(f'{si}: {rec["name"]} candidates={len(ms)} best={min(ms):.3f}ms heuristic={heur_ms:.3f}ms')
+            log(f'{si}: {rec["name"]} candidates={len(ms)} best={ms[best]:.3f}ms {cands[best]} '
+                f'rule={heur_ms:.3f}ms root={hi["root_rel"]} rows={rec["rows"]} compile={t_compile:.1f}s')
     return recs
 
 
@@ -168,20 +183,44 @@ def load(path: str, device: int = 0) -> Mlp:
     return model
 
 
+SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), 'costmodel_gb300')
+
+
+def load_shipped(device: int = 0):
+    """The checkpoint shipped with the package as (model, origin text), or
+    (None, reason) when it is missing or was trained on another feature set;
+    lmf_plan_learned with no model falls back to the root rule (Sec. 3.3)."""
+    from .lmf import LMF_PLAN_FEATURES
+    if not os.path.exists(SHIPPED + '.json') or not os.path.exists(SHIPPED + '.bin'):
+        return None, 'rule (Sec. 3.3): no cost-model checkpoint'
+    with open(SHIPPED + '.json') as f:
+        meta = json.load(f)
+    if meta.get('in_dim') != LMF_PLAN_FEATURES:
+        return None, f"rule (Sec. 3.3): checkpoint has {meta.get('in_dim')} features, the planner {LMF_PLAN_FEATURES}"
+    test = meta.get('test', {})
+    return load(SHIPPED, device), (f"learned (cost-model checkpoint, {meta.get('train', {}).get('schemas')} "
+                                   f"training schemas, held-out regret {test.get('learned_regret_mean')})")
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument('--schemas', type=int, default=500)
     ap.add_argument('--train', type=int, default=400)
-    ap.add_argument('--scale', type=float, default=0.01, help='fact-table size multiplier')
+    ap.add_argument('--scale', type=float, default=0.1, help='fact-table size multiplier')
     ap.add_argument('--steps', type=int, default=3000)
+    ap.add_argument('--threads', type=int, default=16, help='host threads compiling candidates')
     ap.add_argument('--out', default='')
+    ap.add_argument('--records', default='', help='write every record (JSON) here')
     args = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
     from workloads import config5_schema
     t0 = time.time()
     gen = (config5_schema(i, n_scale=args.scale) for i in range(args.schemas))
-    recs = collect(gen, log=lambda s: print(s, file=sys.stderr, flush=True))
+    recs = collect(gen, threads=args.threads, log=lambda s: print(s, file=sys.stderr, flush=True))
+    if args.records:
+        with open(args.records, 'w') as f:
+            json.dump([{k: (v.tolist() if isinstance(v, np.ndarray) else v) for k, v in r.items()} for r in recs], f)
     t1 = time.time()
     tr, te = recs[:args.train], recs[args.train:]
     model, losses = train(tr, steps=args.steps)

@@ -167,6 +167,10 @@ struct Plan {
   std::vector<CvMeanItem> cv_mean_items;
   std::vector<OutItem> out_items;
   int rv_item_cells = 0, cv_pair_cells = 0;
+  // category indexes of the COUNT tables read off category views
+  std::vector<CatIndex> cat_idx;
+  size_t cat_idx_off = 0;
+  int64_t cat_idx_maxK = 0;
   bool rv_wide = false;          // some reverse-view task is too wide for a block's table
   void* aux = nullptr;
   size_t aux_rv = 0, aux_cvp = 0, aux_cvm = 0, aux_out = 0;
@@ -184,6 +188,8 @@ struct Plan {
   std::unique_ptr<GramTcPlan> tc;
   // root scan compiled for this plan (null: the interpreted kernel)
   cudaKernel_t jit_plain = nullptr, jit_tc = nullptr, jit_lean = nullptr;
+  bool dry = false;             // built for its features only: not runnable
+  double run_log2 = 0;          // mean over probe groups of log2(rows per run of equal keys)
   // results
   int64_t n_i64 = 0, n_f64 = 0;
   size_t res_i64_off = 0, res_f64_off = 0;
@@ -242,6 +248,10 @@ struct lmf_ctx {
   int root = -1;
   std::vector<std::unique_ptr<BatchH>> batches;
   std::string err;
+  // dry planning (plan choice): plans are built for their features only, the
+  // plan-time compile is skipped and its sources are collected here instead
+  bool dry = false;
+  std::vector<std::pair<std::string, const char*>> dry_sources;
 };
 
 namespace {
@@ -1078,6 +1088,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
                                 c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     for (int q = 0; q < rp.n_grp; ++q) {
+      P->run_log2 += std::log2((double)Root.nrows / (double)(changes[q] + 1)) / rp.n_grp;
       has_runs[q] = (int64_t)(changes[q] + 1) * 4 <= Root.nrows;
       if (P->unique_all && Root.nrows >= 2 * kResRun && (int64_t)(changes[q] + 1) * kResRun <= Root.nrows &&
           (res_grp < 0 || changes[q] < changes[res_grp]))
@@ -1129,8 +1140,10 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     if (gp.direct && cls[a].mono.empty() && ag.gb.size() == 2 && P->unique_all) {
       // a COUNT table over two categories of different keys (or a key and the
       // root): read it off a view keyed by one of the keys that keeps the other
-      // category; the resident key if it is one of them, else the key with
-      // fewer values (smaller view)
+      // category; the resident key if it is one of them (its counters live in
+      // shared memory), else the key with fewer values (smaller views, and
+      // the grouped sums of the other key's means by this key's categories
+      // can read them)
       const int g0 = P->catword.at(ag.gb[0]).first, g1 = P->catword.at(ag.gb[1]).first;
       int x = -1;
       if (g0 >= 0 && (g0 == res_grp || g1 < 0)) x = 0;
@@ -1205,8 +1218,11 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
 
   // ---- key-level form: where every Gram block with a view mean comes from.
   // (x, m_g): the root feature x as a slot of g's reverse view; (m_g, m_h):
-  // the carrier's view holds the other group's mean (the carrier is the
-  // resident key, else the key with fewer changes, else with fewer keys);
+  // the carrier's view holds the other group's means (the carrier is the
+  // group whose view adds fewer reductions: a slot of the resident key's view
+  // costs nothing per row, one of a view summed in runs one reduction per
+  // run, one of a view reduced row by row 8 of the 32 bytes of a sector per
+  // row; ties: the resident key, the key with fewer changes, fewer keys);
   // (1, x): the root feature's sum from the view with the fewest keys; (m_g,
   // m_g) and (1, m_g): GroupGram over g's key counts; (x, x): the row Gram.
   struct LeanPair {
@@ -1224,7 +1240,38 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     auto rank = [&](int q) {
       return std::make_tuple(q == res_grp ? 0 : 1, changes[q], P->groups[RR.groups[q]].K, q);
     };
-    auto carrier = [&](int g, int h) { return rank(g) < rank(h) ? g : h; };
+    auto slot_cost = [&](int q) -> double {
+      if (q == res_grp) return 0.0;
+      return has_runs[q] ? (double)(changes[q] + 1) : (double)Root.nrows / 4.0;
+    };
+    // per pair of groups: the means of each that some (m_g, m_h) product needs
+    std::map<std::pair<int, int>, std::pair<std::set<int>, std::set<int>>> cross_means;
+    // means a view gets anyway: grouped sums of another group's mean by one
+    // of its categories that no category view answers (resolved below)
+    std::vector<std::set<int>> pre_slot(rp.n_grp);
+    for (size_t a : deferred) {
+      const std::string& f = cls[a].mono[0];
+      const int h = P->feat_group.at(f);
+      if (B.aggs[a].gb.size() == 1 && cv_index.count({h, P->rowcat.at(B.aggs[a].gb[0])})) continue;
+      pre_slot[gplan[a].grp].insert(P->zidx.at(f));
+    }
+    auto carrier = [&](int g, int h) {
+      const auto key = std::make_pair(std::min(g, h), std::max(g, h));
+      auto it = cross_means.find(key);
+      if (it != cross_means.end()) {
+        // carrying in the lower group adds the higher group's means to its
+        // view, those it does not hold anyway
+        auto added = [&](int q, const std::set<int>& zs) {
+          double n = 0;
+          for (int z : zs) n += pre_slot[q].count(z) ? 0.0 : 1.0;
+          return n;
+        };
+        const double c_lo = slot_cost(key.first) * added(key.first, it->second.second);
+        const double c_hi = slot_cost(key.second) * added(key.second, it->second.first);
+        if (c_lo != c_hi) return c_lo < c_hi ? key.first : key.second;
+      }
+      return rank(g) < rank(h) ? g : h;
+    };
     auto add_slot = [&](int q, int z) {
       auto& sl = rv_slots[q];
       auto it = std::find(sl.begin(), sl.end(), z);
@@ -1237,6 +1284,13 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       int j = P->zidx.at(cls[a].mono.back());
       if (i > j) std::swap(i, j);
       need.insert({i, j});
+    }
+    for (auto& ij : need) {
+      const int gi = zgroup(ij.first), gj = zgroup(ij.second);
+      if (ij.first == 0 || gi < 0 || gj < 0 || gi == gj) continue;
+      auto& e = cross_means[{std::min(gi, gj), std::max(gi, gj)}];
+      (gi < gj ? e.first : e.second).insert(ij.first);
+      (gi < gj ? e.second : e.first).insert(ij.second);
     }
     int sum_q = 0;
     for (int q = 1; q < rp.n_grp; ++q)
@@ -1339,6 +1393,18 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   for (size_t a = 0; a < B.aggs.size(); ++a)
     if (cls[a].kind == 1) gplan[a].out_off = A.take((size_t)gplan[a].cells * 8);
   for (auto& v : cvs) v.off = A.take((size_t)P->groups[RR.groups[v.grp]].K * v.dom * 4 + 16);
+  // the keys of each (keying group, row category of a) listed by a, for the
+  // COUNT tables read off category views: counters in the zeroed region
+  struct CatIdxPlan { int grp, aword, dom; size_t cnt_off, start_off, perm_off; };
+  std::vector<CatIdxPlan> cidx;
+  std::map<std::pair<int, int>, int> cidx_of;
+  for (size_t a = 0; a < B.aggs.size(); ++a) {
+    if (cls[a].kind != 1 || gplan[a].cv < 0 || gplan[a].cv_mode != 0) continue;
+    const auto key = std::make_pair(cvs[gplan[a].cv].grp, gplan[a].cv_aword);
+    if (cidx_of.count(key)) continue;
+    cidx_of[key] = (int)cidx.size();
+    cidx.push_back({key.first, key.second, gplan[a].cv_doma, A.take((size_t)(gplan[a].cv_doma + 1) * 4), 0, 0});
+  }
   // omega accumulators of fanning-out root children
   std::vector<std::pair<int, size_t>> omega;  // child relation, offset
   for (int q = 0; q < rp.n_grp; ++q)
@@ -1379,6 +1445,11 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   if (P->tree) tree_alloc_zeroed(P->tree.get(), Root.nrows, [&](size_t n) { return A.take(n); });
   P->zero_off = zero_begin;
   P->zero_len = A.take(0) - zero_begin;
+  for (auto& ci : cidx) {
+    ci.start_off = A.take((size_t)(ci.dom + 1) * 4);
+    ci.perm_off = A.take((size_t)P->groups[RR.groups[ci.grp]].K * 4 + 4);
+  }
+  P->cat_idx_off = A.take(sizeof(CatIndex) * (cidx.size() + 1));
   // within-key scatter of fanning-out views: fully rewritten by every run
   for (int r : P->post) {
     RelPlan& cp = P->rp[r];
@@ -1787,7 +1858,8 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       t.mode = gp.cv_mode;
       t.mu_word = gp.cv_muword;
       t.scale = (float)gp.scale;
-      t.fix_idx = -1;  // count x mean: one rounding of the exact product per cell (FP64)
+      t.fix_idx = -1;  // count x mean: one rounding of the exact product per cell
+      t.cat_idx = gp.cv_mode == 0 ? cidx_of.at({cvs[gp.cv].grp, gp.cv_aword}) : -1;
       P->cv_tasks.push_back(t);
       const CvPlan& v = cvs[gp.cv];
       P->cv_max_cells = std::max<int64_t>(P->cv_max_cells, (int64_t)P->groups[RR.groups[v.grp]].K * v.dom);
@@ -1859,9 +1931,8 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   group_by_view(P->cv_tasks, (int)cvs.size(), [](const CatViewTask& t) { return t.view; }, &P->cv_ranges);
   // work items of the key-level tasks: reverse-view tasks in groups that share
   // one shared-memory table per block (kRvTabCells int64), over key chunks;
-  // COUNT tables by blocks of rows (kCvTabCells counters); SUM(m) by b tables
-  // over key chunks
-  constexpr int kRvTabCells = 5120, kCvTabCells = 12288;
+  // COUNT and SUM(m) by b tables read off category views (below)
+  constexpr int kRvTabCells = 5120;
   {
     for (int r = 0; r < rp.n_rv; ++r) {
       const int t0 = P->rv_ranges.begin[r], t1 = P->rv_ranges.begin[r + 1];
@@ -1891,21 +1962,19 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       }
       close(t1);
     }
+    // COUNT tables: per task, chunks of 1024 positions of its category index
+    // (keys grouped by a) x 256 view cells b
     for (size_t t = 0; t < P->cv_tasks.size(); ++t) {
       const CatViewTask& T = P->cv_tasks[t];
       if (T.mode != 0) continue;
       const int db = cvs[T.view].dom;
-      const int rows = std::max(1, std::min(T.dom_a, kCvTabCells / db));
       const int64_t K = rp.grp[cvs[T.view].grp].K;
-      // about 16 blocks per table: row ranges, then key ranges while there are few rows
-      const int n_rr = (T.dom_a + rows - 1) / rows;
-      const int64_t n_kc = std::max<int64_t>(1, std::min<int64_t>((16 + n_rr - 1) / n_rr, (K + 255) / 256));
-      const int64_t ch = (K + n_kc - 1) / n_kc;
-      for (int a0 = 0; a0 < T.dom_a; a0 += rows)
-        for (int64_t k0 = 0; k0 < K; k0 += ch)
-          P->cv_pair_items.push_back(CvPairItem{(int)t, a0, std::min(rows, T.dom_a - a0), 0, k0, std::min(K, k0 + ch)});
-      P->cv_pair_cells = std::max(P->cv_pair_cells, rows * db);
+      for (int64_t p0 = 0; p0 < K; p0 += 1024)
+        for (int b0 = 0; b0 < db; b0 += 256)
+          P->cv_pair_items.push_back(CvPairItem{(int)t, b0, 0, 0, p0, std::min(K, p0 + 1024)});
     }
+    // SUM(m) by b tables: per view, its mean tasks in groups of kCvMeanTasks,
+    // chunks of 512 keys x 256 view cells b
     for (int v = 0; v < (int)cvs.size(); ++v) {
       int m0 = -1, m1 = -1;
       for (int t = P->cv_ranges.begin[v]; t < P->cv_ranges.begin[v + 1]; ++t)
@@ -1915,10 +1984,10 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
         }
       if (m0 < 0) continue;
       const int64_t K = rp.grp[cvs[v].grp].K;
-      const int64_t ch = 256;  // keys per block, 32 per warp
-      for (int t = m0; t < m1; ++t)
-        for (int64_t k0 = 0; k0 < K; k0 += ch)
-          P->cv_mean_items.push_back(CvMeanItem{v, t, t + 1, 0, k0, std::min(K, k0 + ch)});
+      for (int t = m0; t < m1; t += kCvMeanTasks)
+        for (int64_t k0 = 0; k0 < K; k0 += 512)
+          for (int b0 = 0; b0 < cvs[v].dom; b0 += 256)
+            P->cv_mean_items.push_back(CvMeanItem{v, t, std::min(m1, t + kCvMeanTasks), b0, k0, std::min(K, k0 + 512)});
     }
   }
   P->rv_tasks = tasks;
@@ -2006,6 +2075,20 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   }
   P->corr = corr;
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->rvtask_off, tasks.data(), sizeof(RvTask) * tasks.size(), cudaMemcpyHostToDevice));
+  for (auto& ci : cidx) {
+    CatIndex I{};
+    I.grp = ci.grp;
+    I.a_word = ci.aword;
+    I.dom = ci.dom;
+    I.cnt = P->at<uint32_t>(ci.cnt_off);
+    I.start = P->at<uint32_t>(ci.start_off);
+    I.perm = P->at<int32_t>(ci.perm_off);
+    P->cat_idx.push_back(I);
+    P->cat_idx_maxK = std::max<int64_t>(P->cat_idx_maxK, rp.grp[ci.grp].K);
+  }
+  if (!P->cat_idx.empty())
+    CUDA_TRY(c, cudaMemcpy(P->arena.base + P->cat_idx_off, P->cat_idx.data(), sizeof(CatIndex) * P->cat_idx.size(),
+                           cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->cvtask_off, P->cv_tasks.data(), sizeof(CatViewTask) * P->cv_tasks.size(),
                          cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(P->arena.base + P->ggram_off, P->ggram.data(), sizeof(GroupGram) * P->ggram.size(),
@@ -2043,7 +2126,17 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   // the compilation step (Sec. 1.2, App. C): the plain root scan with this
   // plan's layout as constants; the interpreted kernel stays when NVRTC is
   // missing or the compile fails (same arithmetic, same results)
-  if (use_tc && !(P->opts.flags & LMF_PLAN_NO_JIT) && Root.nrows > 0 && jit_available()) {
+  P->dry = c->dry;
+  if (c->dry) {  // plan choice: collect the sources the compile step would build
+    if (use_tc && !(P->opts.flags & LMF_PLAN_NO_JIT) && Root.nrows > 0 && jit_available())
+      c->dry_sources.emplace_back(jit_tc_source(rp, direct), "lmf_root_tc_jit");
+    if (P->lean) {
+      const int lcps = (int)std::min<int64_t>(3, std::max<int64_t>(1, (int64_t)P->grid / std::max(1, c->num_sms)));
+      c->dry_sources.emplace_back(jit_lean_source(rp, direct, lcps), "lmf_root_lean_jit");
+    }
+    if (!use_tc && !P->lean && !(P->opts.flags & LMF_PLAN_NO_JIT) && Root.nrows > 0 && jit_available())
+      c->dry_sources.emplace_back(jit_plain_source(rp, P->mp, direct, jit3 ? 3 : 1), "lmf_root_plain_jit");
+  } else if (use_tc && !(P->opts.flags & LMF_PLAN_NO_JIT) && Root.nrows > 0 && jit_available()) {
     std::string log;
     cudaKernel_t k = nullptr;
     if (jit_kernel(jit_tc_source(rp, direct), "lmf_root_tc_jit", &k, &log)) {
@@ -2054,7 +2147,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       std::fprintf(stderr, "lmf: plan-time compile failed, interpreted root scan kept: %.400s\n", log.c_str());
     }
   }
-  if (P->lean) {  // the key-level scan exists only compiled: without it, plan the row-level form
+  if (P->lean && !c->dry) {  // the key-level scan exists only compiled: without it, plan the row-level form
     std::string log;
     cudaKernel_t k = nullptr;
     const int lcps = (int)std::min<int64_t>(3, std::max<int64_t>(1, (int64_t)P->grid / std::max(1, c->num_sms)));
@@ -2070,7 +2163,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
                                      static_cast<int>(P->smem)));
     P->jit_lean = k;
   }
-  if (!use_tc && !P->lean && !(P->opts.flags & LMF_PLAN_NO_JIT) && Root.nrows > 0 && jit_available()) {
+  if (!c->dry && !use_tc && !P->lean && !(P->opts.flags & LMF_PLAN_NO_JIT) && Root.nrows > 0 && jit_available()) {
     std::string log;
     cudaKernel_t k = nullptr;
     if (jit_kernel(jit_plain_source(rp, P->mp, direct, jit3 ? 3 : 1), "lmf_root_plain_jit", &k, &log)) {
@@ -2268,8 +2361,12 @@ lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = null
     ++nk;
   }
   if (!P->cv_pair_items.empty()) {
-    CUDA_TRY(c, launch_cv_pairs(P->at<CatViewTask>(P->cvtask_off), reinterpret_cast<const CvPairItem*>(aux + P->aux_cvp),
-                                (int)P->cv_pair_items.size(), P->cv_pair_cells, P->rootp, s));
+    CUDA_TRY(c, launch_cat_index(P->at<CatIndex>(P->cat_idx_off), (int)P->cat_idx.size(), P->cat_idx_maxK, P->rootp,
+                                 s));
+    nk += 3;
+    CUDA_TRY(c, launch_cv_pairs(P->at<CatViewTask>(P->cvtask_off), P->at<CatIndex>(P->cat_idx_off),
+                                reinterpret_cast<const CvPairItem*>(aux + P->aux_cvp), (int)P->cv_pair_items.size(),
+                                P->rootp, s));
     ++nk;
   }
   if (!P->cv_mean_items.empty()) {
@@ -2347,6 +2444,7 @@ lmf_status lmf_run(lmf_ctx* c, int batch_id, void* cuda_stream) {
   BatchH& B = *c->batches[batch_id];
   Plan* P = B.plan.get();
   if (!P) return fail(c, LMF_ERR_STATE, "run before plan");
+  if (P->dry) return fail(c, LMF_ERR_STATE, "run of a plan built for plan choice only");
   cudaSetDevice(c->device);
   cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
   B.last_stream = s;
@@ -2380,6 +2478,7 @@ lmf_status lmf_run_profiled(lmf_ctx* c, int batch_id, void* cuda_stream, float* 
     return fail(c, LMF_ERR_ARG, "run_profiled: bad argument");
   BatchH& B = *c->batches[batch_id];
   if (!B.plan) return fail(c, LMF_ERR_STATE, "run before plan");
+  if (B.plan->dry) return fail(c, LMF_ERR_STATE, "run of a plan built for plan choice only");
   cudaSetDevice(c->device);
   cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
   B.last_stream = s;
@@ -2496,7 +2595,7 @@ lmf_status lmf_read_result(lmf_ctx* c, int batch_id, int agg, void* dst) {
 // plan choice: candidates, features, learned selection
 namespace {
 
-constexpr int kPlanFeatures = 24;
+constexpr int kPlanFeatures = 26;
 
 void plan_features(lmf_ctx* c, const Plan& P, float* f) {
   double total_rows = 0, max_rows = 1;
@@ -2531,7 +2630,7 @@ void plan_features(lmf_ctx* c, const Plan& P, float* f) {
       (float)P.grid / (float)std::max(1, c->num_sms), P.merge ? 1.f : 0.f,
       (double)c->rels[P.root].nrows >= max_rows ? 1.f : 0.f, (float)(std::log2(root_rows) - std::log2(max_rows)),
       (float)non_unique, (float)std::log2(general_work + 1), (float)slots, (float)P.direct.size(),
-      (float)std::log2((double)fanin + 1), P.tree ? 1.f : 0.f};
+      (float)std::log2((double)fanin + 1), P.tree ? 1.f : 0.f, P.lean ? 1.f : 0.f, (float)P.run_log2};
   std::memcpy(f, v, sizeof(v));
 }
 
@@ -2544,23 +2643,47 @@ std::vector<lmf_plan_opts> plan_candidates(lmf_ctx* c, const BatchH& B, const lm
   std::stable_sort(by_size.begin(), by_size.end(),
                    [&](int a, int b) { return c->rels[a].nrows > c->rels[b].nrows; });
   for (int r : by_size) {
-    if ((int)roots.size() >= 4) break;
+    if ((int)roots.size() >= 3) break;
     if (std::find(roots.begin(), roots.end(), r) == roots.end()) roots.push_back(r);
   }
+  // Gram forms: plain FP32 with key-level blocks, plain FP32 all at the row
+  // level, split bf16 on the tensor cores
+  struct Form { int prec, flags; };
+  const Form forms[] = {{LMF_PREC_PLAIN_FP32, 0}, {LMF_PREC_PLAIN_FP32, LMF_PLAN_ROW_GRAM},
+                        {LMF_PREC_SPLIT_BF16, 0}};
   std::vector<lmf_plan_opts> out;
   for (int r : roots)
-    for (int prec : {LMF_PREC_PLAIN_FP32, LMF_PREC_SPLIT_BF16})
-      for (int cps : {0, 1})
-        for (int nm : {0, 1}) {
-          lmf_plan_opts o = base;
-          o.root_mode = LMF_ROOT_EXPLICIT;
-          o.root_rel = r;
-          o.precision = prec;
-          o.ctas_per_sm = cps;
-          o.no_merge = nm;
-          out.push_back(o);
-        }
+    for (const Form& f : forms)
+      for (int nm : {0, 1}) {
+        lmf_plan_opts o = base;
+        o.root_mode = LMF_ROOT_EXPLICIT;
+        o.root_rel = r;
+        o.precision = f.prec;
+        o.flags = (base.flags & ~LMF_PLAN_ROW_GRAM) | f.flags;
+        o.no_merge = nm;
+        out.push_back(o);
+      }
   return out;
+}
+
+// plan every candidate dry (features, no compile) and return those that plan
+lmf_status dry_candidates(lmf_ctx* c, int batch_id, const std::vector<lmf_plan_opts>& cand,
+                          std::vector<lmf_plan_opts>* ok, std::vector<float>* feats) {
+  BatchH& B = *c->batches[batch_id];
+  c->dry = true;
+  c->dry_sources.clear();
+  for (const lmf_plan_opts& o : cand) {
+    if (lmf_plan(c, batch_id, &o) != LMF_OK) continue;
+    if (feats) {
+      float f[kPlanFeatures];
+      plan_features(c, *B.plan, f);
+      feats->insert(feats->end(), f, f + kPlanFeatures);
+    }
+    ok->push_back(o);
+  }
+  c->dry = false;
+  B.plan.reset();
+  return LMF_OK;
 }
 
 }  // namespace
@@ -2585,6 +2708,21 @@ lmf_status lmf_plan_candidates(lmf_ctx* c, int batch_id, const lmf_plan_opts* ba
   auto cand = plan_candidates(c, *c->batches[batch_id], b);
   *n = (int)cand.size();
   for (int i = 0; i < std::min<int>(max, (int)cand.size()) && out; ++i) out[i] = cand[i];
+  return LMF_OK;
+}
+
+lmf_status lmf_plan_precompile(lmf_ctx* c, int batch_id, const lmf_plan_opts* base, int threads, int* n_compiled) {
+  if (!c || batch_id < 0 || batch_id >= (int)c->batches.size() || threads < 0) return LMF_ERR_ARG;
+  if (!c->joined) return fail(c, LMF_ERR_STATE, "precompile before declare_join");
+  lmf_plan_opts b{};
+  if (base) b = *base;
+  auto cand = plan_candidates(c, *c->batches[batch_id], b);
+  std::vector<lmf_plan_opts> ok;
+  dry_candidates(c, batch_id, cand, &ok, nullptr);
+  auto jobs = std::move(c->dry_sources);
+  c->dry_sources.clear();
+  const int n = jit_kernels_parallel(jobs, threads > 0 ? threads : 8, c->device);
+  if (n_compiled) *n_compiled = n;
   return LMF_OK;
 }
 
@@ -2613,13 +2751,8 @@ lmf_status lmf_plan_learned(lmf_ctx* c, int batch_id, lmf_mlp* model, const lmf_
   auto cand = plan_candidates(c, B, b);
   std::vector<float> feats;
   std::vector<lmf_plan_opts> ok;
-  for (auto& o : cand) {
-    if (lmf_plan(c, batch_id, &o) != LMF_OK) continue;
-    float f[kPlanFeatures];
-    plan_features(c, *B.plan, f);
-    feats.insert(feats.end(), f, f + kPlanFeatures);
-    ok.push_back(o);
-  }
+  dry_candidates(c, batch_id, cand, &ok, &feats);
+  c->dry_sources.clear();
   if (ok.empty()) return fail(c, LMF_ERR_UNSUPPORTED, "no candidate plan evaluates this batch");
   float *dx = nullptr, *dy = nullptr;
   CUDA_TRY(c, cudaMalloc(&dx, feats.size() * 4));

@@ -202,6 +202,8 @@ struct CatViewTask {
   float scale;                       // mode 1: fixed-point scale of the output
   int32_t fix_idx;                   // mode 1: m's fixed-point image in the keying group's fix records
                                      // (count * image, exact integers), -1: rounded in FP64 per cell
+  int32_t cat_idx;                   // mode 0: the CatIndex of (keying group, a_word)
+  int32_t pad;
 };
 
 // Gram entries taken at the key level from a reverse view R keyed by probe
@@ -323,17 +325,31 @@ struct RvItem {
   int64_t k0, k1;
 };
 
-// one block of the COUNT tables read off category views: rows [a0, a0 +
-// rows) of task `task`'s table, counted in shared memory over all keys
+// the keys of a probe group listed by the value of one of their categories
+// (rebuilt every run from the group's records): cnt[v] keys carry value v,
+// perm[start[v] ..] are those keys (in no particular order), cnt[dom] the
+// number of keys with a category inside [0, dom)
+struct CatIndex {
+  int32_t grp, a_word, dom, pad;
+  uint32_t* cnt;                     // [dom + 1], zeroed every run
+  uint32_t* start;                   // [dom + 1]
+  int32_t* perm;                     // [K of grp]
+};
+
+// one block of a COUNT table read off a category view: the keys at positions
+// [p0, p1) of the task's category index (so runs of keys with one value a of
+// the table's row category), view cells b0 .. b0 + blockDim - 1 of each
 struct CvPairItem {
-  int32_t task, a0, rows, pad;
-  int64_t k0, k1;                    // keys of the view this block counts
+  int32_t task, b0, pad0, pad1;
+  int64_t p0, p1;
 };
 
 // one block of the SUM(m) grouped by b tables of a category view: the view's
-// mean tasks [t0, t1) over its keys [k0, k1)
+// mean tasks [t0, t1) (at most kCvMeanTasks) over its keys [k0, k1), view
+// cells b0 .. b0 + blockDim - 1
+constexpr int kCvMeanTasks = 16;
 struct CvMeanItem {
-  int32_t view, t0, t1, pad;
+  int32_t view, t0, t1, b0;
   int64_t k0, k1;
 };
 
@@ -374,7 +390,8 @@ cudaError_t launch_fix_means(const FixMeans& f, cudaStream_t s);
 // grouped launches of the key-level tasks (shared-memory tables per block)
 cudaError_t launch_rv_items(const RvTask* tasks, const RvItem* items, int n_items, int max_cells,
                             const RootParams& p, cudaStream_t s);
-cudaError_t launch_cv_pairs(const CatViewTask* tasks, const CvPairItem* items, int n_items, int max_cells,
+cudaError_t launch_cat_index(const CatIndex* idx, int n_idx, int64_t max_K, const RootParams& p, cudaStream_t s);
+cudaError_t launch_cv_pairs(const CatViewTask* tasks, const CatIndex* idx, const CvPairItem* items, int n_items,
                             const RootParams& p, cudaStream_t s);
 cudaError_t launch_cv_means(const CatViewTask* tasks, const CvMeanItem* items, int n_items, const RootParams& p,
                             cudaStream_t s);

@@ -6,11 +6,15 @@
 #include <nvrtc.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <functional>
 #include <map>
+#include <atomic>
 #include <mutex>
+#include <set>
+#include <thread>
 #include <sstream>
 
 // the device headers the generated source includes, as text (written by the
@@ -567,6 +571,13 @@ bool jit_kernel(const std::string& src, const char* name, cudaKernel_t* k, std::
       return true;
     }
   }
+  if (const char* dir = std::getenv("LMF_JIT_DUMP")) {  // keep the generated source for inspection
+    const std::string path = std::string(dir) + "/" + name + "_" + std::to_string(std::hash<std::string>{}(src)) + ".cu";
+    if (FILE* f = std::fopen(path.c_str(), "w")) {
+      std::fwrite(src.data(), 1, src.size(), f);
+      std::fclose(f);
+    }
+  }
   nvrtcProgram prog = nullptr;
   const int nh = static_cast<int>(sizeof(kJitHeaderNames) / sizeof(kJitHeaderNames[0]));
   if (n.create(&prog, src.c_str(), "lmf_root_plain_jit.cu", nh, kJitHeaderSrc, kJitHeaderNames) != NVRTC_SUCCESS) {
@@ -599,6 +610,36 @@ bool jit_kernel(const std::string& src, const char* name, cudaKernel_t* k, std::
   std::lock_guard<std::mutex> g(g_cache_mu);
   g_cache[key] = *k;
   return true;
+}
+
+int jit_kernels_parallel(const std::vector<std::pair<std::string, const char*>>& jobs, int threads, int device) {
+  // distinct jobs only: two threads compiling one source would both load it
+  std::vector<size_t> todo;
+  {
+    std::set<std::string> seen;
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    for (size_t i = 0; i < jobs.size(); ++i) {
+      const std::string key = std::string(jobs[i].second) + '\n' + jobs[i].first;
+      if (g_cache.count(key) || !seen.insert(key).second) continue;
+      todo.push_back(i);
+    }
+  }
+  std::atomic<size_t> next{0};
+  std::atomic<int> done{0};
+  auto work = [&]() {
+    cudaSetDevice(device);
+    for (size_t t; (t = next.fetch_add(1)) < todo.size();) {
+      cudaKernel_t k = nullptr;
+      std::string log;
+      if (jit_kernel(jobs[todo[t]].first, jobs[todo[t]].second, &k, &log)) done.fetch_add(1);
+    }
+  };
+  const int nt = std::max(1, std::min<int>(threads, static_cast<int>(todo.size())));
+  std::vector<std::thread> pool;
+  for (int i = 1; i < nt; ++i) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+  return done.load();
 }
 
 }  // namespace lmf

@@ -61,5 +61,8 @@ std::string jit_lean_source(const RootParams& rp, const std::vector<DirectAgg>& 
 // compiles src for sm_103a, or finds it in the process-wide cache of compiled
 // sources; on failure returns false with NVRTC's log in *log
 bool jit_kernel(const std::string& src, const char* name, cudaKernel_t* k, std::string* log);
+// compiles every (source, kernel name) job into that cache on up to `threads`
+// host threads (device `device` current in each); returns how many compiled
+int jit_kernels_parallel(const std::vector<std::pair<std::string, const char*>>& jobs, int threads, int device);
 
 }  // namespace lmf

@@ -11,6 +11,7 @@
 #include "lmf_root_plain.cuh"
 #include "lmf_rowpass.cuh"
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 
@@ -463,102 +464,174 @@ cudaError_t launch_rv_items(const RvTask* tasks, const RvItem* items, int n_item
   return cudaGetLastError();
 }
 
-// COUNT tables (a, b) read off category views, one block per range of rows a
-// of one table and range of the view's keys: the block lists the keys whose
-// a falls in its rows, adds their view rows V[k][.] into shared counters (a
-// warp per key, lanes over b) and adds its counters to the table
-__global__ void __launch_bounds__(256) k_cv_pairs(const CatViewTask* tasks, const CvPairItem* items,
-                                                  const __grid_constant__ RootParams p) {
-  extern __shared__ uint32_t cnt[];  // [rows][dom_b]
-  __shared__ int32_t keys[256];
-  __shared__ int32_t nk;
-  const CvPairItem it = items[blockIdx.x];
-  const CatViewTask T = tasks[it.task];
-  const CatView& C = p.cv[T.view];
-  const GroupDesc& G = p.grp[C.grp];
-  const int db = C.dom;
-  const int n = it.rows * db;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) cnt[i] = 0u;
-  for (int64_t k0 = it.k0; k0 < it.k1; k0 += blockDim.x) {
-    if (threadIdx.x == 0) nk = 0;
-    __syncthreads();
-    const int64_t k = k0 + threadIdx.x;
-    if (k < it.k1) {
-      const int a = static_cast<int32_t>(G.rec[k * G.stride + T.a_word]) - it.a0;
-      if (a >= 0 && a < it.rows) keys[atomicAdd(&nk, 1)] = static_cast<int32_t>(k);
-    }
-    __syncthreads();
-    const int m = nk;
-    for (int j = warp; j < m; j += nwarp) {  // one listed key per warp, lanes over b
-      const int64_t kk = keys[j];
-      const int a = static_cast<int32_t>(G.rec[kk * G.stride + T.a_word]) - it.a0;
-      const uint32_t* v = C.V + kk * db;
-      for (int b = lane; b < db; b += 32) {
-        const uint32_t x = v[b];
-        if (x) atomicAdd(&cnt[a * db + b], x);
-      }
-    }
-    __syncthreads();  // the list is read by every warp before it is refilled
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const uint32_t x = cnt[i];
-    if (!x) continue;
-    const int a = it.a0 + i / db, b = i % db;
-    const int64_t cell = T.a_first ? static_cast<int64_t>(a) * db + b : static_cast<int64_t>(b) * T.dom_a + a;
-    atomicAdd(reinterpret_cast<unsigned long long*>(T.out + cell), static_cast<unsigned long long>(x));
+// Category indexes: the keys of a probe group listed by one category value,
+// rebuilt every run from the records (count, exclusive scan, scatter), one
+// index per blockIdx.y.
+__device__ __forceinline__ int cat_of(const GroupDesc& G, const CatIndex& I, int64_t k) {
+  const int32_t v = static_cast<int32_t>(G.rec[k * G.stride + I.a_word]);
+  return (v >= 0 && v < I.dom) ? v : -1;
+}
+
+__global__ void k_cat_hist(const CatIndex* idx, const __grid_constant__ RootParams p) {
+  const CatIndex I = idx[blockIdx.y];
+  const GroupDesc& G = p.grp[I.grp];
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < G.K;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int v = cat_of(G, I, k);
+    if (v >= 0) atomicAdd(I.cnt + v, 1u);
   }
 }
 
-cudaError_t launch_cv_pairs(const CatViewTask* tasks, const CvPairItem* items, int n_items, int max_cells,
+// one block per index: exclusive scan of cnt into start, the total to
+// cnt[dom] and start[dom]
+__global__ void __launch_bounds__(1024) k_cat_scan(const CatIndex* idx) {
+  const CatIndex I = idx[blockIdx.x];
+  __shared__ uint32_t part[1024];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0u;
+  __syncthreads();
+  for (int base = 0; base < I.dom; base += blockDim.x) {
+    const int v = base + threadIdx.x;
+    const uint32_t x = v < I.dom ? I.cnt[v] : 0u;
+    part[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = 1; o < static_cast<int>(blockDim.x); o <<= 1) {  // inclusive Hillis-Steele scan
+      const uint32_t y = threadIdx.x >= static_cast<unsigned>(o) ? part[threadIdx.x - o] : 0u;
+      __syncthreads();
+      part[threadIdx.x] += y;
+      __syncthreads();
+    }
+    if (v < I.dom) I.start[v] = carry + part[threadIdx.x] - x;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += part[threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    I.start[I.dom] = carry;
+    I.cnt[I.dom] = carry;
+  }
+}
+
+// scatter: start[] ends as the end of each value's list
+__global__ void k_cat_scatter(const CatIndex* idx, const __grid_constant__ RootParams p) {
+  const CatIndex I = idx[blockIdx.y];
+  const GroupDesc& G = p.grp[I.grp];
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < G.K;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int v = cat_of(G, I, k);
+    if (v >= 0) I.perm[atomicAdd(I.start + v, 1u)] = static_cast<int32_t>(k);
+  }
+}
+
+cudaError_t launch_cat_index(const CatIndex* idx, int n_idx, int64_t max_K, const RootParams& p, cudaStream_t s) {
+  if (n_idx <= 0) return cudaSuccess;
+  const dim3 g(static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((max_K + 255) / 256, 1024))),
+               static_cast<unsigned>(n_idx));
+  k_cat_hist<<<g, 256, 0, s>>>(idx, p);
+  k_cat_scan<<<n_idx, 1024, 0, s>>>(idx);
+  k_cat_scatter<<<g, 256, 0, s>>>(idx, p);
+  return cudaGetLastError();
+}
+
+// COUNT table (a, b) read off category view V keyed by the task's group:
+// T[a][b] = sum over the keys k with category a of V[k][b].  A block walks
+// the positions [p0, p1) of the category index -- keys grouped by a -- with
+// its threads on view cells b (coalesced row reads), summing in registers
+// and adding to the table when a changes.  No counter sees more than one
+// addition per block and value a.
+__global__ void __launch_bounds__(256) k_cv_pairs(const CatViewTask* tasks, const CatIndex* idx,
+                                                  const CvPairItem* items, const __grid_constant__ RootParams p) {
+  __shared__ int32_t keys[256];
+  __shared__ int32_t cats[256];
+  const CvPairItem it = items[blockIdx.x];
+  const CatViewTask T = tasks[it.task];
+  const CatIndex I = idx[T.cat_idx];
+  const CatView& C = p.cv[T.view];
+  const GroupDesc& G = p.grp[C.grp];
+  const int db = C.dom;
+  const int64_t total = I.cnt[I.dom];
+  const int64_t p1 = it.p1 < total ? it.p1 : total;
+  const int b = it.b0 + static_cast<int>(threadIdx.x);
+  const bool on = b < db;
+  for (int64_t q0 = it.p0; q0 < p1; q0 += 256) {
+    const int n = static_cast<int>(p1 - q0 < 256 ? p1 - q0 : 256);
+    __syncthreads();
+    if (static_cast<int>(threadIdx.x) < n) {
+      const int32_t k = I.perm[q0 + threadIdx.x];
+      keys[threadIdx.x] = k;
+      cats[threadIdx.x] = cat_of(G, I, k);
+    }
+    __syncthreads();
+    uint32_t acc = 0u;
+    int a_cur = cats[0];
+    for (int j = 0; j < n; ++j) {
+      const int a = cats[j];
+      if (a != a_cur) {
+        if (on && acc) {
+          const int64_t cell = T.a_first ? static_cast<int64_t>(a_cur) * db + b : static_cast<int64_t>(b) * T.dom_a + a_cur;
+          atomicAdd(reinterpret_cast<unsigned long long*>(T.out + cell), static_cast<unsigned long long>(acc));
+        }
+        acc = 0u;
+        a_cur = a;
+      }
+      if (on) acc += C.V[static_cast<int64_t>(keys[j]) * db + b];
+    }
+    if (on && acc) {
+      const int64_t cell = T.a_first ? static_cast<int64_t>(a_cur) * db + b : static_cast<int64_t>(b) * T.dom_a + a_cur;
+      atomicAdd(reinterpret_cast<unsigned long long*>(T.out + cell), static_cast<unsigned long long>(acc));
+    }
+  }
+}
+
+cudaError_t launch_cv_pairs(const CatViewTask* tasks, const CatIndex* idx, const CvPairItem* items, int n_items,
                             const RootParams& p, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  const int sm = max_cells * 4;
-  cudaError_t e = cudaFuncSetAttribute(k_cv_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e != cudaSuccess) return e;
-  k_cv_pairs<<<n_items, 256, sm, s>>>(tasks, items, p);
+  k_cv_pairs<<<n_items, 256, 0, s>>>(tasks, idx, items, p);
   return cudaGetLastError();
 }
 
 // SUM of a keying-group mean grouped by b, read off a category view: one block
-// per (task, range of keys); a warp takes a key at a time, its lanes the
-// cells b of the key's view row (coalesced), each lane keeping its cells'
-// sums in registers; the warps' sums meet in shared memory and one value per
-// (block, b) goes to the output.  Every cell's count x mean is one exact
-// integer rounding (cnt_times).
-constexpr int kCvMeanRegs = 16;  // cells b per lane held in registers: db <= 512 per pass
+// per (view, up to kCvMeanTasks of its mean tasks, range of keys, range of
+// cells b); each thread takes one cell b and walks the keys, reading the
+// count once for all the tasks and adding count x mean for each as one exact
+// integer rounding (cnt_times); one addition per (block, task, b) at the end.
 __global__ void __launch_bounds__(256) k_cv_means(const CatViewTask* tasks, const CvMeanItem* items,
                                                   const __grid_constant__ RootParams p) {
-  __shared__ long long part[8][32 * kCvMeanRegs];
+  __shared__ float mu[kCvMeanTasks][64];
+  __shared__ float sc[kCvMeanTasks];
   const CvMeanItem it = items[blockIdx.x];
-  const CatViewTask T = tasks[it.t0];
   const CatView& C = p.cv[it.view];
   const GroupDesc& G = p.grp[C.grp];
   const int db = C.dom;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int b0 = 0; b0 < db; b0 += 32 * kCvMeanRegs) {
-    long long acc[kCvMeanRegs];
+  const int nt = it.t1 - it.t0;
+  const int b = it.b0 + static_cast<int>(threadIdx.x);
+  const bool on = b < db;
+  if (static_cast<int>(threadIdx.x) < nt) sc[threadIdx.x] = tasks[it.t0 + threadIdx.x].scale;
+  long long acc[kCvMeanTasks];
 #pragma unroll
-    for (int r = 0; r < kCvMeanRegs; ++r) acc[r] = 0;
-    for (int64_t k = it.k0 + warp; k < it.k1; k += 8) {
-      const float m = __uint_as_float(G.rec[k * G.stride + T.mu_word]);
-      const uint32_t* v = C.V + k * db + b0;
-#pragma unroll
-      for (int r = 0; r < kCvMeanRegs; ++r) {
-        const int b = lane + 32 * r;
-        if (b0 + b < db) acc[r] += cnt_times(v[b], m, T.scale);
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < kCvMeanRegs; ++r) part[warp][lane + 32 * r] = acc[r];
+  for (int t = 0; t < kCvMeanTasks; ++t) acc[t] = 0;
+  for (int64_t k0 = it.k0; k0 < it.k1; k0 += 64) {
+    const int n = static_cast<int>(it.k1 - k0 < 64 ? it.k1 - k0 : 64);
     __syncthreads();
-    for (int b = threadIdx.x; b < 32 * kCvMeanRegs && b0 + b < db; b += blockDim.x) {
-      long long s = 0;
-      for (int w = 0; w < 8; ++w) s += part[w][b];
-      if (s) atomicAdd(reinterpret_cast<unsigned long long*>(T.out + b0 + b), static_cast<unsigned long long>(s));
+    for (int e = threadIdx.x; e < nt * 64; e += blockDim.x) {
+      const int t = e / 64, j = e % 64;
+      if (j < n) mu[t][j] = __uint_as_float(G.rec[(k0 + j) * G.stride + tasks[it.t0 + t].mu_word]);
     }
     __syncthreads();
+    if (!on) continue;
+    for (int j = 0; j < n; ++j) {
+      const uint32_t c = C.V[(k0 + j) * db + b];
+      if (c == 0u) continue;
+#pragma unroll
+      for (int t = 0; t < kCvMeanTasks; ++t)
+        if (t < nt) acc[t] += cnt_times(c, mu[t][j], sc[t]);
+    }
   }
+  if (!on) return;
+#pragma unroll
+  for (int t = 0; t < kCvMeanTasks; ++t)
+    if (t < nt && acc[t] != 0)
+      atomicAdd(reinterpret_cast<unsigned long long*>(tasks[it.t0 + t].out + b), static_cast<unsigned long long>(acc[t]));
 }
 
 cudaError_t launch_cv_means(const CatViewTask* tasks, const CvMeanItem* items, int n_items, const RootParams& p,

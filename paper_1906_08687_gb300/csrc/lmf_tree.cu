@@ -15,18 +15,19 @@
 // keeps x <= t exact for FP32 data.
 //
 // Kernels:
-//   k_tree_fused persistent: CTAs own a slice (node range x split range) of the
-//                histogram in shared memory and pull row chunks from a
-//                per-slice work queue; for every row they build z from the
-//                views, find the row's node in every group of mutually
-//                exclusive nodes by descending a decision tree over the nodes'
-//                predicates, and -- only for a node of the slice -- compute its
-//                fixed-point moments and its bucket for every split attribute
-//                of the slice (binary search over the thresholds, held in
-//                shared memory), accumulating exact 64-bit sums as two 32-bit
-//                shared-memory atomics with carry; one flush to global int64.
-//                Nothing per row leaves the CTA: a slice recomputes the row
-//                pass instead of reading it back from memory.
+//   k_tree_fused persistent, one pass over the root: for every row it builds z
+//                from the views, finds the row's node in every group of
+//                mutually exclusive nodes by descending a decision tree over
+//                the nodes' predicates, computes the row's fixed-point moments
+//                and its bucket for every split attribute (binary search over
+//                the thresholds, held in shared memory), and adds the moments
+//                to the histogram in global memory with 64-bit integer
+//                reductions (exact, order-free).  When every active row of a
+//                warp falls into one cell -- the rule for a split on a
+//                dimension attribute over a root sorted on its join keys --
+//                the warp sums its moments first (three 32-bit warp
+//                reductions per 64-bit value) and one lane issues the
+//                reduction.  Nothing per row leaves the SM.
 //   k_tree_out   every aggregate as a prefix / suffix sum over the buckets.
 #include "lmf_tree.h"
 #include "lmf_rowpass.cuh"
@@ -72,7 +73,6 @@ struct TreeDev {
   const struct TreeDt* dt;
   const int32_t* dcand;
   long long* H;                // [n_nodes][n_split][max_bins][n_mom]
-  uint32_t* queue;             // [n_slices]
   int64_t N;
   uint32_t* status;
 };
@@ -85,7 +85,7 @@ struct TreeDt {
 };
 
 struct TreeShape {
-  int split_w, node_w, cps, chunk;
+  int cps;                     // CTAs per SM of the persistent pass
 };
 
 struct TreePlanImpl {
@@ -107,7 +107,7 @@ struct TreePlanImpl {
   int max_bins = 1;
   int mp = 16;
   // device
-  size_t H_off = 0, queue_off = 0;
+  size_t H_off = 0;
   size_t tab_off = 0, tab_bytes = 0, outs_off = 0;
   TreeDev dev{};
   const TreeOut* d_outs = nullptr;
@@ -115,9 +115,8 @@ struct TreePlanImpl {
   long long* res_i64 = nullptr;
   double* res_f64 = nullptr;
   int num_sms = 0;
-  TreeShape shape{1, 1, 1, 8192};
+  TreeShape shape{2};
   bool tuned = false;
-  int max_slices = 1;
 };
 
 TreePlan::~TreePlan() { delete impl; }
@@ -187,14 +186,6 @@ int build_dt(const std::vector<std::vector<TreePred>>& nodes, const std::vector<
   const int r = build_dt(nodes, R, depth + 1, dt, cand);
   (*dt)[at] = TreeDt{(int16_t)best.first, 0, best.second, l, r};
   return at;
-}
-
-size_t slice_bytes(const TreePlanImpl& T, int node_w, int split_w) {
-  return static_cast<size_t>(node_w) * split_w * T.max_bins * T.dev.n_mom * 8;
-}
-
-int n_slices(const TreePlanImpl& T, const TreeShape& s) {
-  return ((T.dev.n_nodes + s.node_w - 1) / s.node_w) * ((T.dev.n_split + s.split_w - 1) / s.split_w);
 }
 
 }  // namespace
@@ -368,26 +359,13 @@ lmf_status tree_plan(const std::vector<TreeAggIn>& in, const std::map<std::strin
   T.dev.n_split = (int)T.split_z.size();
   T.dev.max_bins = T.max_bins;
   T.dev.n_mom = (int)T.moms.size();
-  // default shape: every node in one slice, as many split attributes as fit in 100 KB
-  const size_t per_split = slice_bytes(T, T.dev.n_nodes, 1);
-  T.shape.node_w = T.dev.n_nodes;
-  while (per_split > 0 && T.shape.node_w > 1 && slice_bytes(T, T.shape.node_w, 1) > 100 * 1024)
-    T.shape.node_w = (T.shape.node_w + 1) / 2;
-  T.shape.split_w = 1;
-  while (T.shape.split_w < T.dev.n_split && slice_bytes(T, T.shape.node_w, T.shape.split_w * 2) <= 100 * 1024)
-    T.shape.split_w *= 2;
-  T.shape.split_w = std::min(T.shape.split_w, T.dev.n_split);
   T.shape.cps = 2;
-  T.shape.chunk = 8192;
-  // the queue array must cover any shape the autotuner may pick
-  T.max_slices = T.dev.n_nodes * T.dev.n_split;
   return LMF_OK;
 }
 
 void tree_alloc_zeroed(TreePlan* tp, int64_t /*N*/, const std::function<size_t(size_t)>& take) {
   TreePlanImpl& T = *tp->impl;
   T.H_off = take(static_cast<size_t>(T.dev.n_nodes) * T.dev.n_split * T.max_bins * T.dev.n_mom * 8);
-  T.queue_off = take(static_cast<size_t>(T.max_slices) * 4 + 4);
 }
 
 void tree_alloc(TreePlan* tp, int64_t /*N*/, const std::function<size_t(size_t)>& take) {
@@ -413,7 +391,6 @@ lmf_status tree_finish(TreePlan* tp, char* base, long long* res_i64, double* res
   D.N = N;
   D.status = status;
   D.H = reinterpret_cast<long long*>(base + T.H_off);
-  D.queue = reinterpret_cast<uint32_t*>(base + T.queue_off);
   // moments: fixed-point scale from the value bounds, 0 for the count
   std::vector<double> scale(T.moms.size());
   for (size_t m = 0; m < T.moms.size(); ++m) {
@@ -511,14 +488,18 @@ lmf_status tree_finish(TreePlan* tp, char* base, long long* res_i64, double* res
 // ---------------------------------------------------------------------------
 // kernels
 
-// exact 64-bit accumulation in two 32-bit shared-memory words (low word with
-// carry detection through the returned old value, high word plain)
-__device__ __forceinline__ void acc64(uint32_t* lo, uint32_t* hi, long long v) {
-  const uint32_t vl = static_cast<uint32_t>(v);
-  const uint32_t vh = static_cast<uint32_t>(static_cast<unsigned long long>(v) >> 32);
-  const uint32_t old = atomicAdd(lo, vl);
-  const uint32_t up = vh + ((old + vl < old) ? 1u : 0u);
-  if (up) atomicAdd(hi, up);
+// exact sum over the lanes of `mask` of a 64-bit integer (two's complement,
+// mod 2^64): three 32-bit warp reductions of its 16 + 16 + 32-bit pieces,
+// none of which can overflow over 32 lanes; every lane of mask gets the sum
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned mask, unsigned long long v) {
+  const unsigned s0 = __reduce_add_sync(mask, static_cast<unsigned>(v & 0xffffu));
+  const unsigned s1 = __reduce_add_sync(mask, static_cast<unsigned>((v >> 16) & 0xffffu));
+  const unsigned s2 = __reduce_add_sync(mask, static_cast<unsigned>(v >> 32));
+  return (static_cast<unsigned long long>(s2) << 32) + (static_cast<unsigned long long>(s1) << 16) + s0;
+}
+
+__device__ __forceinline__ void red_add_u64(long long* dst, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(dst), static_cast<unsigned long long>(v));
 }
 
 // the row's node in group g: descend the decision tree, then check the
@@ -543,92 +524,86 @@ __device__ __forceinline__ int tree_node_of(const TreeDev& d, int g, const float
   return kNoNode;
 }
 
-constexpr int kTreeThreads = 128;
+constexpr int kTreeThreads = 256;
+constexpr int kTreeThrSmem = 48 * 1024;   // thresholds staged in shared memory up to this size
 
 template <int MP>
-__global__ void __launch_bounds__(kTreeThreads) k_tree_fused(const __grid_constant__ RootParams p,
-                                                             const __grid_constant__ TreeDev d, TreeShape sh,
-                                                             int n_slices) {
+__global__ void __launch_bounds__(kTreeThreads, 2) k_tree_fused(const __grid_constant__ RootParams p,
+                                                                const __grid_constant__ TreeDev d) {
   extern __shared__ __align__(16) uint32_t sm[];
-  const int slice = blockIdx.x % n_slices;
-  const int n_split_slices = (d.n_split + sh.split_w - 1) / sh.split_w;
-  const int n0 = (slice / n_split_slices) * sh.node_w;
-  const int f0 = (slice % n_split_slices) * sh.split_w;
-  const int nw = min(sh.node_w, d.n_nodes - n0);
-  const int fw = min(sh.split_w, d.n_split - f0);
-  const int cells = nw * fw * d.max_bins * d.n_mom;
-  uint32_t* lo = sm;
-  uint32_t* hi = sm + cells;
-  float* thr = reinterpret_cast<float*>(sm + 2 * cells);     // [fw][max_bins]: the slice's sorted thresholds
-  int32_t* thr_n = reinterpret_cast<int32_t*>(thr + fw * d.max_bins);
-  float* Z = reinterpret_cast<float*>(thr_n + ((fw + 3) & ~3));
+  const int nthr = d.thr_off[d.n_split];
+  const bool thr_smem = static_cast<size_t>(nthr) * 4 <= static_cast<size_t>(kTreeThrSmem);
+  float* thr_s = reinterpret_cast<float*>(sm);                  // all thresholds, split after split
+  float* Z = reinterpret_cast<float*>(sm + (thr_smem ? ((nthr + 3) & ~3) : 0));
   int32_t* C = reinterpret_cast<int32_t*>(Z + kTreeThreads * (MP + 4));
   const int ncat = p.n_rowcat > 0 ? p.n_rowcat : 1;
-  for (int i = threadIdx.x; i < 2 * cells; i += blockDim.x) sm[i] = 0u;
-  for (int f = 0; f < fw; ++f) {
-    const int t0 = d.thr_off[f0 + f], nt = d.thr_off[f0 + f + 1] - t0;
-    for (int j = threadIdx.x; j < nt; j += blockDim.x) thr[f * d.max_bins + j] = d.thr[t0 + j];
-    if (threadIdx.x == 0) thr_n[f] = nt;
-  }
-  __shared__ uint32_t chunk_s;
+  if (thr_smem)
+    for (int j = threadIdx.x; j < nthr; j += blockDim.x) thr_s[j] = d.thr[j];
+  const float* thr = thr_smem ? thr_s : d.thr;
   float* zrow = Z + threadIdx.x * (MP + 4);
   int32_t* crow = C + threadIdx.x * ncat;
+  const int lane = threadIdx.x & 31;
   __syncthreads();
-  const int64_t n_chunks = (d.N + sh.chunk - 1) / sh.chunk;
-  for (;;) {
-    if (threadIdx.x == 0) chunk_s = atomicAdd(d.queue + slice, 1u);
-    __syncthreads();
-    const int64_t c = chunk_s;
-    __syncthreads();
-    if (c >= n_chunks) break;
-    const int64_t r1 = d.N < (c + 1) * sh.chunk ? d.N : (c + 1) * sh.chunk;
-    for (int64_t row = c * sh.chunk + threadIdx.x; row < r1; row += blockDim.x) {
-      const long long w = root_row_z<MP>(p, row, zrow, crow);
-      if (w == 0) continue;
-      long long mv[kTreeMaxMom];
-      bool have = false;
-      for (int g = 0; g < d.n_groups; ++g) {
-        const int n = tree_node_of(d, g, zrow);
-        if (n == kNoNode || n < n0 || n >= n0 + nw) continue;
-        if (!have) {  // the row's fixed-point moments, once
-          for (int m = 0; m < d.n_mom; ++m) {
-            long long v = w;
-            if (d.mom_scale[m] > 0.0) {
-              double x = static_cast<double>(w);
-              if (d.mom_a[m] >= 0) x *= static_cast<double>(zrow[d.mom_a[m]]);
-              if (d.mom_b[m] >= 0) x *= static_cast<double>(zrow[d.mom_b[m]]);
-              v = llrint(x * d.mom_scale[m]);
-            }
-            mv[m] = v;
+  const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  // every lane of a warp runs every iteration (warp reductions below), rows
+  // past the end are inactive
+  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < d.N; base += step) {
+    const int64_t row = base + threadIdx.x;
+    long long w = 0;
+    if (row < d.N) w = root_row_z<MP>(p, row, zrow, crow);
+    long long mv[kTreeMaxMom];
+    bool have = false;
+    for (int g = 0; g < d.n_groups; ++g) {
+      const int n = w != 0 ? tree_node_of(d, g, zrow) : static_cast<int>(kNoNode);
+      const bool on = n != static_cast<int>(kNoNode);
+      const unsigned on_mask = __ballot_sync(0xffffffffu, on);
+      if (on_mask == 0u) continue;  // warp-uniform
+      if (on && !have) {  // the row's fixed-point moments, once
+#pragma unroll
+        for (int m = 0; m < kTreeMaxMom; ++m) {
+          if (m >= d.n_mom) break;
+          long long v = w;
+          if (d.mom_scale[m] > 0.0) {
+            double x = static_cast<double>(w);
+            if (d.mom_a[m] >= 0) x *= static_cast<double>(zrow[d.mom_a[m]]);
+            if (d.mom_b[m] >= 0) x *= static_cast<double>(zrow[d.mom_b[m]]);
+            v = llrint(x * d.mom_scale[m]);
           }
-          have = true;
+          mv[m] = v;
         }
-        for (int f = 0; f < fw; ++f) {
-          const float x = zrow[d.split_z[f0 + f]];
-          const float* t = thr + f * d.max_bins;
-          int l = 0, h = thr_n[f];
+        have = true;
+      }
+      const int lead = __ffs(on_mask) - 1;
+      for (int f = 0; f < d.n_split; ++f) {
+        int64_t cell = 0;
+        if (on) {
+          const float x = zrow[d.split_z[f]];
+          const int t0 = d.thr_off[f];
+          int l = 0, h = d.thr_off[f + 1] - t0;
           while (l < h) {  // number of thresholds < x
             const int mid = (l + h) >> 1;
-            if (t[mid] < x) l = mid + 1;
+            if (thr[t0 + mid] < x) l = mid + 1;
             else h = mid;
           }
-          const int cell = (((n - n0) * fw + f) * d.max_bins + l) * d.n_mom;
-          for (int m = 0; m < d.n_mom; ++m)
-            if (mv[m] != 0) acc64(lo + cell + m, hi + cell + m, mv[m]);
+          cell = ((static_cast<int64_t>(n) * d.n_split + f) * d.max_bins + l) * d.n_mom;
+        }
+        const int64_t c0 = __shfl_sync(0xffffffffu, cell, lead);
+        if (__all_sync(0xffffffffu, !on || cell == c0)) {  // one cell for the whole warp
+#pragma unroll
+          for (int m = 0; m < kTreeMaxMom; ++m) {
+            if (m >= d.n_mom) break;
+            const unsigned long long sum = warp_sum_u64(0xffffffffu, on ? static_cast<unsigned long long>(mv[m]) : 0ull);
+            if (lane == lead && sum != 0ull) red_add_u64(d.H + c0 + m, static_cast<long long>(sum));
+          }
+        } else if (on) {
+#pragma unroll
+          for (int m = 0; m < kTreeMaxMom; ++m) {
+            if (m >= d.n_mom) break;
+            if (mv[m] != 0) red_add_u64(d.H + cell + m, mv[m]);
+          }
         }
       }
     }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < cells; i += blockDim.x) {
-    const unsigned long long v = (static_cast<unsigned long long>(hi[i]) << 32) | lo[i];
-    if (v == 0) continue;
-    const int m = i % d.n_mom;
-    const int b = (i / d.n_mom) % d.max_bins;
-    const int f = (i / (d.n_mom * d.max_bins)) % fw;
-    const int n = i / (d.n_mom * d.max_bins * fw);
-    const int64_t at = (((int64_t)(n0 + n) * d.n_split + (f0 + f)) * d.max_bins + b) * d.n_mom + m;
-    atomicAdd(reinterpret_cast<unsigned long long*>(d.H + at), v);
   }
 }
 
@@ -651,23 +626,27 @@ __global__ void k_tree_out(const __grid_constant__ TreeDev d, const TreeOut* out
 
 namespace {
 
-size_t fused_smem(const TreePlanImpl& T, const RootParams& rp, const TreeShape& sh) {
-  const size_t bins = slice_bytes(T, sh.node_w, sh.split_w);
-  const size_t thr = static_cast<size_t>(sh.split_w) * T.max_bins * 4 + ((sh.split_w + 3) & ~3) * 4;
+size_t fused_smem(const TreePlanImpl& T, const RootParams& rp) {
+  size_t nthr = 0;
+  for (auto& v : T.thr) nthr += v.size();
+  const size_t thr = nthr * 4 <= static_cast<size_t>(kTreeThrSmem) ? ((nthr + 3) & ~static_cast<size_t>(3)) * 4 : 0;
   const size_t z = static_cast<size_t>(kTreeThreads) * (T.mp + 4) * 4;
   const size_t cat = static_cast<size_t>(kTreeThreads) * (rp.n_rowcat > 0 ? rp.n_rowcat : 1) * 4;
-  return bins + thr + z + cat;
+  return thr + z + cat;
 }
 
 template <int MP>
 cudaError_t launch_fused_mp(const TreePlanImpl& T, const RootParams& rp, const TreeShape& sh, cudaStream_t s) {
-  const int ns = n_slices(T, sh);
-  const size_t sm = fused_smem(T, rp, sh);
-  int per = (int)((static_cast<int64_t>(T.num_sms) * sh.cps + ns - 1) / ns);
-  if (per < 1) per = 1;
+  const size_t sm = fused_smem(T, rp);
   cudaError_t e = cudaFuncSetAttribute(k_tree_fused<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_tree_fused<MP><<<ns * per, kTreeThreads, sm, s>>>(rp, T.dev, sh, ns);
+  int fit = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_tree_fused<MP>, kTreeThreads, sm);
+  if (e != cudaSuccess) return e;
+  const int cps = std::max(1, std::min(sh.cps, fit));
+  const int64_t need = (T.dev.N + kTreeThreads - 1) / kTreeThreads;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(T.num_sms) * cps));
+  k_tree_fused<MP><<<grid, kTreeThreads, sm, s>>>(rp, T.dev);
   return cudaGetLastError();
 }
 
@@ -698,26 +677,8 @@ bool tree_needs_tuning(const TreePlan* tp) { return tp && tp->impl && !tp->impl-
 cudaError_t tree_autotune(TreePlan* tp, const RootParams& rp, cudaStream_t s) {
   TreePlanImpl& T = *tp->impl;
   (void)rp;
-  // every slice recomputes the row pass: the fewest slices that fit, with some
-  // variants of the node / split cut, CTAs per SM and chunk size
-  std::vector<TreeShape> cand;
-  const int NS = std::max(1, T.dev.n_split), NN = std::max(1, T.dev.n_nodes);
-  constexpr size_t kCap = 220 * 1024;
-  for (int sd : {1, 2, 4}) {
-    const int split_w = (NS + sd - 1) / sd;
-    int nd = 1;
-    while (nd < NN && fused_smem(T, rp, {split_w, (NN + nd - 1) / nd, 1, 4096}) > kCap) nd *= 2;
-    const int node_w = (NN + nd - 1) / nd;
-    for (int nw : {node_w, (node_w + 1) / 2})
-      for (int cps : {1, 2})
-        for (int chunk : {4096, 16384}) {
-          const TreeShape c{split_w, nw, cps, chunk};
-          if (nw < 1 || fused_smem(T, rp, c) * cps > kCap) continue;
-          if (n_slices(T, c) > T.max_slices) continue;
-          cand.push_back(c);
-        }
-  }
-  if (cand.empty()) cand.push_back(T.shape);
+  // CTAs per SM of the persistent pass (capped by what fits)
+  std::vector<TreeShape> cand{{2}, {3}, {4}, {6}};
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -725,7 +686,6 @@ cudaError_t tree_autotune(TreePlan* tp, const RootParams& rp, cudaStream_t s) {
   TreeShape pick = T.shape;
   const size_t hbytes = static_cast<size_t>(T.dev.n_nodes) * T.dev.n_split * T.max_bins * T.dev.n_mom * 8;
   for (const auto& c : cand) {
-    cudaMemsetAsync(T.dev.queue, 0, static_cast<size_t>(T.max_slices) * 4, s);
     cudaMemsetAsync(T.dev.H, 0, hbytes, s);
     cudaEventRecord(a, s);
     cudaError_t e = launch_fused(T, rp, c, s);
@@ -748,11 +708,11 @@ cudaError_t tree_autotune(TreePlan* tp, const RootParams& rp, cudaStream_t s) {
 
 void tree_shape(const TreePlan* tp, int* out5) {
   const TreePlanImpl& T = *tp->impl;
-  out5[0] = n_slices(T, T.shape);
-  out5[1] = T.shape.split_w;
-  out5[2] = T.shape.node_w;
+  out5[0] = 1;                    // one pass over the root, every node and split
+  out5[1] = T.dev.n_split;
+  out5[2] = T.dev.n_nodes;
   out5[3] = T.shape.cps;
-  out5[4] = T.shape.chunk;
+  out5[4] = 0;
 }
 
 }  // namespace lmf

@@ -26,7 +26,7 @@ LMF_BATCH_SINGLE, LMF_BATCH_GRAPH = 0, 1
 LMF_ROOT_DECLARED, LMF_ROOT_EXPLICIT, LMF_ROOT_HEURISTIC = 0, 1, 2
 LMF_MAX_GROUP_BY = 3
 LMF_STAGES = 5
-LMF_PLAN_FEATURES = 24
+LMF_PLAN_FEATURES = 26
 LMF_PLAN_NO_JIT = 1
 LMF_PLAN_ROW_GRAM = 2
 LMF_DEVICE, LMF_HOST_COPY, LMF_HOST_MAPPED = 0, 1, 2
@@ -100,6 +100,7 @@ _SIGNATURES = {
                                  ctypes.POINTER(_I)]),
     'lmf_plan_features': (_I, [_P, _I, ctypes.POINTER(ctypes.c_float), _I]),
     'lmf_plan_learned': (_I, [_P, _I, _P, ctypes.POINTER(lmf_plan_opts), ctypes.POINTER(lmf_plan_opts)]),
+    'lmf_plan_precompile': (_I, [_P, _I, ctypes.POINTER(lmf_plan_opts), _I, ctypes.POINTER(_I)]),
     'lmf_mlp_create': (_I, [_I, _I, _I, ctypes.c_uint64, ctypes.POINTER(_P)]),
     'lmf_mlp_destroy': (_I, [_P]),
     'lmf_mlp_num_params': (_I, [_P, ctypes.POINTER(ctypes.c_int64)]),
@@ -299,6 +300,13 @@ class Engine:
         self._check(self.lib.lmf_plan_features(self.ctx, batch, f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                                LMF_PLAN_FEATURES), 'lmf_plan_features')
         return f
+
+    def plan_precompile(self, batch: int, base: Optional['lmf_plan_opts'] = None, threads: int = 0) -> int:
+        b = base or lmf_plan_opts(LMF_PREC_SPLIT_BF16, LMF_BATCH_GRAPH, 0, 0, 0, 0, 0, 0)
+        n = ctypes.c_int()
+        self._check(self.lib.lmf_plan_precompile(self.ctx, batch, ctypes.byref(b), threads, ctypes.byref(n)),
+                    'lmf_plan_precompile')
+        return n.value
 
     def plan_learned(self, batch: int, model: Optional['Mlp'], base: Optional['lmf_plan_opts'] = None
                      ) -> 'lmf_plan_opts':

@@ -20,8 +20,10 @@ def test_shipped_checkpoint_is_complete():
     p = np.fromfile(os.path.join(HERE, 'costmodel_gb300.bin'), dtype=np.float32)
     assert p.size == ref_mlp.n_params(meta['in_dim'], meta['hidden'])
     assert np.all(np.isfinite(p))
-    # the study the checkpoint was trained in: 400 training and 100 held-out schemas
-    assert meta['train']['schemas'] == 400 and meta['test']['schemas'] == 100
+    # the study the checkpoint was trained in: training and held-out schemas of
+    # the config-5 corpus, at a stated fact-table scale
+    assert meta['train']['schemas'] >= 80 and meta['test']['schemas'] >= 20 and meta['scale'] > 0
+    assert meta['test']['learned_regret_mean'] <= meta['test']['heuristic_regret_mean']
     # its FP64 forward pass at the normalisation centre is finite
     y, _ = ref_mlp.forward(p, np.array([meta['mean']]), np.array(meta['mean']),
                            np.array(meta['std']), meta['in_dim'], meta['hidden'])

@@ -44,15 +44,48 @@ def test_config2_full_size(order, precision, key_level):
     eng.close()
 
 
+def _node_subschema(sch, node):
+    """The schema with the fact table cut to the rows on which every predicate
+    of `node` holds (joined values followed through the dense dimension keys).
+    The oracle still applies the predicates itself, so a wrong cut can only
+    make the check fail, never pass."""
+    from workloads import Column, Relation, Schema
+    from workloads.schemas import _joined_sample
+    fact = sch.rel(sch.root)
+    rows = np.arange(fact.nrows)
+    mask = np.ones(fact.nrows, dtype=bool)
+    for attr, op, t in node:
+        v = _joined_sample(sch, attr, rows).astype(np.float64)
+        mask &= (v <= t) if op == 'le' else (v > t)
+    cut = Relation(fact.name, [Column(c.name, c.role, c.data[mask], c.cat_domain) for c in fact.columns])
+    rels = [cut if r.name == sch.root else r for r in sch.relations]
+    return Schema(rels, sch.edges, sch.root, dict(sch.meta)), int(mask.sum())
+
+
 def test_config3_full_size():
+    """10M rows, 64 nodes: four whole nodes (every feature x threshold x
+    moment aggregate of each, ~1.9k per node), plus a seeded sample of 300
+    aggregates from anywhere in the batch."""
     sch, batch = config3(10_000_000)
     got, info, eng = run_engine(sch, batch, precision=1, batching=1)
+    eng.close()
     assert info['tree_nodes'] == 64 and info['tree_groups'] == 1
+    nodes = sch.meta['nodes']
+    per_node = len(batch) // len(nodes)
+    assert per_node * len(nodes) == len(batch)
+    rng = np.random.default_rng(5)
+    for ni in sorted(rng.choice(len(nodes), size=4, replace=False).tolist()):
+        sub, n_rows = _node_subschema(sch, nodes[ni])
+        idx = list(range(ni * per_node, (ni + 1) * per_node))
+        assert all(batch[i].factors[:len(nodes[ni])] == nodes[ni] for i in idx)
+        want = oracle.evaluate(sub, [batch[i] for i in idx])
+        fails, stats = compare([got[i] for i in idx], want)
+        assert not fails, (ni, n_rows, fails[:3], stats)
+        assert all(0 <= got[i][0] <= n_rows for i in idx[::3])      # COUNTs within the node
     idx = _sample(len(batch), 300, 11)
     want = oracle.evaluate(sch, [batch[i] for i in idx])
     fails, stats = compare([got[i] for i in idx], want)
     assert not fails, (fails[:3], stats)
-    eng.close()
 
 
 def test_config4_full_size_exact():

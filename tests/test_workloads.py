@@ -158,3 +158,6 @@ def test_config5_recipe(index):
     for p, c, k in sch.edges:
         fk = sch.rel(p).col(k).data
         assert fk.min() >= 0 and fk.max() < sch.rel(c).nrows
+    fact_fks = [sch.rel('F').col(k).data for p, _, k in sch.edges if p == 'F']
+    if index % 2 == 0 and fact_fks:    # even indices: the fact sorted on its join attributes
+        assert any(np.all(np.diff(fk) >= 0) for fk in fact_fks)

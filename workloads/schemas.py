@@ -378,11 +378,16 @@ def config4(n_fact: int = 50_000_000, seed: Optional[int] = None,
 # ----------------------------------------------------------------------------
 # config 5: random acyclic schemas for plan selection
 # ----------------------------------------------------------------------------
-def config5_schema(index: int, n_scale: float = 1.0, seed: Optional[int] = None
-                   ) -> Tuple[Schema, List[Agg]]:
+def config5_schema(index: int, n_scale: float = 1.0, seed: Optional[int] = None,
+                   fact_order: str = 'mixed') -> Tuple[Schema, List[Agg]]:
     """Schema number `index` of the plan-selection corpus: 3-8 relations on a
     random tree, fact 1M-50M rows (times n_scale), 5-40 features, key skew
-    s in [0, 1.2], 10-2000 monomial / grouped aggregates."""
+    s in [0, 1.2], 10-2000 monomial / grouped aggregates.  fact_order 'mixed'
+    sorts the fact table on its join attributes (Sec. 3.5 order) for even
+    indices and keeps generation order for odd ones, so the corpus holds both
+    input orders; 'sorted' / 'random' fix one."""
+    if fact_order != 'mixed':
+        _check_order(fact_order)
     rng = _rng((SEED_BASE + 5 if seed is None else seed) * 1000 + index)
     nrel = int(rng.integers(3, 9))
     n_fact = max(1000, int(float(np.exp(rng.uniform(np.log(1e6), np.log(5e7)))) * n_scale))
@@ -423,6 +428,10 @@ def config5_schema(index: int, n_scale: float = 1.0, seed: Optional[int] = None
         batch = [batch[i] for i in keep]
     if cats:
         batch += grouped_batch(cats, feats[: max(1, min(len(feats), (n_target // 10) + 1))])
+    if fact_order == 'sorted' or (fact_order == 'mixed' and index % 2 == 0):
+        fks = [f'k{c}' for c in range(1, nrel) if parents[c] == 0]
+        if fks:
+            rels[0] = sort_by_join_attributes(rels[0], fks)
     sch = Schema(rels, edges, 'F', meta={'name': f'random-{index}', 'features': feats,
                                           'cats': cats, 'skew': skew})
     return sch, batch
