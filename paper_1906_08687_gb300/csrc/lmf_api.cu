@@ -1097,8 +1097,12 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   }
 
   // ---- key-level form (lmf_root_lean.cuh): every child key unique, plain
-  // precision, a compiled scan, at least one probe group and one feature
-  P->lean = P->unique_all && rp.n_grp >= 1 && m > 1 && Root.nrows > 0 &&
+  // precision, a compiled scan, at least one probe group and one feature, and
+  // some foreign key in runs (on a root in no useful order every reverse-view
+  // update is a reduction of its own: the row-level form is faster there)
+  bool any_runs = false;
+  for (int q = 0; q < rp.n_grp; ++q) any_runs = any_runs || has_runs[q];
+  P->lean = any_runs && P->unique_all && rp.n_grp >= 1 && m > 1 && Root.nrows > 0 &&
             P->opts.precision == LMF_PREC_PLAIN_FP32 && !(P->opts.flags & (LMF_PLAN_NO_JIT | LMF_PLAN_ROW_GRAM)) &&
             jit_available();
   std::vector<size_t> deferred;   // grouped sums of another group's mean, placed with the carriers
@@ -1512,7 +1516,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       ++n_direct_planned;
       direct_z = direct_z || !cls[a].mono.empty();
     }
-  if (P->lean) {  // three CTAs per SM: what the z tile and the bulk staging leave of 74 KB
+  if (P->lean) {  // two CTAs per SM: what the z tile, the bulk staging and the row Gram's sums leave of 110 KB
     rp.lean = 1;
     rp.gram_off = 1;
     rp.gram_n = rp.n_x;
@@ -1521,8 +1525,8 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     t.n_direct = n_direct_planned;
     lmf_status st = fill_rvs(t);
     if (st) return st;
-    base_smem = lean_shape(t, direct_z).cache_off;
-    smem_cap = 74 * 1024;
+    base_smem = lean_shape(t, direct_z).cache_off + kLeanGacc + 16;
+    smem_cap = 110 * 1024;
   }
   const int64_t cell_budget = std::max<int64_t>(0, (smem_cap - (int64_t)base_smem) / 4);
   const int64_t kResBudget = cell_budget * 3 / 4;
@@ -1962,19 +1966,19 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       }
       close(t1);
     }
-    // COUNT tables: per task, chunks of 1024 positions of its category index
+    // COUNT tables: per task, chunks of 256 positions of its category index
     // (keys grouped by a) x 256 view cells b
     for (size_t t = 0; t < P->cv_tasks.size(); ++t) {
       const CatViewTask& T = P->cv_tasks[t];
       if (T.mode != 0) continue;
       const int db = cvs[T.view].dom;
       const int64_t K = rp.grp[cvs[T.view].grp].K;
-      for (int64_t p0 = 0; p0 < K; p0 += 1024)
+      for (int64_t p0 = 0; p0 < K; p0 += 256)
         for (int b0 = 0; b0 < db; b0 += 256)
-          P->cv_pair_items.push_back(CvPairItem{(int)t, b0, 0, 0, p0, std::min(K, p0 + 1024)});
+          P->cv_pair_items.push_back(CvPairItem{(int)t, b0, 0, 0, p0, std::min(K, p0 + 256)});
     }
     // SUM(m) by b tables: per view, its mean tasks in groups of kCvMeanTasks,
-    // chunks of 512 keys x 256 view cells b
+    // chunks of 64 keys x 256 view cells b
     for (int v = 0; v < (int)cvs.size(); ++v) {
       int m0 = -1, m1 = -1;
       for (int t = P->cv_ranges.begin[v]; t < P->cv_ranges.begin[v + 1]; ++t)
@@ -1985,9 +1989,9 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       if (m0 < 0) continue;
       const int64_t K = rp.grp[cvs[v].grp].K;
       for (int t = m0; t < m1; t += kCvMeanTasks)
-        for (int64_t k0 = 0; k0 < K; k0 += 512)
+        for (int64_t k0 = 0; k0 < K; k0 += 64)
           for (int b0 = 0; b0 < cvs[v].dom; b0 += 256)
-            P->cv_mean_items.push_back(CvMeanItem{v, t, std::min(m1, t + kCvMeanTasks), b0, k0, std::min(K, k0 + 512)});
+            P->cv_mean_items.push_back(CvMeanItem{v, t, std::min(m1, t + kCvMeanTasks), b0, k0, std::min(K, k0 + 64)});
     }
   }
   P->rv_tasks = tasks;

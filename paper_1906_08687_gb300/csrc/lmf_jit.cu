@@ -5,6 +5,7 @@
 #include <dlfcn.h>
 #include <nvrtc.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -328,9 +329,10 @@ LeanShape lean_shape(const RootParams& rp, bool direct_z) {
   off += static_cast<uint32_t>(kLeanT * L.cat_w * 4);
   L.cache_off = (off + 15u) & ~15u;
   const size_t total = L.cache_off + static_cast<size_t>(rp.cache_cells + rp.res_cells) * 4;
+  L.gacc_off = static_cast<uint32_t>((total + 15u) & ~static_cast<size_t>(15u));
   const int nbk = L.mpx / 4, nb = nbk * (nbk + 1) / 2, rg = nb >= 256 ? 1 : 256 / nb;
   const size_t red = static_cast<size_t>(nb) * 16 * rg * sizeof(double);
-  L.smem = std::max(total, red);
+  L.smem = std::max(static_cast<size_t>(L.gacc_off) + kLeanGacc, red);
   return L;
 }
 
@@ -369,8 +371,27 @@ std::string jit_lean_source(const RootParams& rp, const std::vector<DirectAgg>& 
     << ", kStageW = " << L.stage_w << ", kCatW = " << L.cat_w << ", kRacc = " << L.racc << ";\n"
     << "  static constexpr bool kResident = " << ((res_rv >= 0 || rp.res_cells > 0) ? "true" : "false") << ";\n"
     << "  static constexpr uint32_t kXgOff = " << L.xg_off << "u, kZfOff = " << L.zf_off << "u, kStageOff = "
-    << L.stage_off << "u, kCatOff = " << L.cat_off << "u, kCacheOff = " << L.cache_off << "u;\n"
-    << "  static __device__ __forceinline__ long long run(const RootParams& p, int64_t row, long long* zi,\n"
+    << L.stage_off << "u, kCatOff = " << L.cat_off << "u, kCacheOff = " << L.cache_off << "u, kGaccOff = "
+    << L.gacc_off << "u;\n"
+    ;
+  // the root row's own columns (foreign keys, features, root categories),
+  // loaded one tile ahead of their use
+  const int n_rc = rp.n_rcat;
+  o << "  struct Row {\n    int32_t fk[" << std::max(1, rp.n_grp) << "];\n    float x[" << std::max(1, rp.n_x)
+    << "];\n    int32_t rc[" << std::max(1, n_rc) << "];\n  };\n"
+    << "  static __device__ __forceinline__ void load(const RootParams& p, int64_t row, Row& r) {\n"
+    << "    if (row >= p.N) return;\n";
+  // the root's columns are read once per launch: streaming loads (evict first)
+  for (int i = 0; i < rp.n_x; ++i) {
+    if (rp.x[i].dtype == 2)
+      o << "    r.x[" << i << "] = static_cast<float>(__ldcs(static_cast<const double*>(p.x[" << i << "].p) + row));\n";
+    else
+      o << "    r.x[" << i << "] = __ldcs(static_cast<const float*>(p.x[" << i << "].p) + row);\n";
+  }
+  for (int g = 0; g < rp.n_grp; ++g) o << "    r.fk[" << g << "] = __ldcs(p.grp[" << g << "].fk + row);\n";
+  for (int i = 0; i < n_rc; ++i) o << "    r.rc[" << i << "] = __ldcs(p.rcat[" << i << "] + row);\n";
+  o << "  }\n"
+    << "  static __device__ __forceinline__ long long run(const RootParams& p, int64_t row, const Row& r, long long* zi,\n"
        "      float* xg, float* zrow, int32_t* crow, uint32_t* cache, uint32_t* res_hist, long long res_key,\n"
        "      long long* racc, unsigned long long* stage) {\n"
        "    const int lane = threadIdx.x & 31;\n"
@@ -381,17 +402,11 @@ std::string jit_lean_source(const RootParams& rp, const std::vector<DirectAgg>& 
   for (int z = 1; z < rp.m; ++z)
     if (fixed(z)) o << "    long long fz" << z << " = 0;\n";
   o << "    if (row < p.N) {\n      w = 1;\n";
-  // the root's columns are read once per launch: streaming loads (evict first)
-  for (int i = 0; i < rp.n_x; ++i) {
-    if (rp.x[i].dtype == 2)
-      o << "      z" << 1 + i << " = static_cast<float>(__ldcs(static_cast<const double*>(p.x[" << i << "].p) + row));\n";
-    else
-      o << "      z" << 1 + i << " = __ldcs(static_cast<const float*>(p.x[" << i << "].p) + row);\n";
-  }
+  for (int i = 0; i < rp.n_x; ++i) o << "      z" << 1 + i << " = r.x[" << i << "];\n";
   for (int g = 0; g < rp.n_grp; ++g) {
     const GroupDesc& G = rp.grp[g];
     const int nw = G.n_cnt + G.n_mu + G.n_cat;
-    o << "      {\n        const int32_t fk = __ldcs(p.grp[" << g << "].fk + row);\n"
+    o << "      {\n        const int32_t fk = r.fk[" << g << "];\n"
       << "        fk" << g << " = fk;\n"
       << "        if (fk < 0 || fk >= " << G.K << ") {\n          w = 0;\n        } else {\n"
       << "          const uint4* rec = reinterpret_cast<const uint4*>(p.grp[" << g
@@ -447,7 +462,7 @@ std::string jit_lean_source(const RootParams& rp, const std::vector<DirectAgg>& 
   }
   for (int i = 0; i < rp.n_rcat; ++i) {
     const int c = rp.n_rowcat - rp.n_rcat + i;
-    o << "      {\n        int32_t v = __ldcs(p.rcat[" << i << "] + row);\n"
+    o << "      {\n        int32_t v = r.rc[" << i << "];\n"
       << "        if (v < 0 || v >= " << rp.rcat_dom[i] << ") {\n"
       << "          atomicOr(p.status, kStatusCatRange);\n          v = 0;\n        }\n"
       << "        c" << c << " = v;\n      }\n";
@@ -468,7 +483,9 @@ std::string jit_lean_source(const RootParams& rp, const std::vector<DirectAgg>& 
     if (c >= L.ncol) return "0ull";
     const int z = z_of_col[c];
     if (fixed(z)) return "(live ? static_cast<unsigned long long>(fz" + std::to_string(z) + ") : 0ull)";
-    return "static_cast<unsigned long long>(__float2ll_rn(z" + std::to_string(z) + " * " + flit(L.col_scale[c]) + "))";
+    int e2 = 0;
+    std::frexp(L.col_scale[c], &e2);  // the scale is 2^(e2 - 1)
+    return "static_cast<unsigned long long>(lean_fx(z" + std::to_string(z) + ", " + std::to_string(e2 - 1) + "))";
   };
   for (int c = 0; c < L.zi_ld; c += 2)
     o << "    reinterpret_cast<ulonglong2*>(zi)[" << c / 2 << "] = make_ulonglong2(" << col_expr(c) << ", "

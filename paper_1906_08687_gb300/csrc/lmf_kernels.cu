@@ -564,17 +564,26 @@ __global__ void __launch_bounds__(256) k_cv_pairs(const CatViewTask* tasks, cons
     __syncthreads();
     uint32_t acc = 0u;
     int a_cur = cats[0];
-    for (int j = 0; j < n; ++j) {
-      const int a = cats[j];
-      if (a != a_cur) {
-        if (on && acc) {
-          const int64_t cell = T.a_first ? static_cast<int64_t>(a_cur) * db + b : static_cast<int64_t>(b) * T.dom_a + a_cur;
-          atomicAdd(reinterpret_cast<unsigned long long*>(T.out + cell), static_cast<unsigned long long>(acc));
+    for (int j0 = 0; j0 < n; j0 += 8) {  // eight independent loads in flight, then the sums
+      uint32_t v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = (on && j0 + u < n) ? __ldg(C.V + static_cast<int64_t>(keys[j0 + u]) * db + b) : 0u;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (j0 + u >= n) break;
+        const int a = cats[j0 + u];
+        if (a != a_cur) {
+          if (on && acc) {
+            const int64_t cell =
+                T.a_first ? static_cast<int64_t>(a_cur) * db + b : static_cast<int64_t>(b) * T.dom_a + a_cur;
+            atomicAdd(reinterpret_cast<unsigned long long*>(T.out + cell), static_cast<unsigned long long>(acc));
+          }
+          acc = 0u;
+          a_cur = a;
         }
-        acc = 0u;
-        a_cur = a;
+        acc += v[u];
       }
-      if (on) acc += C.V[static_cast<int64_t>(keys[j]) * db + b];
     }
     if (on && acc) {
       const int64_t cell = T.a_first ? static_cast<int64_t>(a_cur) * db + b : static_cast<int64_t>(b) * T.dom_a + a_cur;
@@ -619,12 +628,18 @@ __global__ void __launch_bounds__(256) k_cv_means(const CatViewTask* tasks, cons
     }
     __syncthreads();
     if (!on) continue;
-    for (int j = 0; j < n; ++j) {
-      const uint32_t c = C.V[(k0 + j) * db + b];
-      if (c == 0u) continue;
+    for (int j0 = 0; j0 < n; j0 += 8) {  // eight independent loads in flight, then the products
+      uint32_t cv[8];
 #pragma unroll
-      for (int t = 0; t < kCvMeanTasks; ++t)
-        if (t < nt) acc[t] += cnt_times(c, mu[t][j], sc[t]);
+      for (int u = 0; u < 8; ++u) cv[u] = j0 + u < n ? __ldg(C.V + (k0 + j0 + u) * db + b) : 0u;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const uint32_t c = cv[u];
+        if (c == 0u) continue;
+#pragma unroll
+        for (int t = 0; t < kCvMeanTasks; ++t)
+          if (t < nt) acc[t] += cnt_times(c, mu[t][j0 + u], sc[t]);
+      }
     }
   }
   if (!on) return;

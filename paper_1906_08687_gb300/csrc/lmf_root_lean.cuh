@@ -39,6 +39,23 @@ namespace lmf {
 
 constexpr int kLeanFoldTiles = 8;     // tiles per FP32 chain of the row Gram before the two-float fold
 
+// round(z * 2^e) to the nearest integer (ties away from zero), exactly, with
+// integer operations: z = +-m * 2^(ez - 150) with the 24-bit significand m, so
+// z * 2^e = m * 2^sh, a left shift or a rounded right shift of m.  The plan's
+// scales keep |z| * 2^e below 2^62.
+__device__ __forceinline__ long long lean_fx(float z, int e) {
+  const uint32_t b = __float_as_uint(z);
+  const int ez = static_cast<int>((b >> 23) & 0xffu);
+  const unsigned long long m = (b & 0x7fffffu) | 0x800000u;
+  const int sh = ez - 150 + e;
+  unsigned long long v;
+  if (sh >= 0) v = m << (sh < 63 ? sh : 63);
+  else if (sh > -26) v = (m + (1ull << (-sh - 1))) >> -sh;
+  else v = 0ull;
+  if (ez == 0) v = 0ull;  // zero (and subnormals, below any scale's resolution)
+  return (b >> 31) ? -static_cast<long long>(v) : static_cast<long long>(v);
+}
+
 // sum of record word w (column col of the warp's fixed-point rows, exact
 // integers) over every run of equal keys among the warp's 32 rows, one
 // reduction per run; ziw: the warp's first fixed-point row (rows ld words
@@ -154,19 +171,32 @@ __device__ __forceinline__ void root_lean_body(const RootParams& p, int64_t n_ti
     ++bi;
   }
   const int bj = bi + tb;
-  float hi[16], lo[16], acc[16];
+  // the row Gram: FP32 chains in registers, folded every kLeanFoldTiles tiles
+  // into two-float sums kept in shared memory ([32][256]: hi, then lo)
+  float* gacc = reinterpret_cast<float*>(smem_raw + RowPass::kGaccOff);
+  float acc[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) hi[q] = lo[q] = acc[q] = 0.f;
+  for (int q = 0; q < 16; ++q) {
+    acc[q] = 0.f;
+    gacc[q * 256 + tid] = 0.f;
+    gacc[(16 + q) * 256 + tid] = 0.f;
+  }
   int fold_t = 0;
   long long cnt_acc = 0;
   const bool resident = RowPass::kResident && p.res_grp >= 0;
 
+  // the root's columns of the next tile are loaded while this one is processed
+  const int64_t t_begin = blockIdx.x * n_tiles / gridDim.x;
   const int64_t t_end = (blockIdx.x + 1) * n_tiles / gridDim.x;
-  for (int64_t tile = blockIdx.x * n_tiles / gridDim.x; tile < t_end; ++tile) {
+  typename RowPass::Row cur, nxt;
+  if (t_begin < t_end) RowPass::load(p, t_begin * T + tid, cur);
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    if (tile + 1 < t_end) RowPass::load(p, (tile + 1) * T + tid, nxt);
     if (resident) lean_res_advance<RowPass>(p, tile * T, res_hist, res_key, racc);
-    cnt_acc += RowPass::run(p, tile * T + tid, Zi + tid * RowPass::kZiLd, Xg + tid * MPX, Zf + tid * RowPass::kZfLd,
-                            Cs + tid * RowPass::kCatW, p.cache_cells ? cache : nullptr, res_hist, res_key, racc,
-                            stage + tid * RowPass::kStageW);
+    cnt_acc += RowPass::run(p, tile * T + tid, cur, Zi + tid * RowPass::kZiLd, Xg + tid * MPX,
+                            Zf + tid * RowPass::kZfLd, Cs + tid * RowPass::kCatW, p.cache_cells ? cache : nullptr,
+                            res_hist, res_key, racc, stage + tid * RowPass::kStageW);
+    cur = nxt;
     __syncthreads();
     // row-level Gram of the root's features
     if (active) {
@@ -184,15 +214,23 @@ __device__ __forceinline__ void root_lean_body(const RootParams& p, int64_t n_ti
         fold_t = 0;                      // along a chain, and the fold bounds its length
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          two_sum(hi[q], lo[q], acc[q]);
+          float h = gacc[q * 256 + tid], l = gacc[(16 + q) * 256 + tid];
+          two_sum(h, l, acc[q]);
+          gacc[q * 256 + tid] = h;
+          gacc[(16 + q) * 256 + tid] = l;
           acc[q] = 0.f;
         }
       }
     }
     __syncthreads();
   }
+  float hi[16], lo[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) two_sum(hi[q], lo[q], acc[q]);
+  for (int q = 0; q < 16; ++q) {
+    hi[q] = gacc[q * 256 + tid];
+    lo[q] = gacc[(16 + q) * 256 + tid];
+    two_sum(hi[q], lo[q], acc[q]);
+  }
   if (resident) {
     if (p.res_cells > 0) root_res_flush(p, res_hist, res_key);
     RowPass::flush_resident(p, racc, res_key);
