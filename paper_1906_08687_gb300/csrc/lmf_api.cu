@@ -1516,7 +1516,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       ++n_direct_planned;
       direct_z = direct_z || !cls[a].mono.empty();
     }
-  if (P->lean) {  // two CTAs per SM: what the z tile, the bulk staging and the row Gram's sums leave of 110 KB
+  if (P->lean) {  // three CTAs per SM: what the z tile and the bulk staging leave of 74 KB
     rp.lean = 1;
     rp.gram_off = 1;
     rp.gram_n = rp.n_x;
@@ -1525,8 +1525,8 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     t.n_direct = n_direct_planned;
     lmf_status st = fill_rvs(t);
     if (st) return st;
-    base_smem = lean_shape(t, direct_z).cache_off + kLeanGacc + 16;
-    smem_cap = 110 * 1024;
+    base_smem = lean_shape(t, direct_z).cache_off;
+    smem_cap = 74 * 1024;
   }
   const int64_t cell_budget = std::max<int64_t>(0, (smem_cap - (int64_t)base_smem) / 4);
   const int64_t kResBudget = cell_budget * 3 / 4;
@@ -1678,11 +1678,10 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     const LeanShape L = lean_shape(t, direct_z);
     P->lean_mpx = L.mpx;
     P->smem = L.smem;
-    // two CTAs per SM by default: the generated row pass keeps its z values in
-    // registers (128 a thread without spills); three when asked and the shared
-    // memory allows
-    const int lcps = P->opts.ctas_per_sm > 0 ? std::min(P->opts.ctas_per_sm, L.smem <= 74 * 1024 ? 3 : 2)
-                                              : (L.smem <= 110 * 1024 ? 2 : 1);
+    // three CTAs per SM (80 registers a thread) when the shared memory allows,
+    // else two; ctas_per_sm caps it
+    const int fit = L.smem <= 74 * 1024 ? 3 : (L.smem <= 110 * 1024 ? 2 : 1);
+    const int lcps = P->opts.ctas_per_sm > 0 ? std::min(P->opts.ctas_per_sm, fit) : fit;
     P->grid = (int)std::max<int64_t>(1, std::min<int64_t>(P->n_tiles, (int64_t)c->num_sms * lcps));
   }
   const int grid_max = std::max(P->grid, grid_jit);

@@ -327,12 +327,10 @@ LeanShape lean_shape(const RootParams& rp, bool direct_z) {
   off += static_cast<uint32_t>(kLeanT * L.stage_w * 8);
   L.cat_off = off;
   off += static_cast<uint32_t>(kLeanT * L.cat_w * 4);
-  L.cache_off = (off + 15u) & ~15u;
-  const size_t total = L.cache_off + static_cast<size_t>(rp.cache_cells + rp.res_cells) * 4;
-  L.gacc_off = static_cast<uint32_t>((total + 15u) & ~static_cast<size_t>(15u));
-  const int nbk = L.mpx / 4, nb = nbk * (nbk + 1) / 2, rg = nb >= 256 ? 1 : 256 / nb;
-  const size_t red = static_cast<size_t>(nb) * 16 * rg * sizeof(double);
-  L.smem = std::max(static_cast<size_t>(L.gacc_off) + kLeanGacc, red);
+  // the counters live across tiles: after the row Gram's fold staging, which
+  // reuses the start of the per-tile scratch
+  L.cache_off = std::max<uint32_t>((off + 15u) & ~15u, static_cast<uint32_t>(kLeanFoldStage));
+  L.smem = L.cache_off + static_cast<size_t>(rp.cache_cells + rp.res_cells) * 4;
   return L;
 }
 
@@ -371,8 +369,7 @@ std::string jit_lean_source(const RootParams& rp, const std::vector<DirectAgg>& 
     << ", kStageW = " << L.stage_w << ", kCatW = " << L.cat_w << ", kRacc = " << L.racc << ";\n"
     << "  static constexpr bool kResident = " << ((res_rv >= 0 || rp.res_cells > 0) ? "true" : "false") << ";\n"
     << "  static constexpr uint32_t kXgOff = " << L.xg_off << "u, kZfOff = " << L.zf_off << "u, kStageOff = "
-    << L.stage_off << "u, kCatOff = " << L.cat_off << "u, kCacheOff = " << L.cache_off << "u, kGaccOff = "
-    << L.gacc_off << "u;\n"
+    << L.stage_off << "u, kCatOff = " << L.cat_off << "u, kCacheOff = " << L.cache_off << "u;\n"
     ;
   // the root row's own columns (foreign keys, features, root categories),
   // loaded one tile ahead of their use
@@ -399,8 +396,11 @@ std::string jit_lean_source(const RootParams& rp, const std::vector<DirectAgg>& 
   for (int g = 0; g < rp.n_grp; ++g) o << "    int32_t fk" << g << " = -1;\n";
   for (int i = 1; i < rp.m; ++i) o << "    float z" << i << " = 0.f;\n";
   for (int i = 0; i < rp.n_rowcat; ++i) o << "    int32_t c" << i << " = 0;\n";
-  for (int z = 1; z < rp.m; ++z)
-    if (fixed(z)) o << "    long long fz" << z << " = 0;\n";
+  // the row's earlier bulk reductions read its fixed-point row: wait for them
+  // before anything writes it
+  bool any_bulk = false;
+  for (int r = 0; r < rp.n_rv; ++r) any_bulk = any_bulk || rp.rv[r].mode == kRvBulk;
+  if (any_bulk) o << "    lean_bulk_wait_read();\n";
   o << "    if (row < p.N) {\n      w = 1;\n";
   for (int i = 0; i < rp.n_x; ++i) o << "      z" << 1 + i << " = r.x[" << i << "];\n";
   for (int g = 0; g < rp.n_grp; ++g) {
@@ -452,9 +452,9 @@ std::string jit_lean_source(const RootParams& rp, const std::vector<DirectAgg>& 
           if (rp.fix_of_z[z] / 2 == q) in_q.push_back(z);
         if (in_q.empty()) continue;
         o << "          {\n          const uint4 f = __ldg(fx + " << q << ");\n";
-        for (int z : in_q)
-          o << "          fz" << z << " = static_cast<long long>((static_cast<unsigned long long>("
-            << (rp.fix_of_z[z] % 2 ? "f.w" : "f.y") << ") << 32) | " << (rp.fix_of_z[z] % 2 ? "f.z" : "f.x") << ");\n";
+        for (int z : in_q)  // straight into the row's fixed-point tile row (no register held)
+          o << "          reinterpret_cast<unsigned long long*>(zi)[" << L.col_of_z[z] << "] = (static_cast<unsigned long long>("
+            << (rp.fix_of_z[z] % 2 ? "f.w" : "f.y") << ") << 32) | " << (rp.fix_of_z[z] % 2 ? "f.z" : "f.x") << ";\n";
         o << "          }\n";
       }
     }
@@ -469,27 +469,41 @@ std::string jit_lean_source(const RootParams& rp, const std::vector<DirectAgg>& 
   }
   o << "    }\n    const bool live = w != 0;\n";
   for (int i = 1; i < rp.m; ++i) o << "    z" << i << " = live ? z" << i << " : 0.f;\n";
-  // the row's earlier bulk reductions read its fixed-point row: wait for them
-  bool any_bulk = false;
-  for (int r = 0; r < rp.n_rv; ++r) any_bulk = any_bulk || rp.rv[r].mode == kRvBulk;
-  if (any_bulk) o << "    lean_bulk_wait_read();\n";
   // the fixed-point row: column 0 the count, then each value at its scale
   // (exact: a power-of-two scaling rounded to an integer)
   std::vector<int> z_of_col(L.ncol, 0);
   for (int z = 0; z < kMaxZ; ++z)
     if (L.col_of_z[z] >= 0) z_of_col[L.col_of_z[z]] = z;
+  auto col_fixed = [&](int c) { return c > 0 && c < L.ncol && fixed(z_of_col[c]); };
   auto col_expr = [&](int c) -> std::string {
     if (c == 0) return "(live ? 1ull : 0ull)";
     if (c >= L.ncol) return "0ull";
     const int z = z_of_col[c];
-    if (fixed(z)) return "(live ? static_cast<unsigned long long>(fz" + std::to_string(z) + ") : 0ull)";
     int e2 = 0;
     std::frexp(L.col_scale[c], &e2);  // the scale is 2^(e2 - 1)
     return "static_cast<unsigned long long>(lean_fx(z" + std::to_string(z) + ", " + std::to_string(e2 - 1) + "))";
   };
-  for (int c = 0; c < L.zi_ld; c += 2)
-    o << "    reinterpret_cast<ulonglong2*>(zi)[" << c / 2 << "] = make_ulonglong2(" << col_expr(c) << ", "
-      << col_expr(c + 1) << ");\n";
+  // (the fixed-point images of means were stored as they arrived; a row that
+  // does not join clears them)
+  for (int c = 0; c < L.zi_ld; c += 2) {
+    if (!col_fixed(c) && !col_fixed(c + 1)) {
+      o << "    reinterpret_cast<ulonglong2*>(zi)[" << c / 2 << "] = make_ulonglong2(" << col_expr(c) << ", "
+        << col_expr(c + 1) << ");\n";
+      continue;
+    }
+    for (int e = c; e < c + 2; ++e)
+      if (!col_fixed(e)) o << "    reinterpret_cast<unsigned long long*>(zi)[" << e << "] = " << col_expr(e) << ";\n";
+  }
+  {
+    bool anyf = false;
+    for (int c = 0; c < L.zi_ld; ++c) anyf = anyf || col_fixed(c);
+    if (anyf) {
+      o << "    if (!live) {\n";
+      for (int c = 0; c < L.zi_ld; ++c)
+        if (col_fixed(c)) o << "      reinterpret_cast<unsigned long long*>(zi)[" << c << "] = 0ull;\n";
+      o << "    }\n";
+    }
+  }
   auto zv = [&](int i) { return i < rp.m ? "z" + std::to_string(i) : std::string("0.f"); };
   for (int c = 0; c < L.mpx; c += 4)
     o << "    *reinterpret_cast<float4*>(xg + " << c << ") = make_float4(" << zv(rp.gram_off + c) << ", "

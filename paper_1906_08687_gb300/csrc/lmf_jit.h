@@ -38,8 +38,9 @@ std::string jit_source(const RootParams& rp, int mp, const std::vector<DirectAgg
 // Gram [256][mpx] floats, the z rows of per-row tables that sum a feature
 // [256][zf_ld] floats, staging for bulk reductions [256][stage_w] int64, the
 // row categories of per-row tables [256][cat_w] int32, then the hot-cell and
-// resident-key counters, then the row Gram's two-float sums (kLeanGacc bytes).
-constexpr int kLeanGacc = 32 * 256 * 4;
+// resident-key counters (never below kLeanFoldStage: between tiles the row
+// Gram's chains are summed through the start of shared memory).
+constexpr int kLeanFoldStage = 16 * 256 * 4;  // the row Gram's fold staging at the start of shared memory
 struct LeanShape {
   int mpx = 4;                  // width of the row-level Gram block (multiple of 4)
   int ncol = 1;                 // columns of the fixed-point tile
@@ -53,7 +54,6 @@ struct LeanShape {
   int cat_w = 0;                // row categories staged per row
   int racc = 1;                 // 32-word chunks of the resident view's record
   uint32_t xg_off = 0, zf_off = 0, stage_off = 0, cat_off = 0, cache_off = 0;
-  uint32_t gacc_off = 0;        // the row Gram's two-float sums, [32][256] floats, after the counters
   size_t smem = 0;              // dynamic shared memory of one CTA, counters included
 };
 LeanShape lean_shape(const RootParams& rp, bool direct_z);

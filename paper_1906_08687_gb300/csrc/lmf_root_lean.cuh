@@ -56,6 +56,12 @@ __device__ __forceinline__ long long lean_fx(float z, int e) {
   return (b >> 31) ? -static_cast<long long>(v) : static_cast<long long>(v);
 }
 
+// reduction into a reverse view: nothing in the scan reads the views, so the
+// compiler may move shared-memory loads across it (no memory clobber)
+__device__ __forceinline__ void lean_red_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v));
+}
+
 // sum of record word w (column col of the warp's fixed-point rows, exact
 // integers) over every run of equal keys among the warp's 32 rows, one
 // reduction per run; ziw: the warp's first fixed-point row (rows ld words
@@ -78,7 +84,7 @@ __device__ __forceinline__ void lean_rv_runs(const WarpRuns& q, long long fk, co
   if (q.heads == 1u) {  // one run over the whole warp (warp-uniform)
     const long long acc = lean_warp_sum(ziw, ld, col);
     const long long k0 = __shfl_sync(kFullWarp, fk, 0);
-    if (on && k0 >= 0 && acc != 0) rp_red_u64(rec0 + k0 * stride + w, static_cast<unsigned long long>(acc));
+    if (on && k0 >= 0 && acc != 0) lean_red_u64(rec0 + k0 * stride + w, static_cast<unsigned long long>(acc));
     return;
   }
   long long acc = 0;
@@ -87,7 +93,7 @@ __device__ __forceinline__ void lean_rv_runs(const WarpRuns& q, long long fk, co
     acc += ziw[j * ld + col];
     if (j == 31 || ((q.heads >> (j + 1)) & 1u)) {  // row j ends a run (warp-uniform)
       const long long kj = __shfl_sync(kFullWarp, fk, j);
-      if (on && kj >= 0 && acc != 0) rp_red_u64(rec0 + kj * stride + w, static_cast<unsigned long long>(acc));
+      if (on && kj >= 0 && acc != 0) lean_red_u64(rec0 + kj * stride + w, static_cast<unsigned long long>(acc));
       acc = 0;
     }
   }
@@ -171,17 +177,40 @@ __device__ __forceinline__ void root_lean_body(const RootParams& p, int64_t n_ti
     ++bi;
   }
   const int bj = bi + tb;
-  // the row Gram: FP32 chains in registers, folded every kLeanFoldTiles tiles
-  // into two-float sums kept in shared memory ([32][256]: hi, then lo)
-  float* gacc = reinterpret_cast<float*>(smem_raw + RowPass::kGaccOff);
-  float acc[16];
+  // the row Gram: FP32 chains in registers (a 4x4 block of the upper
+  // triangle per thread, RG threads per block); every kLeanFoldTiles tiles the
+  // chains of a block entry are summed into one two-float total held by the
+  // entry's owner thread (entry e = block * 16 + q owned by thread e mod 256)
+  constexpr int NE = (NB * 16 + T - 1) / T;
+  float acc[16], ghi[NE], glo[NE];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    acc[q] = 0.f;
-    gacc[q * 256 + tid] = 0.f;
-    gacc[(16 + q) * 256 + tid] = 0.f;
-  }
+  for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+#pragma unroll
+  for (int e = 0; e < NE; ++e) ghi[e] = glo[e] = 0.f;
   int fold_t = 0;
+  // fold: the chains go through shared memory at the start of the tile (the
+  // fixed-point tile is free between tiles once this thread's bulk
+  // reductions have read it); every thread of the CTA calls this
+  auto fold = [&]() {
+    float* st = reinterpret_cast<float*>(smem_raw);  // [16][T]
+    lean_bulk_wait_read();
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      st[q * T + tid] = active ? acc[q] : 0.f;
+      acc[q] = 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+      const int ent = tid + e * T;
+      if (ent < NB * 16) {
+        const int b = ent / 16, q = ent % 16;
+        for (int g = 0; g < RG; ++g) two_sum(ghi[e], glo[e], st[q * T + g * NB + b]);
+      }
+    }
+    __syncthreads();
+  };
   long long cnt_acc = 0;
   const bool resident = RowPass::kResident && p.res_grp >= 0;
 
@@ -210,52 +239,34 @@ __device__ __forceinline__ void root_lean_body(const RootParams& p, int64_t n_ti
 #pragma unroll
           for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fmaf(av[u], bv[v], acc[u * 4 + v]);
       }
-      if (++fold_t == kLeanFoldTiles) {  // products of root features vary row by row: no value repeats
-        fold_t = 0;                      // along a chain, and the fold bounds its length
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          float h = gacc[q * 256 + tid], l = gacc[(16 + q) * 256 + tid];
-          two_sum(h, l, acc[q]);
-          gacc[q * 256 + tid] = h;
-          gacc[(16 + q) * 256 + tid] = l;
-          acc[q] = 0.f;
-        }
-      }
     }
     __syncthreads();
+    if (++fold_t == kLeanFoldTiles) {  // products of root features vary row by row: no value repeats
+      fold_t = 0;                      // along a chain, and the fold bounds its length
+      fold();
+    }
   }
-  float hi[16], lo[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    hi[q] = gacc[q * 256 + tid];
-    lo[q] = gacc[(16 + q) * 256 + tid];
-    two_sum(hi[q], lo[q], acc[q]);
-  }
+  fold();
   if (resident) {
     if (p.res_cells > 0) root_res_flush(p, res_hist, res_key);
     RowPass::flush_resident(p, racc, res_key);
   }
   root_cache_flush(p, cache);
   lean_bulk_wait_all();
-  __syncthreads();  // the reduction below reuses the start of shared memory
-  double* red = reinterpret_cast<double*>(smem_raw);  // [NB * 16][RG]
-  if (active) {
-#pragma unroll
-    for (int q = 0; q < 16; ++q) red[(gblk * 16 + q) * RG + grow] = (double)hi[q] + (double)lo[q];
-  }
-  __syncthreads();
   double* out = p.gram_part + (int64_t)blockIdx.x * MPX * MPX;
-  for (int e = tid; e < NB * 16; e += blockDim.x) {
-    const int b = e / 16, q = e % 16;
-    int ii = 0, tt = b;
-    while (tt >= NBK - ii) {
-      tt -= NBK - ii;
-      ++ii;
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    const int ent = tid + e * T;
+    if (ent < NB * 16) {
+      const int b = ent / 16, q = ent % 16;
+      int ii = 0, tt = b;
+      while (tt >= NBK - ii) {
+        tt -= NBK - ii;
+        ++ii;
+      }
+      const int jj = ii + tt;
+      out[(4 * ii + q / 4) * MPX + 4 * jj + q % 4] = (double)ghi[e] + (double)glo[e];
     }
-    const int jj = ii + tt;
-    double s = 0.0;
-    for (int g = 0; g < RG; ++g) s += red[e * RG + g];
-    out[(4 * ii + q / 4) * MPX + 4 * jj + q % 4] = s;
   }
   __shared__ long long cred[8];
   long long c = cnt_acc;
