@@ -68,10 +68,12 @@ def parse():
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--workload', default='snowflake', choices=sorted(WORKLOADS))
     ap.add_argument('--n-fact', type=int, default=None, help='fact rows (default: the workload\'s)')
-    ap.add_argument('--precision', default='auto', choices=['auto', 'split', 'plain'],
-                    help='Gram precision of the chosen plan; auto lets the learned plan choice '
+    ap.add_argument('--precision', default='auto', choices=['auto', 'split', 'plain', 'plain-rowlevel'],
+                    help='Gram form of the chosen plan; auto lets the learned plan choice '
                          '(shipped cost-model checkpoint, the Sec. 3.3 rule without one) pick the '
-                         'root, the Gram form and view merging')
+                         'root, the Gram form and view merging; split: split-bf16 tensor cores; '
+                         'plain: FP32 (key-level blocks where eligible); plain-rowlevel: FP32, '
+                         'every block per row')
     ap.add_argument('--fact-order', default='sorted', choices=['sorted', 'random'],
                     help='fact rows sorted by their join attributes (the input order of the '
                          "paper's experiments) or in generation order")
@@ -438,9 +440,10 @@ def main():
         chosen_opts = eng.plan_learned(bid, model, base)
     else:
         origin = f'fixed by --precision {args.precision}'
-        eng.plan(bid, precision=names[args.precision], batching=1)
-        chosen_opts = lmf_plan_opts(names[args.precision], LMF_BATCH_GRAPH, 0, 0, 1,
-                                    eng.plan_info(bid)['root_rel'], 0, 0)
+        prec_f = names[args.precision.split('-')[0]]
+        flags = LMF_PLAN_ROW_GRAM if args.precision == 'plain-rowlevel' else 0
+        eng.plan_opts(bid, lmf_plan_opts(prec_f, LMF_BATCH_GRAPH, 0, 0, 0, 0, 0, flags))
+        chosen_opts = lmf_plan_opts(prec_f, LMF_BATCH_GRAPH, 0, 0, 1, eng.plan_info(bid)['root_rel'], 0, flags)
     # the rule's plan (Sec. 3.3 root, default options) for comparison
     e_r, b_r = make(None, None, dev, opts=lmf_plan_opts(LMF_PREC_SPLIT_BF16, LMF_BATCH_GRAPH, 0, 0,
                                                         LMF_ROOT_HEURISTIC, 0, 0, 0))

@@ -412,6 +412,57 @@ lmf_status lmf_mlp_train_step(lmf_mlp* m, const float* x_dev, const float* y_dev
 lmf_status lmf_plan_learned(lmf_ctx* ctx, int batch_id, lmf_mlp* model, const lmf_plan_opts* base,
                             lmf_plan_opts* chosen);
 
+/* ---------------------------------------------------------------------------
+ * Consumers of a batch (Sec. 2): models trained from aggregates the engine
+ * already holds in device memory.  Each is one small launch on cuda_stream
+ * (NULL: the legacy default stream), asynchronous, deterministic (fixed-order
+ * reductions).  Inputs and outputs are device pointers.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Ridge linear regression by batch gradient descent over the covar matrix
+ * (Sec. 2, objective J and its gradient; Sec. 4 setup: Barzilai-Borwein steps
+ * with Armijo backtracking).  dev_sigma: m x m doubles, row-major, the covar
+ * matrix sum X X^T over (X_1 = 1, features ..., label) -- the label last, its
+ * parameter fixed at -1; count = |D|; lam >= 0 the penalty on theta_1..n.
+ * Writes theta (m - 1 doubles) to dev_theta and the iterations run to
+ * dev_iters (one int).  Stops when ||grad|| <= tol * max(1, ||grad_0||) or
+ * after max_iter iterations.  Limits: 2 <= m <= 96.  Errors: LMF_ERR_ARG,
+ * LMF_ERR_CUDA.
+ */
+lmf_status lmf_ridge_bgd(const double* dev_sigma, int m, double count, double lam, int max_iter, double tol,
+                         double* dev_theta, int* dev_iters, void* cuda_stream);
+
+/* One categorical pair of lmf_mutual_information: device pointers to the
+ * marginal counts beta (dom_i) and gamma (dom_j) and the joint counts delta
+ * (dom_i x dom_j, row-major), e.g. results of COUNT grouped by X_i, by X_j and
+ * by (X_i, X_j). */
+typedef struct {
+  const int64_t* beta;
+  const int64_t* gamma;
+  const int64_t* delta;
+  int32_t dom_i, dom_j;
+} lmf_mi_pair;
+
+/*
+ * Mutual information of n_pairs categorical pairs (Sec. 2, Eq. mi: the sum of
+ * delta/alpha * log(alpha delta / (beta gamma)) over the cells with delta > 0,
+ * natural logarithm), alpha = the COUNT.  dev_pairs: device array of n_pairs
+ * lmf_mi_pair; dev_mi: n_pairs doubles.  Errors: LMF_ERR_ARG (null pointers,
+ * alpha <= 0), LMF_ERR_CUDA.
+ */
+lmf_status lmf_mutual_information(const lmf_mi_pair* dev_pairs, int n_pairs, int64_t alpha, double* dev_mi,
+                                  void* cuda_stream);
+
+/*
+ * Chow-Liu tree over n attributes (Sec. 2): pairs in decreasing mutual
+ * information (ties: the pair (i, j), i < j, first in row-major order), each
+ * kept unless it closes a cycle.  dev_mi: n x n doubles (entries i < j read);
+ * dev_edges: 2 (n - 1) ints, the kept pairs (i, j) in the order taken;
+ * dev_n_edges: one int.  Limit n <= 64.  Errors: LMF_ERR_ARG, LMF_ERR_CUDA.
+ */
+lmf_status lmf_chow_liu(const double* dev_mi, int n, int* dev_edges, int* dev_n_edges, void* cuda_stream);
+
 /*
  * The covar Gram of one relation (the covar matrix of Sec. 2, Eq. lr-sigma,
  * over a single relation), computed without allocating any device memory.

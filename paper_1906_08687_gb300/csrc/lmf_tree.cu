@@ -535,12 +535,12 @@ __global__ void __launch_bounds__(kTreeThreads, 2) k_tree_fused(const __grid_con
   const bool thr_smem = static_cast<size_t>(nthr) * 4 <= static_cast<size_t>(kTreeThrSmem);
   float* thr_s = reinterpret_cast<float*>(sm);                  // all thresholds, split after split
   float* Z = reinterpret_cast<float*>(sm + (thr_smem ? ((nthr + 3) & ~3) : 0));
-  int32_t* C = reinterpret_cast<int32_t*>(Z + kTreeThreads * (MP + 4));
+  int32_t* C = reinterpret_cast<int32_t*>(Z + kTreeThreads * (MP + 1));
   const int ncat = p.n_rowcat > 0 ? p.n_rowcat : 1;
   if (thr_smem)
     for (int j = threadIdx.x; j < nthr; j += blockDim.x) thr_s[j] = d.thr[j];
   const float* thr = thr_smem ? thr_s : d.thr;
-  float* zrow = Z + threadIdx.x * (MP + 4);
+  float* zrow = Z + threadIdx.x * (MP + 1);  // odd stride: no bank conflicts
   int32_t* crow = C + threadIdx.x * ncat;
   const int lane = threadIdx.x & 31;
   __syncthreads();
@@ -630,7 +630,7 @@ size_t fused_smem(const TreePlanImpl& T, const RootParams& rp) {
   size_t nthr = 0;
   for (auto& v : T.thr) nthr += v.size();
   const size_t thr = nthr * 4 <= static_cast<size_t>(kTreeThrSmem) ? ((nthr + 3) & ~static_cast<size_t>(3)) * 4 : 0;
-  const size_t z = static_cast<size_t>(kTreeThreads) * (T.mp + 4) * 4;
+  const size_t z = static_cast<size_t>(kTreeThreads) * (T.mp + 1) * 4;
   const size_t cat = static_cast<size_t>(kTreeThreads) * (rp.n_rowcat > 0 ? rp.n_rowcat : 1) * 4;
   return thr + z + cat;
 }

@@ -75,6 +75,11 @@ class lmf_plan_stats(ctypes.Structure):
                 ('jit', ctypes.c_int32), ('key_level', ctypes.c_int32)]
 
 
+class lmf_mi_pair(ctypes.Structure):
+    _fields_ = [('beta', ctypes.c_void_p), ('gamma', ctypes.c_void_p), ('delta', ctypes.c_void_p),
+                ('dom_i', ctypes.c_int32), ('dom_j', ctypes.c_int32)]
+
+
 # every symbol include/lmf.h declares, with its ctypes signature
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -112,6 +117,9 @@ _SIGNATURES = {
     'lmf_mlp_grad': (_I, [_P, _P, _P, _I, _P, ctypes.POINTER(ctypes.c_float)]),
     'lmf_mlp_train_step': (_I, [_P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
     'lmf_gram_noalloc': (_I, [ctypes.POINTER(ctypes.c_void_p), _I, ctypes.c_int64, _P, _P]),
+    'lmf_ridge_bgd': (_I, [_P, _I, ctypes.c_double, ctypes.c_double, _I, ctypes.c_double, _P, _P, _P]),
+    'lmf_mutual_information': (_I, [_P, _I, ctypes.c_int64, _P, _P]),
+    'lmf_chow_liu': (_I, [_P, _I, _P, _P, _P]),
     'lmf_wait_selftest': (_I, [_P]),
     'lmf_status_string': (ctypes.c_char_p, [_I]),
     'lmf_error_message': (ctypes.c_char_p, [_P]),
@@ -426,3 +434,26 @@ def register_schema(engine: Engine, schema, tensors: dict, on_host=False) -> Non
         engine.register_relation(r.name, int(r.nrows), cols)
     ids = engine.rel_ids
     engine.declare_join([(ids[p], ids[c], k) for p, c, k in schema.edges])
+
+
+# -- consumers of a batch (Sec. 2): thin wrappers over the C ABI, device pointers in and out
+def ridge_bgd(sigma_ptr: int, m: int, count: float, lam: float, theta_ptr: int, iters_ptr: int,
+              max_iter: int = 10_000, tol: float = 1e-13, stream: int = 0) -> None:
+    """lmf_ridge_bgd: theta (m - 1 doubles) from the m x m covar matrix."""
+    st = load().lmf_ridge_bgd(sigma_ptr, m, count, lam, max_iter, tol, theta_ptr, iters_ptr, stream or None)
+    if st != LMF_OK:
+        raise LmfError(st, 'lmf_ridge_bgd')
+
+
+def mutual_information(pairs_ptr: int, n_pairs: int, alpha: int, out_ptr: int, stream: int = 0) -> None:
+    """lmf_mutual_information over a device array of lmf_mi_pair."""
+    st = load().lmf_mutual_information(pairs_ptr, n_pairs, alpha, out_ptr, stream or None)
+    if st != LMF_OK:
+        raise LmfError(st, 'lmf_mutual_information')
+
+
+def chow_liu(mi_ptr: int, n: int, edges_ptr: int, n_edges_ptr: int, stream: int = 0) -> None:
+    """lmf_chow_liu: the tree's edges from an n x n MI matrix."""
+    st = load().lmf_chow_liu(mi_ptr, n, edges_ptr, n_edges_ptr, stream or None)
+    if st != LMF_OK:
+        raise LmfError(st, 'lmf_chow_liu')

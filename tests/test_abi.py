@@ -57,7 +57,7 @@ def test_struct_layouts_match_header(tmp_path):
     from paper_1906_08687_gb300 import lmf
     structs = {'lmf_column': lmf.lmf_column, 'lmf_factor': lmf.lmf_factor,
                'lmf_agg_spec': lmf.lmf_agg_spec, 'lmf_plan_opts': lmf.lmf_plan_opts,
-               'lmf_plan_stats': lmf.lmf_plan_stats}
+               'lmf_plan_stats': lmf.lmf_plan_stats, 'lmf_mi_pair': lmf.lmf_mi_pair}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lmf.h"', 'int main(void) {']
     for name, cls in structs.items():
         lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
