@@ -57,6 +57,7 @@ struct TreeOut {
 
 struct TreeDev {
   int32_t n_nodes, n_groups, n_split, max_bins, n_mom;
+  int32_t mom_stride;          // words per histogram cell: 4 (one 32-byte sector) when n_mom <= 4
   const int32_t* pred_off;     // [n_nodes + 1]
   const TreePred* preds;
   const int32_t* group_off;    // [n_groups + 1] into group_nodes
@@ -72,7 +73,7 @@ struct TreeDev {
   const int32_t* droot;        // [n_groups]
   const struct TreeDt* dt;
   const int32_t* dcand;
-  long long* H;                // [n_nodes][n_split][max_bins][n_mom]
+  long long* H;                // [n_nodes][n_split][max_bins][mom_stride]
   int64_t N;
   uint32_t* status;
 };
@@ -359,13 +360,14 @@ lmf_status tree_plan(const std::vector<TreeAggIn>& in, const std::map<std::strin
   T.dev.n_split = (int)T.split_z.size();
   T.dev.max_bins = T.max_bins;
   T.dev.n_mom = (int)T.moms.size();
+  T.dev.mom_stride = T.dev.n_mom <= 4 ? 4 : T.dev.n_mom;
   T.shape.cps = 2;
   return LMF_OK;
 }
 
 void tree_alloc_zeroed(TreePlan* tp, int64_t /*N*/, const std::function<size_t(size_t)>& take) {
   TreePlanImpl& T = *tp->impl;
-  T.H_off = take(static_cast<size_t>(T.dev.n_nodes) * T.dev.n_split * T.max_bins * T.dev.n_mom * 8);
+  T.H_off = take(static_cast<size_t>(T.dev.n_nodes) * T.dev.n_split * T.max_bins * T.dev.mom_stride * 8);
 }
 
 void tree_alloc(TreePlan* tp, int64_t /*N*/, const std::function<size_t(size_t)>& take) {
@@ -537,6 +539,9 @@ __global__ void __launch_bounds__(kTreeThreads, 2) k_tree_fused(const __grid_con
   float* Z = reinterpret_cast<float*>(sm + (thr_smem ? ((nthr + 3) & ~3) : 0));
   int32_t* C = reinterpret_cast<int32_t*>(Z + kTreeThreads * (MP + 1));
   const int ncat = p.n_rowcat > 0 ? p.n_rowcat : 1;
+  // the row's moments, one 32-byte record, the source of its bulk reductions
+  __shared__ __align__(16) unsigned long long stage[kTreeThreads][4];
+  const bool bulk = d.mom_stride == 4;
   if (thr_smem)
     for (int j = threadIdx.x; j < nthr; j += blockDim.x) thr_s[j] = d.thr[j];
   const float* thr = thr_smem ? thr_s : d.thr;
@@ -572,6 +577,12 @@ __global__ void __launch_bounds__(kTreeThreads, 2) k_tree_fused(const __grid_con
           mv[m] = v;
         }
         have = true;
+        if (bulk) {  // the previous row's reductions have read the record: refill it
+          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+#pragma unroll
+          for (int m = 0; m < 4; ++m) stage[threadIdx.x][m] = m < d.n_mom ? static_cast<unsigned long long>(mv[m]) : 0ull;
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
       }
       const int lead = __ffs(on_mask) - 1;
       for (int f = 0; f < d.n_split; ++f) {
@@ -585,7 +596,7 @@ __global__ void __launch_bounds__(kTreeThreads, 2) k_tree_fused(const __grid_con
             if (thr[t0 + mid] < x) l = mid + 1;
             else h = mid;
           }
-          cell = ((static_cast<int64_t>(n) * d.n_split + f) * d.max_bins + l) * d.n_mom;
+          cell = ((static_cast<int64_t>(n) * d.n_split + f) * d.max_bins + l) * d.mom_stride;
         }
         const int64_t c0 = __shfl_sync(0xffffffffu, cell, lead);
         if (__all_sync(0xffffffffu, !on || cell == c0)) {  // one cell for the whole warp
@@ -595,6 +606,10 @@ __global__ void __launch_bounds__(kTreeThreads, 2) k_tree_fused(const __grid_con
             const unsigned long long sum = warp_sum_u64(0xffffffffu, on ? static_cast<unsigned long long>(mv[m]) : 0ull);
             if (lane == lead && sum != 0ull) red_add_u64(d.H + c0 + m, static_cast<long long>(sum));
           }
+        } else if (on && bulk) {  // the row's record added to its 32-byte cell in one reduction
+          asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], 32;" ::"l"(d.H + cell),
+                       "r"(static_cast<uint32_t>(__cvta_generic_to_shared(&stage[threadIdx.x][0])))
+                       : "memory");
         } else if (on) {
 #pragma unroll
           for (int m = 0; m < kTreeMaxMom; ++m) {
@@ -603,8 +618,10 @@ __global__ void __launch_bounds__(kTreeThreads, 2) k_tree_fused(const __grid_con
           }
         }
       }
+      if (bulk) asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
   }
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 __global__ void k_tree_out(const __grid_constant__ TreeDev d, const TreeOut* outs, int n, long long* res_i64,
@@ -613,12 +630,12 @@ __global__ void k_tree_out(const __grid_constant__ TreeDev d, const TreeOut* out
   if (k >= n) return;
   const TreeOut o = outs[k];
   const int nb = d.thr_off[o.split + 1] - d.thr_off[o.split] + 1;
-  const long long* h = d.H + ((int64_t)o.node * d.n_split + o.split) * d.max_bins * d.n_mom + o.mom;
+  const long long* h = d.H + ((int64_t)o.node * d.n_split + o.split) * d.max_bins * d.mom_stride + o.mom;
   long long s = 0;
   if (o.op == 0) {
-    for (int b = 0; b <= o.j; ++b) s += h[(int64_t)b * d.n_mom];
+    for (int b = 0; b <= o.j; ++b) s += h[(int64_t)b * d.mom_stride];
   } else {
-    for (int b = o.j + 1; b < nb; ++b) s += h[(int64_t)b * d.n_mom];
+    for (int b = o.j + 1; b < nb; ++b) s += h[(int64_t)b * d.mom_stride];
   }
   if (o.is_count) res_i64[o.dst] = s;
   else res_f64[o.dst] = static_cast<double>(s) * o.inv_scale;
@@ -684,7 +701,7 @@ cudaError_t tree_autotune(TreePlan* tp, const RootParams& rp, cudaStream_t s) {
   cudaEventCreate(&b);
   float best = 1e30f;
   TreeShape pick = T.shape;
-  const size_t hbytes = static_cast<size_t>(T.dev.n_nodes) * T.dev.n_split * T.max_bins * T.dev.n_mom * 8;
+  const size_t hbytes = static_cast<size_t>(T.dev.n_nodes) * T.dev.n_split * T.max_bins * T.dev.mom_stride * 8;
   for (const auto& c : cand) {
     cudaMemsetAsync(T.dev.H, 0, hbytes, s);
     cudaEventRecord(a, s);
