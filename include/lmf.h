@@ -84,6 +84,9 @@ typedef int32_t lmf_status;
 #define LMF_ROOT_EXPLICIT    1   /* lmf_plan_opts.root_rel */
 #define LMF_ROOT_HEURISTIC   2   /* the root rule of Sec. 3.3: largest total group-by
                                     weight, ties to the largest relation */
+#define LMF_ROOT_PER_QUERY   3   /* per-query roots (Sec. 3.3): the declared root when the
+                                    whole batch evaluates there, else the aggregates grouped by
+                                    a root each (see lmf_plan) */
 
 #define LMF_MAX_GROUP_BY 3
 #define LMF_MAX_FACTORS  16
@@ -176,6 +179,10 @@ typedef struct {
   int32_t resident_cells;     /* shared-memory counters of the resident-key tables */
   int32_t jit;                /* 1: the root scan runs a kernel compiled for this plan */
   int32_t key_level;          /* 1: key-level Gram blocks (see LMF_PLAN_ROW_GRAM) */
+  int32_t n_roots;            /* roots the batch is evaluated at (LMF_ROOT_PER_QUERY), else 1;
+                                 with several, the other fields describe the first root's
+                                 plan, except the aggregate, view and kernel totals and
+                                 root_rel = -1 */
 } lmf_plan_stats;
 
 /*
@@ -245,9 +252,18 @@ lmf_status lmf_declare_batch(lmf_ctx* ctx, const lmf_agg_spec* aggs, int n, int*
  * scan's form and tiles, allocate all device buffers, and measure value
  * ranges of the columns the batch reads (for the exact fixed-point
  * accumulators).  opts may be NULL (defaults: split-bf16 Gram, graph batching).
+ * With root_mode LMF_ROOT_PER_QUERY a batch that does not evaluate at the
+ * declared root (a group-by or threshold attribute reached through a
+ * fanning-out key, Sec. 3.3's per-query roots) is split: aggregates are
+ * grouped by the relation holding their first such attribute (the declared
+ * root for sums of monomials), each group planned at the first root that evaluates
+ * it -- its own attribute's relation, the declared root, then the largest
+ * relations -- and every run runs each group's plan and copies its results
+ * into this batch's layout (lmf_plan_info reports n_roots).
  * Errors: LMF_ERR_UNSUPPORTED for aggregate shapes outside this engine
- * (e.g. group-by attributes reached through a non-unique key, degree-2
- * monomials under a group-by), LMF_ERR_OOM, LMF_ERR_CUDA.
+ * (e.g. group-by attributes reached through a non-unique key without
+ * LMF_ROOT_PER_QUERY, degree-2 monomials under a group-by), LMF_ERR_OOM,
+ * LMF_ERR_CUDA.
  */
 lmf_status lmf_plan(lmf_ctx* ctx, int batch_id, const lmf_plan_opts* opts);
 
@@ -323,7 +339,7 @@ lmf_status lmf_read_result(lmf_ctx* ctx, int batch_id, int agg, void* dst);
 /* ---------------------------------------------------------------------------
  * Plan choice.  The paper picks the root of each query by a weight rule
  * (Sec. 3.3).  This engine adds a learned cost model over candidate plans
- * (root, precision, CTAs per SM, view merging); the rule stays the fallback
+ * (root and Gram form); the rule stays the fallback
  * and the reference its regret is measured against.
  * ------------------------------------------------------------------------- */
 
@@ -338,8 +354,8 @@ lmf_status lmf_read_result(lmf_ctx* ctx, int batch_id, int agg, void* dst);
 /*
  * Candidate plans for a declared batch: up to three roots (the declared one,
  * the Sec. 3.3 rule's one, the largest relations) x Gram form (plain FP32 with
- * key-level blocks, plain FP32 all at the row level, split bf16) x view
- * merging, each as explicit plan options derived from *base (NULL: zero
+ * key-level blocks, plain FP32 all at the row level, split bf16), views merged
+ * per parent key, each as explicit plan options derived from *base (NULL: zero
  * options; its CTAs per SM and compile flag carry over).  Writes
  * min(max, count) entries to out (may be NULL) and the count to *n.
  * Errors: LMF_ERR_ARG (null n), LMF_ERR_STATE before lmf_declare_join.

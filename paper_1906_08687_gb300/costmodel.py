@@ -1,7 +1,7 @@
 """Learned plan choice for the engine: timing corpus, training, regret.
 
-The planner's candidates for a batch (lmf_plan_candidates: roots x Gram form x
-view merging) are each planned, compiled and timed on the GPU; the cost
+The planner's candidates for a batch (lmf_plan_candidates: roots x Gram form)
+are each planned, compiled and timed on the GPU; the cost
 model (lmf_mlp, trained here with the engine's own forward/backward/Adam
 kernels) learns log run time from the plan features; on held-out schemas its
 choice is compared with the exhaustive best and with the paper's root rule

@@ -213,6 +213,11 @@ struct Plan {
   T* at(size_t off) const { return reinterpret_cast<T*>(arena.base + off); }
   // device resources of the plan; a plan that fails half-way releases what it
   // had allocated when it is dropped
+  // per-query roots (LMF_ROOT_PER_QUERY): the hidden batches, each planned at
+  // its own root, whose results this plan's arrays collect
+  std::vector<int> subs;
+  std::vector<ResultCopy> copies;
+  size_t copies_off = 0;
   void release() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -861,6 +866,7 @@ int heuristic_root(lmf_ctx* c, const BatchH& B) {
 }
 
 lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, int root);
+lmf_status plan_per_query(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts);
 
 }  // namespace
 
@@ -889,6 +895,8 @@ extern "C" lmf_status lmf_plan(lmf_ctx* c, int batch_id, const lmf_plan_opts* op
       if (s == LMF_ERR_UNSUPPORTED && r != c->root) s = plan_with_root(c, batch_id, o, c->root);
       return s;
     }
+    case LMF_ROOT_PER_QUERY:
+      return plan_per_query(c, batch_id, o);
     default:
       return fail(c, LMF_ERR_ARG, "plan: root_mode %d", o.root_mode);
   }
@@ -2189,6 +2197,142 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
 
 namespace {
 
+// Per-query roots (Sec. 3.3: every query evaluated at a root of its own, with
+// the directional views towards that root).  The whole batch at the declared
+// root when it plans there; otherwise its aggregates are grouped by the root
+// they are tried at first -- the relation holding the first group-by,
+// threshold or power attribute (where a group-by category is a column of the
+// root itself), the declared root for plain linear sums -- each group planned
+// as a hidden batch at the first of its candidate roots that evaluates it
+// (single aggregates when a group fits none), and this batch's plan becomes
+// the place their results are copied to after every run.
+lmf_status plan_per_query(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts) {
+  {  // the hidden batches of an earlier per-query plan of this batch give back their memory
+    BatchH& B0 = *c->batches[batch_id];
+    if (B0.plan)
+      for (int id : B0.plan->subs) c->batches[id]->plan.reset();
+  }
+  lmf_plan_opts o = opts;
+  o.root_mode = LMF_ROOT_EXPLICIT;
+  o.root_rel = c->root;
+  lmf_status s = plan_with_root(c, batch_id, o, c->root);
+  if (s != LMF_ERR_UNSUPPORTED) return s;
+  BatchH& B = *c->batches[batch_id];
+  const int n = (int)B.aggs.size();
+  std::vector<int> by_size(c->rels.size());
+  for (size_t r = 0; r < by_size.size(); ++r) by_size[r] = (int)r;
+  std::stable_sort(by_size.begin(), by_size.end(),
+                   [&](int a, int b) { return c->rels[a].nrows > c->rels[b].nrows; });
+  auto candidates = [&](const AggH& a) {
+    std::vector<int> out;
+    auto add = [&](int r) {
+      if (r >= 0 && std::find(out.begin(), out.end(), r) == out.end()) out.push_back(r);
+    };
+    int col = 0;
+    for (auto& g : a.gb) add(owner_of(c, g, &col));
+    for (auto& f : a.f)
+      if (f.kind != LMF_POW) add(owner_of(c, f.attr, &col));
+    add(c->root);
+    for (int r : by_size) add(r);
+    return out;
+  };
+  // groups keyed by the candidate list, in order of first appearance
+  std::vector<std::vector<int>> keys;
+  std::vector<std::vector<int>> members;
+  for (int a = 0; a < n; ++a) {
+    auto k = candidates(B.aggs[a]);
+    size_t g = 0;
+    while (g < keys.size() && keys[g] != k) ++g;
+    if (g == keys.size()) {
+      keys.push_back(k);
+      members.emplace_back();
+    }
+    members[g].push_back(a);
+  }
+  std::vector<int> subs;
+  std::vector<std::pair<int, int>> where(n, {-1, -1});  // aggregate -> (hidden batch, index in it)
+  auto plan_group = [&](const std::vector<int>& aggs, const std::vector<int>& cand) -> lmf_status {
+    const int id = (int)c->batches.size();
+    auto hb = std::make_unique<BatchH>();
+    for (int a : aggs) hb->aggs.push_back(B.aggs[a]);
+    c->batches.push_back(std::move(hb));
+    lmf_status st = LMF_ERR_UNSUPPORTED;
+    for (int r : cand) {
+      lmf_plan_opts q = o;
+      q.root_rel = r;
+      st = plan_with_root(c, id, q, r);
+      if (st != LMF_ERR_UNSUPPORTED) break;
+    }
+    if (st != LMF_OK) {
+      c->batches.pop_back();
+      return st;
+    }
+    for (size_t j = 0; j < aggs.size(); ++j) where[aggs[j]] = {id, (int)j};
+    subs.push_back(id);
+    return LMF_OK;
+  };
+  for (size_t g = 0; g < keys.size(); ++g) {
+    lmf_status st = plan_group(members[g], keys[g]);
+    if (st == LMF_ERR_UNSUPPORTED && members[g].size() > 1) {
+      for (int a : members[g]) {
+        st = plan_group({a}, keys[g]);
+        if (st) return fail(c, st, "aggregate %d fits no root", a);
+      }
+    } else if (st) {
+      return st;
+    }
+  }
+  // this batch's plan: the result arrays in the batch's layout and the copies
+  auto P = std::make_unique<Plan>();
+  P->opts = opts;
+  P->root = c->root;
+  P->subs = subs;
+  P->agg_dtype.resize(n);
+  P->agg_off.resize(n);
+  P->agg_n.resize(n);
+  for (int a = 0; a < n; ++a) {
+    const Plan& S = *c->batches[where[a].first]->plan;
+    const int j = where[a].second;
+    P->agg_dtype[a] = S.agg_dtype[j];
+    P->agg_n[a] = S.agg_n[j];
+    if (S.agg_dtype[j] == LMF_I64) {
+      P->agg_off[a] = P->n_i64;
+      P->n_i64 += S.agg_n[j];
+    } else {
+      P->agg_off[a] = P->n_f64;
+      P->n_f64 += S.agg_n[j];
+    }
+  }
+  Arena& A = P->arena;
+  P->status_off = A.take(16);
+  P->res_i64_off = A.take((size_t)std::max<int64_t>(1, P->n_i64) * 8);
+  P->res_f64_off = A.take((size_t)std::max<int64_t>(1, P->n_f64) * 8);
+  P->copies_off = A.take(sizeof(ResultCopy) * (size_t)std::max(1, n));
+  A.size = A.used + 256;
+  {
+    void* base = nullptr;
+    if (cudaMalloc(&base, A.size) != cudaSuccess) return fail(c, LMF_ERR_OOM, "per-query result arrays");
+    A.base = static_cast<char*>(base);
+  }
+  CUDA_TRY(c, cudaMemset(A.base, 0, A.size));
+  for (int a = 0; a < n; ++a) {
+    const Plan& S = *c->batches[where[a].first]->plan;
+    const int j = where[a].second;
+    const bool i64 = S.agg_dtype[j] == LMF_I64;
+    ResultCopy rc;
+    rc.src = reinterpret_cast<const long long*>(S.arena.base + (i64 ? S.res_i64_off : S.res_f64_off)) + S.agg_off[j];
+    rc.dst = reinterpret_cast<long long*>(A.base + (i64 ? P->res_i64_off : P->res_f64_off)) + P->agg_off[a];
+    rc.n = S.agg_n[j];
+    P->copies.push_back(rc);
+  }
+  CUDA_TRY(c, cudaMemcpy(A.base + P->copies_off, P->copies.data(), sizeof(ResultCopy) * P->copies.size(),
+                         cudaMemcpyHostToDevice));
+  for (int id : subs) P->n_kernels += c->batches[id]->plan->n_kernels;
+  P->n_kernels += 1;
+  B.plan = std::move(P);
+  return LMF_OK;
+}
+
 // ev (optional): LMF_STAGES + 1 events recorded on s at the stage boundaries
 lmf_status enqueue(lmf_ctx* c, BatchH& B, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   Plan* P = B.plan.get();
@@ -2410,7 +2554,25 @@ lmf_status lmf_plan_info(lmf_ctx* c, int batch_id, lmf_plan_stats* info) {
   if (!c || !info || batch_id < 0 || batch_id >= (int)c->batches.size()) return LMF_ERR_ARG;
   Plan* P = c->batches[batch_id]->plan.get();
   if (!P) return fail(c, LMF_ERR_STATE, "batch not planned");
+  if (!P->subs.empty()) {  // per-query roots: the first root's plan, with the totals of all
+    lmf_status st = lmf_plan_info(c, P->subs[0], info);
+    if (st) return st;
+    info->n_roots = (int32_t)P->subs.size();
+    info->n_kernels_per_run = P->n_kernels;
+    info->n_gram_aggs = info->n_grouped_aggs = info->n_filtered_aggs = 0;
+    info->n_views = 0;
+    for (int id : P->subs) {
+      const Plan& S = *c->batches[id]->plan;
+      info->n_gram_aggs += S.n_gram;
+      info->n_grouped_aggs += S.n_grouped;
+      info->n_filtered_aggs += S.n_filtered;
+      info->n_views += S.n_views;
+    }
+    info->root_rel = -1;
+    return LMF_OK;
+  }
   std::memset(info, 0, sizeof(*info));
+  info->n_roots = 1;
   info->n_views = P->n_views;
   info->n_probe_groups = P->rootp.n_grp;
   info->z_len = P->rootp.m;
@@ -2451,6 +2613,14 @@ lmf_status lmf_run(lmf_ctx* c, int batch_id, void* cuda_stream) {
   cudaSetDevice(c->device);
   cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
   B.last_stream = s;
+  if (!P->subs.empty()) {  // per-query roots: every root's plan, then the results copied in
+    for (int id : P->subs) {
+      lmf_status st = lmf_run(c, id, s);
+      if (st) return st;
+    }
+    CUDA_TRY(c, launch_copy_results(P->at<ResultCopy>(P->copies_off), (int)P->copies.size(), s));
+    return LMF_OK;
+  }
   {
     lmf_status st = ensure_tuned(c, B, s);
     if (st) return st;
@@ -2485,6 +2655,18 @@ lmf_status lmf_run_profiled(lmf_ctx* c, int batch_id, void* cuda_stream, float* 
   cudaSetDevice(c->device);
   cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
   B.last_stream = s;
+  if (!B.plan->subs.empty()) {  // per-query roots: the stages summed over the roots' plans
+    for (int i = 0; i < LMF_STAGES; ++i) stage_ms[i] = 0.f;
+    for (int id : B.plan->subs) {
+      float st_ms[LMF_STAGES];
+      lmf_status st = lmf_run_profiled(c, id, s, st_ms);
+      if (st) return st;
+      for (int i = 0; i < LMF_STAGES; ++i) stage_ms[i] += st_ms[i];
+    }
+    CUDA_TRY(c, launch_copy_results(B.plan->at<ResultCopy>(B.plan->copies_off), (int)B.plan->copies.size(), s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    return LMF_OK;
+  }
   {
     lmf_status st = ensure_tuned(c, B, s);
     if (st) return st;
@@ -2530,6 +2712,10 @@ lmf_status lmf_sync(lmf_ctx* c, int batch_id) {
   Plan* P = B.plan.get();
   if (!P) return fail(c, LMF_ERR_STATE, "sync before plan");
   cudaSetDevice(c->device);
+  for (int id : P->subs) {  // per-query roots: each root's plan reports its own status
+    lmf_status st = lmf_sync(c, id);
+    if (st) return st;
+  }
   cudaStream_t s = B.last_stream ? B.last_stream : c->stream;
   uint32_t st = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&st, P->arena.base + P->status_off, sizeof(st), cudaMemcpyDeviceToHost, s));
@@ -2650,22 +2836,24 @@ std::vector<lmf_plan_opts> plan_candidates(lmf_ctx* c, const BatchH& B, const lm
     if (std::find(roots.begin(), roots.end(), r) == roots.end()) roots.push_back(r);
   }
   // Gram forms: plain FP32 with key-level blocks, plain FP32 all at the row
-  // level, split bf16 on the tensor cores
+  // level, split bf16 on the tensor cores.  Views stay merged per parent key
+  // (case (1) of Sec. 3.4): across the plan-choice corpus turning merging off
+  // changed no candidate's time by more than 1% (median ratio 1.000), while on
+  // a snowflake whose sub-dimensions share a key it costs a gather per view
   struct Form { int prec, flags; };
   const Form forms[] = {{LMF_PREC_PLAIN_FP32, 0}, {LMF_PREC_PLAIN_FP32, LMF_PLAN_ROW_GRAM},
                         {LMF_PREC_SPLIT_BF16, 0}};
   std::vector<lmf_plan_opts> out;
   for (int r : roots)
-    for (const Form& f : forms)
-      for (int nm : {0, 1}) {
-        lmf_plan_opts o = base;
-        o.root_mode = LMF_ROOT_EXPLICIT;
-        o.root_rel = r;
-        o.precision = f.prec;
-        o.flags = (base.flags & ~LMF_PLAN_ROW_GRAM) | f.flags;
-        o.no_merge = nm;
-        out.push_back(o);
-      }
+    for (const Form& f : forms) {
+      lmf_plan_opts o = base;
+      o.root_mode = LMF_ROOT_EXPLICIT;
+      o.root_rel = r;
+      o.precision = f.prec;
+      o.flags = (base.flags & ~LMF_PLAN_ROW_GRAM) | f.flags;
+      o.no_merge = 0;
+      out.push_back(o);
+    }
   return out;
 }
 
@@ -2697,6 +2885,7 @@ lmf_status lmf_plan_features(lmf_ctx* c, int batch_id, float* feat, int n) {
   if (!c || !feat || batch_id < 0 || batch_id >= (int)c->batches.size()) return LMF_ERR_ARG;
   Plan* P = c->batches[batch_id]->plan.get();
   if (!P) return fail(c, LMF_ERR_STATE, "features before plan");
+  if (!P->subs.empty()) return fail(c, LMF_ERR_STATE, "a per-query plan has no single set of features");
   if (n < kPlanFeatures) return fail(c, LMF_ERR_ARG, "need %d feature slots", kPlanFeatures);
   plan_features(c, *P, feat);
   return LMF_OK;

@@ -390,6 +390,13 @@ cudaError_t launch_fix_means(const FixMeans& f, cudaStream_t s);
 // grouped launches of the key-level tasks (shared-memory tables per block)
 cudaError_t launch_rv_items(const RvTask* tasks, const RvItem* items, int n_items, int max_cells,
                             const RootParams& p, cudaStream_t s);
+// one aggregate's results copied from a per-root plan into the batch's arrays
+struct ResultCopy {
+  const long long* src;              // int64 or float64 words (copied as bits)
+  long long* dst;
+  int64_t n;
+};
+cudaError_t launch_copy_results(const ResultCopy* items, int n_items, cudaStream_t s);
 cudaError_t launch_cat_index(const CatIndex* idx, int n_idx, int64_t max_K, const RootParams& p, cudaStream_t s);
 cudaError_t launch_cv_pairs(const CatViewTask* tasks, const CatIndex* idx, const CvPairItem* items, int n_items,
                             const RootParams& p, cudaStream_t s);

@@ -945,4 +945,17 @@ cudaError_t launch_out_map(const OutMap* maps, const OutItem* items, int n_items
   return cudaGetLastError();
 }
 
+// the results of per-root plans placed in the batch's result arrays: one block
+// per aggregate, 64-bit words copied as they are
+__global__ void k_copy_results(const ResultCopy* items) {
+  const ResultCopy it = items[blockIdx.x];
+  for (int64_t i = threadIdx.x; i < it.n; i += blockDim.x) it.dst[i] = it.src[i];
+}
+
+cudaError_t launch_copy_results(const ResultCopy* items, int n_items, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  k_copy_results<<<n_items, 256, 0, s>>>(items);
+  return cudaGetLastError();
+}
+
 }  // namespace lmf

@@ -23,7 +23,7 @@ LMF_KEY, LMF_CONT, LMF_CAT = 0, 1, 2
 LMF_POW, LMF_LE, LMF_GT = 0, 1, 2
 LMF_PREC_PLAIN_FP32, LMF_PREC_SPLIT_BF16 = 0, 1
 LMF_BATCH_SINGLE, LMF_BATCH_GRAPH = 0, 1
-LMF_ROOT_DECLARED, LMF_ROOT_EXPLICIT, LMF_ROOT_HEURISTIC = 0, 1, 2
+LMF_ROOT_DECLARED, LMF_ROOT_EXPLICIT, LMF_ROOT_HEURISTIC, LMF_ROOT_PER_QUERY = 0, 1, 2, 3
 LMF_MAX_GROUP_BY = 3
 LMF_STAGES = 5
 LMF_PLAN_FEATURES = 26
@@ -72,7 +72,7 @@ class lmf_plan_stats(ctypes.Structure):
                 ('tree_chunk', ctypes.c_int32),
                 ('root_rows', ctypes.c_int64), ('scratch_bytes', ctypes.c_int64),
                 ('resident_group', ctypes.c_int32), ('resident_cells', ctypes.c_int32),
-                ('jit', ctypes.c_int32), ('key_level', ctypes.c_int32)]
+                ('jit', ctypes.c_int32), ('key_level', ctypes.c_int32), ('n_roots', ctypes.c_int32)]
 
 
 class lmf_mi_pair(ctypes.Structure):

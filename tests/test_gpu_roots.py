@@ -74,3 +74,63 @@ def test_heuristic_root_rule():
     assert info['root_rel'] == 0
     fails, _ = compare(got, oracle.evaluate(sch, batch), arith_floor=ARITH_FLOOR)
     assert not fails
+
+
+# ----------------------------------------------------------------------------
+# per-query roots (LMF_ROOT_PER_QUERY)
+def test_chain_each_query_at_its_own_root():
+    """Sec. 3.3's chain S_1 ... S_{n-1} (many-to-many joins): Q_i = COUNT grouped
+    by X_i for every i.  From the declared root S_1 only Q_1 evaluates (X_2.. sit
+    behind fanning-out keys); with per-query roots each Q_i runs at a root
+    holding X_i and every count is bit-identical to the oracle's (the L_i R_i
+    products)."""
+    from workloads import Agg, chain_schema
+    n, size, dom = 6, 400, 7
+    sch = chain_schema(n, size, dom, seed=3, group_copies=True)
+    batch = [Agg(group_by=('X1',))] + [Agg(group_by=(f'G{i}',)) for i in range(2, n)] + [Agg(group_by=(f'X{n}',))]
+    want = oracle.evaluate(sch, batch)
+    got, info = _run(sch, batch, precision=0, batching=1, root_mode=3)
+    assert info['n_roots'] >= n - 1
+    for i, (g, w) in enumerate(zip(got, want.values)):
+        assert np.array_equal(np.asarray(g, np.int64), w), i
+    # the same batch from the declared root alone is refused
+    from paper_1906_08687_gb300 import LmfError
+    with pytest.raises(LmfError):
+        _run(sch, batch, precision=0, batching=1, root_mode=0)
+
+
+@pytest.mark.parametrize('seed', [0, 1, 3, 4, 6, 7])
+def test_tiny_fanout_grouped_per_query(seed):
+    """Tiny schemas with duplicate child keys and dangling foreign keys: the
+    covar batch plus COUNT and SUM(x) grouped by every category, categories
+    behind fanning-out keys included, evaluated with per-query roots, against
+    the oracle (counts bit-exact, sums within the error rule with the small-input
+    floor); twice in a row (the per-root plans and the result copies repeat)."""
+    from workloads import grouped_batch
+    sch, _ = tiny_schema(5000 + seed, unique_keys=False)
+    feats, cats = sch.meta['features'], sch.meta['cats']
+    batch = covar_batch(feats) + grouped_batch(cats, feats)
+    want = oracle.evaluate(sch, batch)
+    from paper_1906_08687_gb300 import Engine, register_schema
+    from lmf_testlib import to_device
+    eng = Engine(0)
+    tens = to_device(sch)
+    register_schema(eng, sch, tens)
+    bid = eng.declare_batch(batch)
+    eng.plan(bid, precision=0, batching=1, root_mode=3)
+    for _ in range(2):
+        eng.run(bid)
+        eng.sync(bid)
+        got = eng.results(bid, len(batch))
+        fails, stats = compare(got, want, arith_floor=ARITH_FLOOR)
+        assert not fails, (fails[:3], stats, eng.plan_info(bid))
+    eng.close()
+
+
+def test_per_query_keeps_a_batch_that_fits_the_declared_root():
+    """A batch the declared root evaluates is planned there as one plan."""
+    sch, batch = config1(20_000)
+    got, info = _run(sch, batch, precision=0, batching=1, root_mode=3)
+    assert info['n_roots'] == 1 and info['root_rel'] == 0
+    fails, stats = compare(got, oracle.evaluate(sch, batch), arith_floor=ARITH_FLOOR)
+    assert not fails, (fails[:3], stats)

@@ -304,6 +304,13 @@ def test_chain_example_left_right_views():
     assert res.join_size == size_bf
     for i in range(n):
         assert np.array_equal(res.values[i], want[i])
+    # the categorical copies G_i of the join attributes (the per-query-root
+    # GPU tests group by them) give the same L_i * R_i counts
+    sch_g = chain_schema(n, size, dom, seed=11, group_copies=True)
+    batch_g = [Agg(group_by=(f'G{i}',)) for i in range(2, n)]
+    res_g = oracle.evaluate(sch_g, batch_g)
+    for i in range(2, n):
+        assert np.array_equal(res_g.values[i - 2], (L[i] * R[i]).astype(np.int64)), i
 
 
 # ----------------------------------------------------------------------------

@@ -515,10 +515,12 @@ def tiny_schema(seed: int, max_rel: int = 4, max_rows: int = 9, unique_keys: boo
     return sch, batch
 
 
-def chain_schema(n: int, size: int, dom: int, seed: int) -> Schema:
+def chain_schema(n: int, size: int, dom: int, seed: int, group_copies: bool = False) -> Schema:
     """The chain join S_1(X_1,X_2), ..., S_{n-1}(X_{n-1},X_n) of Sec. 3.3 with
     `size` random tuples per relation over a domain of `dom` values.  The
-    tree is rooted at S_1; S_k is joined to S_{k+1} on X_{k+1}."""
+    tree is rooted at S_1; S_k is joined to S_{k+1} on X_{k+1}.  group_copies:
+    S_k (k >= 2) also carries G{k}, a categorical copy of its join attribute
+    X_k, so that Q_k(X_k; COUNT) can be declared as COUNT grouped by G{k}."""
     rng = _rng(seed)
     rels = []
     edges = []
@@ -529,6 +531,8 @@ def chain_schema(n: int, size: int, dom: int, seed: int) -> Schema:
         # S_k's left attribute is the join key towards S_{k-1}
         cols.append(Column(f'X{k}', 'key' if k > 1 else 'cat', a, dom))
         cols.append(Column(f'X{k + 1}', 'key' if k < n - 1 else 'cat', b, dom))
+        if group_copies and k > 1:
+            cols.append(Column(f'G{k}', 'cat', a.copy(), dom))
         rels.append(Relation(f'S{k}', cols))
         if k > 1:
             edges.append((f'S{k - 1}', f'S{k}', f'X{k}'))
