@@ -543,11 +543,22 @@ std::string jit_lean_source(const RootParams& rp, const std::vector<DirectAgg>& 
     o << "    const long long fres = -2ll;\n";
   o << "    __syncwarp();  // the warp's rows are in shared memory\n";
   gen_grouped(o, rp, direct, [](int i) { return "c" + std::to_string(i); });
-  // reverse views summed in warps
+  // reverse views summed in warps.  One view in runs whose record is the
+  // first columns of the tile row (at most 32 words) is reduced in place, after
+  // every other reader of the tile: each run's sums are written into the run's
+  // last row and that row's thread adds the record with one bulk reduction
+  int inplace = -1;
+  for (int r = 0; r < rp.n_rv && inplace < 0; ++r) {
+    const RevView& R = rp.rv[r];
+    if (R.mode != kRvRuns || 1 + R.n_slot > 32 || R.stride > L.zi_ld) continue;
+    bool prefix = true;
+    for (int sl = 0; sl < R.n_slot && prefix; ++sl) prefix = L.col_of_z[R.slot_z[sl]] == 1 + sl;
+    if (prefix) inplace = r;
+  }
   for (int r = 0; r < rp.n_rv; ++r) {
     const RevView& R = rp.rv[r];
     const int nw = 1 + R.n_slot;
-    if (R.mode == kRvBulk) continue;
+    if (R.mode == kRvBulk || r == inplace) continue;
     o << "    {  // reverse view " << r << (R.mode == kRvResident ? " (resident key)" : " (runs)") << "\n"
       << "      const long long fk = live ? static_cast<long long>(fk" << R.grp << ") : -1ll;\n"
       << "      const WarpRuns q = warp_runs(fk);\n"
@@ -564,6 +575,20 @@ std::string jit_lean_source(const RootParams& rp, const std::vector<DirectAgg>& 
       o << "      }\n";
     }
     o << "    }\n";
+  }
+  if (inplace >= 0) {
+    const RevView& R = rp.rv[inplace];
+    o << "    {  // reverse view " << inplace << " (runs, reduced in place)\n"
+      << "      const long long fk = live ? static_cast<long long>(fk" << R.grp << ") : -1ll;\n"
+      << "      const WarpRuns q = warp_runs(fk);\n"
+      << "      lean_bulk_wait_read();  // this row's earlier bulk reductions have read the tile row\n"
+      << "      __syncwarp();\n"
+      << "      lean_rv_inplace(q, zi - lane * kZiLd, kZiLd, lane, lane < " << 1 + R.n_slot << ");\n"
+      << "      __syncwarp();\n"
+      << "      if (fk >= 0 && (lane == 31 || ((q.heads >> (lane + 1)) & 1u)))\n"
+      << "        lean_bulk_add(reinterpret_cast<unsigned long long*>(p.rv[" << inplace << "].hist) + fk * " << R.stride
+      << ", reinterpret_cast<const unsigned long long*>(zi), " << R.stride * 8 << ");\n"
+      << "    }\n";
   }
   o << "    (void)lane;\n    (void)fres;\n    (void)stage;\n    (void)racc;\n    (void)cache;\n    (void)crow;\n"
        "    (void)zrow;\n    return w;\n  }\n";

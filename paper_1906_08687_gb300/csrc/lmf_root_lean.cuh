@@ -20,7 +20,10 @@
 // updates (RevView::mode), record [K][stride] int64, word 0 the count, word
 // 1 + s slot s:
 //   runs      rows sorted on the key (runs of equal keys in a warp): lane w
-//             sums word w over each run and issues one reduction per run;
+//             sums word w over each run and issues one reduction per run; or,
+//             when the record is the first columns of the tile row, writes
+//             the run's sums into the run's last row, whose thread adds the
+//             whole record with one bulk reduction;
 //   resident  the CTA's resident key (the first sort attribute of the root,
 //             the outer loop of the trie scan of Sec. 3.5): when a warp's 32
 //             rows all carry it, lane w adds the warp's sum of word w to a
@@ -94,6 +97,23 @@ __device__ __forceinline__ void lean_rv_runs(const WarpRuns& q, long long fk, co
     if (j == 31 || ((q.heads >> (j + 1)) & 1u)) {  // row j ends a run (warp-uniform)
       const long long kj = __shfl_sync(kFullWarp, fk, j);
       if (on && kj >= 0 && acc != 0) lean_red_u64(rec0 + kj * stride + w, static_cast<unsigned long long>(acc));
+      acc = 0;
+    }
+  }
+}
+
+// run sums of column col written in place: the sum over each run of equal
+// keys replaces the column's value in the run's last row (the rows are the
+// warp's own, each lane reads and writes only its column); every lane of the
+// warp calls this
+__device__ __forceinline__ void lean_rv_inplace(const WarpRuns& q, long long* ziw, int ld, int col, bool on) {
+  if (!on) return;
+  long long acc = 0;
+#pragma unroll 8
+  for (int j = 0; j < 32; ++j) {
+    acc += ziw[j * ld + col];
+    if (j == 31 || ((q.heads >> (j + 1)) & 1u)) {  // row j ends a run
+      ziw[j * ld + col] = acc;
       acc = 0;
     }
   }
