@@ -35,5 +35,10 @@ def test_profiled_traffic_follows_the_kernel_sources():
         path = os.path.join(bench.ROOT, 'profiles', summary)
         assert os.path.exists(path), name
         with open(path) as f:
-            assert 'traffic_bytes_per_launch[plain]' in f.read()
+            text = f.read()
+        # a traffic figure with its source hash, or a statement that there is none
+        assert 'traffic_bytes_per_launch[' in text or '`traffic` as null' in text, name
     assert bench.profiled_traffic('plain', os.path.join(bench.ROOT, 'profiles', 'no_such.md')) is None
+    # the headline workload's summary was taken on the current kernel sources
+    snow = os.path.join(bench.ROOT, 'profiles', bench.WORKLOADS['snowflake'][6])
+    assert bench.profiled_traffic('keylevel', snow) is not None
