@@ -1104,6 +1104,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
     }
   }
 
+  const int sorted_q = res_grp;  // the first sort key's probe group (-1: the root is not sorted so)
   // ---- key-level form (lmf_root_lean.cuh): every child key unique, plain
   // precision, a compiled scan, at least one probe group and one feature, and
   // some foreign key in runs (on a root in no useful order every reverse-view
@@ -1588,7 +1589,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
       gplan[a].res_off = res_cells;
       res_cells += gplan[a].res_n * (gplan[a].res_lanes ? 32 : 1);
     }
-    if (res_cells == 0 && !P->lean) res_grp = -1;
+    if (res_cells == 0 && !P->lean) res_grp = -1;  // (sorted_q keeps it for the tree pass)
   }
 
   // ---- hot-cell cache: per CTA, the hottest (value, value) cells of every
@@ -2128,7 +2129,7 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
   if (P->tree) {
     lmf_status s = tree_finish(P->tree.get(), P->arena.base, P->at<long long>(P->res_i64_off),
                                P->at<double>(P->res_f64_off), P->agg_off, filt_idx, P->agg_dtype,
-                               P->at<uint32_t>(P->status_off), Root.nrows, c->num_sms, bound, W, rp);
+                               P->at<uint32_t>(P->status_off), Root.nrows, c->num_sms, bound, W, rp, sorted_q);
     if (s) return fail(c, s, "tree plan: device tables");
   }
   if (use_tc) {

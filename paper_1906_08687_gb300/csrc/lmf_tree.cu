@@ -41,6 +41,7 @@
 namespace lmf {
 
 constexpr int kTreeMaxMom = 8;
+constexpr int kTreeResNodes = 256;  // nodes whose resident-key sums fit the shared table
 constexpr uint16_t kNoNode = 0xFFFF;
 
 struct TreePred {
@@ -73,6 +74,11 @@ struct TreeDev {
   const int32_t* droot;        // [n_groups]
   const struct TreeDt* dt;
   const int32_t* dcand;
+  // splits on an attribute of the resident key's dimension (the root's first
+  // sort key, Sec. 3.5): bit f of res_mask; their cells are summed per
+  // (node, key) in shared memory and added once per key (res_q: the probe group, -1: none)
+  int32_t res_q;
+  unsigned long long res_mask;
   long long* H;                // [n_nodes][n_split][max_bins][mom_stride]
   int64_t N;
   uint32_t* status;
@@ -386,10 +392,18 @@ void tree_alloc(TreePlan* tp, int64_t /*N*/, const std::function<size_t(size_t)>
 lmf_status tree_finish(TreePlan* tp, char* base, long long* res_i64, double* res_f64,
                        const std::vector<int64_t>& agg_off, const std::vector<int>& filt_idx,
                        const std::vector<int32_t>& agg_dtype, uint32_t* status, int64_t N, int num_sms,
-                       const std::map<std::string, double>& bound, double W, const RootParams& /*rp*/) {
+                       const std::map<std::string, double>& bound, double W, const RootParams& rp, int res_q) {
   TreePlanImpl& T = *tp->impl;
   T.num_sms = num_sms;
   TreeDev& D = T.dev;
+  D.res_q = -1;
+  D.res_mask = 0ull;
+  if (res_q >= 0 && res_q < rp.n_grp && D.n_nodes <= kTreeResNodes && D.n_mom <= 4 && D.n_split <= 64) {
+    const int z0 = rp.grp_zoff[res_q], z1 = z0 + rp.grp[res_q].n_mu;
+    for (int f = 0; f < D.n_split; ++f)
+      if (T.split_z[f] >= z0 && T.split_z[f] < z1) D.res_mask |= 1ull << f;
+    if (D.res_mask) D.res_q = res_q;
+  }
   D.N = N;
   D.status = status;
   D.H = reinterpret_cast<long long*>(base + T.H_off);
@@ -548,22 +562,69 @@ __global__ void __launch_bounds__(kTreeThreads, 2) k_tree_fused(const __grid_con
   float* zrow = Z + threadIdx.x * (MP + 1);  // odd stride: no bank conflicts
   int32_t* crow = C + threadIdx.x * ncat;
   const int lane = threadIdx.x & 31;
+  // the resident key's sums per node, added to the histogram once per key
+  __shared__ unsigned long long racc[kTreeResNodes][4];
+  const bool resident = d.res_q >= 0;
+  const GroupDesc& RG = p.grp[resident ? d.res_q : 0];
+  long long res_key = -1;
+  for (int i = threadIdx.x; i < kTreeResNodes * 4; i += blockDim.x) (&racc[0][0])[i] = 0ull;
+  // adds the resident key's sums to their cells (one per node and resident
+  // split) and clears them; every thread of the CTA calls this
+  auto res_flush = [&]() {
+    __syncthreads();
+    int nres = 0;
+    int fres[64];
+    for (int f = 0; f < d.n_split && f < 64; ++f)
+      if ((d.res_mask >> f) & 1ull) fres[nres++] = f;
+    if (res_key >= 0)
+      for (int e = threadIdx.x; e < d.n_nodes * nres; e += blockDim.x) {
+        const int n = e / nres, f = fres[e % nres];
+        if (racc[n][0] == 0ull && racc[n][1] == 0ull && racc[n][2] == 0ull && racc[n][3] == 0ull) continue;
+        const int zf = d.split_z[f];
+        const float x = __uint_as_float(RG.rec[res_key * RG.stride + RG.n_cnt + (zf - p.grp_zoff[d.res_q])]);
+        const int t0 = d.thr_off[f];
+        int l = 0, h = d.thr_off[f + 1] - t0;
+        while (l < h) {
+          const int mid = (l + h) >> 1;
+          if (thr[t0 + mid] < x) l = mid + 1;
+          else h = mid;
+        }
+        const int64_t cell = ((static_cast<int64_t>(n) * d.n_split + f) * d.max_bins + l) * d.mom_stride;
+        for (int m = 0; m < d.n_mom; ++m)
+          if (racc[n][m] != 0ull) red_add_u64(d.H + cell + m, static_cast<long long>(racc[n][m]));
+      }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTreeResNodes * 4; i += blockDim.x) (&racc[0][0])[i] = 0ull;
+    __syncthreads();
+  };
   __syncthreads();
-  const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  // every lane of a warp runs every iteration (warp reductions below), rows
-  // past the end are inactive
-  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < d.N; base += step) {
+  // each CTA a contiguous range of rows (the resident key changes rarely
+  // inside it); every lane of a warp runs every iteration (warp reductions
+  // below), rows past the range are inactive
+  const int64_t r_begin = static_cast<int64_t>(blockIdx.x) * d.N / gridDim.x;
+  const int64_t r_end = (static_cast<int64_t>(blockIdx.x) + 1) * d.N / gridDim.x;
+  for (int64_t base = r_begin; base < r_end; base += blockDim.x) {
+    if (resident) {  // CTA-uniform: the key of the chunk's first row
+      const int32_t k0 = RG.fk[base];
+      const long long nk = (k0 >= 0 && k0 < RG.K) ? k0 : -1;
+      if (nk != res_key) {
+        res_flush();
+        res_key = nk;
+      }
+    }
     const int64_t row = base + threadIdx.x;
     long long w = 0;
-    if (row < d.N) w = root_row_z<MP>(p, row, zrow, crow);
+    if (row < r_end) w = root_row_z<MP>(p, row, zrow, crow);
+    // the row's cells of resident splits go to the shared sums
+    const bool row_res = resident && w != 0 && res_key >= 0 && static_cast<long long>(RG.fk[row]) == res_key;
     long long mv[kTreeMaxMom];
     bool have = false;
     for (int g = 0; g < d.n_groups; ++g) {
       const int n = w != 0 ? tree_node_of(d, g, zrow) : static_cast<int>(kNoNode);
-      const bool on = n != static_cast<int>(kNoNode);
-      const unsigned on_mask = __ballot_sync(0xffffffffu, on);
+      const bool on_g = n != static_cast<int>(kNoNode);
+      const unsigned on_mask = __ballot_sync(0xffffffffu, on_g);
       if (on_mask == 0u) continue;  // warp-uniform
-      if (on && !have) {  // the row's fixed-point moments, once
+      if (on_g && !have) {  // the row's fixed-point moments, once
 #pragma unroll
         for (int m = 0; m < kTreeMaxMom; ++m) {
           if (m >= d.n_mom) break;
@@ -584,8 +645,12 @@ __global__ void __launch_bounds__(kTreeThreads, 2) k_tree_fused(const __grid_con
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
       }
-      const int lead = __ffs(on_mask) - 1;
+      if (on_g && row_res)
+        for (int m = 0; m < d.n_mom && m < 4; ++m)
+          if (mv[m] != 0) atomicAdd(&racc[n][m], static_cast<unsigned long long>(mv[m]));
       for (int f = 0; f < d.n_split; ++f) {
+        // a resident split of a row with the resident key is in the shared sums
+        const bool on = on_g && !(row_res && f < 64 && ((d.res_mask >> f) & 1ull));
         int64_t cell = 0;
         if (on) {
           const float x = zrow[d.split_z[f]];
@@ -598,13 +663,16 @@ __global__ void __launch_bounds__(kTreeThreads, 2) k_tree_fused(const __grid_con
           }
           cell = ((static_cast<int64_t>(n) * d.n_split + f) * d.max_bins + l) * d.mom_stride;
         }
-        const int64_t c0 = __shfl_sync(0xffffffffu, cell, lead);
+        const unsigned f_mask = __ballot_sync(0xffffffffu, on);
+        if (f_mask == 0u) continue;  // warp-uniform
+        const int f_lead = __ffs(f_mask) - 1;
+        const int64_t c0 = __shfl_sync(0xffffffffu, cell, f_lead);
         if (__all_sync(0xffffffffu, !on || cell == c0)) {  // one cell for the whole warp
 #pragma unroll
           for (int m = 0; m < kTreeMaxMom; ++m) {
             if (m >= d.n_mom) break;
             const unsigned long long sum = warp_sum_u64(0xffffffffu, on ? static_cast<unsigned long long>(mv[m]) : 0ull);
-            if (lane == lead && sum != 0ull) red_add_u64(d.H + c0 + m, static_cast<long long>(sum));
+            if (lane == f_lead && sum != 0ull) red_add_u64(d.H + c0 + m, static_cast<long long>(sum));
           }
         } else if (on && bulk) {  // the row's record added to its 32-byte cell in one reduction
           asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], 32;" ::"l"(d.H + cell),
@@ -621,6 +689,7 @@ __global__ void __launch_bounds__(kTreeThreads, 2) k_tree_fused(const __grid_con
       if (bulk) asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
   }
+  if (resident) res_flush();
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 

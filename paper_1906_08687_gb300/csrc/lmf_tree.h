@@ -42,7 +42,7 @@ lmf_status tree_finish(TreePlan* tp, char* base, long long* res_i64, double* res
                        const std::vector<int64_t>& agg_off, const std::vector<int>& filt_idx,
                        const std::vector<int32_t>& agg_dtype, uint32_t* status, int64_t N,
                        int num_sms, const std::map<std::string, double>& bound, double W,
-                       const RootParams& rp);
+                       const RootParams& rp, int res_q);
 cudaError_t tree_launch(TreePlan* tp, const RootParams& rp, cudaStream_t s, int* n_kernels);
 // The autotuner times the histogram pass over its shape candidates once the
 // per-row buffers hold a run's data, and keeps the fastest.
