@@ -49,8 +49,12 @@ WORKLOADS = {
     'chowliu': ('config4', 4, 50_000_000, 20_000_000, 500_000, -1, 'pair_counts_chowliu50M.md'),
     'star': ('config1', 1, 200_000, 200_000, 200_000, -1, None),
 }
-KERNEL_SOURCES = ['paper_1906_08687_gb300/csrc/lmf_tree.cu',
-                  'paper_1906_08687_gb300/csrc/lmf_kernels.cu',
+# the sources a traffic figure in a profile depends on: the root scan's kernels
+# (snowflake, Chow-Liu, star) or the tree pass's (tree)
+TREE_SOURCES = ['paper_1906_08687_gb300/csrc/lmf_tree.cu',
+                'paper_1906_08687_gb300/csrc/lmf_rowpass.cuh',
+                'paper_1906_08687_gb300/csrc/lmf_internal.h']
+KERNEL_SOURCES = ['paper_1906_08687_gb300/csrc/lmf_kernels.cu',
                   'paper_1906_08687_gb300/csrc/lmf_gram_tc.cu',
                   'paper_1906_08687_gb300/csrc/lmf_rowpass.cuh',
                   'paper_1906_08687_gb300/csrc/lmf_root_plain.cuh',
@@ -181,15 +185,15 @@ def measured_peaks() -> dict:
     return {'hbm_gbs': 6800.0, 'bf16_tflops': 1900.0, 'source': 'fallback'}
 
 
-def kernel_hash() -> str:
+def kernel_hash(sources=None) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in (KERNEL_SOURCES if sources is None else sources):
         with open(os.path.join(ROOT, f), 'rb') as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(precision: str, summary: str):
+def profiled_traffic(precision: str, summary: str, sources=None):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, when it was taken on the current kernel sources (else None)."""
     if not summary or not os.path.exists(summary):
@@ -197,7 +201,7 @@ def profiled_traffic(precision: str, summary: str):
     with open(summary) as f:
         text = f.read()
     m = re.search(rf'traffic_bytes_per_launch\[{precision}\]:\s*([0-9.e+]+)\s+sources:\s*([0-9a-f]+)', text)
-    if not m or m.group(2) != kernel_hash():
+    if not m or m.group(2) != kernel_hash(sources):
         return None
     return float(m.group(1))
 
@@ -521,7 +525,7 @@ def main():
     roof = {'bound': 'hbm', 'achieved': achieved, 'peak': peaks['hbm_gbs'], 'unit': 'GB/s',
             'frac': achieved / peaks['hbm_gbs'],
             'traffic': profiled_traffic('split' if prec == 1 else ('keylevel' if info['key_level'] else 'plain'),
-                                        args.profile),
+                                        args.profile, TREE_SOURCES if dom_stage == 'tree' else KERNEL_SOURCES),
             'peak_source': peaks['source'], 'kernel': f'{dom_stage} stage',
             'algorithmic_bytes_per_launch': algo, 'launch_ms': root_ms,
             'stage_ms': {n: float(v) for n, v in zip(STAGE_NAMES, stage)}}
