@@ -52,6 +52,8 @@ WORKLOADS = {
 # the sources a traffic figure in a profile depends on: the root scan's kernels
 # (snowflake, Chow-Liu, star) or the tree pass's (tree)
 TREE_SOURCES = ['paper_1906_08687_gb300/csrc/lmf_tree.cu',
+                'paper_1906_08687_gb300/csrc/lmf_tree_dev.cuh',
+                'paper_1906_08687_gb300/csrc/lmf_jit_tree.cu',
                 'paper_1906_08687_gb300/csrc/lmf_rowpass.cuh',
                 'paper_1906_08687_gb300/csrc/lmf_internal.h']
 KERNEL_SOURCES = ['paper_1906_08687_gb300/csrc/lmf_kernels.cu',

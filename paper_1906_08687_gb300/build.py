@@ -22,7 +22,8 @@ ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 FLAGS = ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC', '--expt-relaxed-constexpr',
          '-I', INCLUDE, '-I', CSRC, '-I', OUT_DIR]
 # device headers the plan-time compiler (NVRTC) gets as in-memory sources
-JIT_HEADERS = ['lmf_internal.h', 'lmf_rowpass.cuh', 'lmf_root_plain.cuh', 'lmf_root_tc.cuh', 'lmf_root_lean.cuh']
+JIT_HEADERS = ['lmf_internal.h', 'lmf_rowpass.cuh', 'lmf_root_plain.cuh', 'lmf_root_tc.cuh', 'lmf_root_lean.cuh',
+               'lmf_tree_dev.cuh']
 JIT_INC = os.path.join(OUT_DIR, 'lmf_jit_headers.inc')
 
 

@@ -2131,6 +2131,24 @@ lmf_status plan_with_root(lmf_ctx* c, int batch_id, const lmf_plan_opts& opts, i
                                P->at<double>(P->res_f64_off), P->agg_off, filt_idx, P->agg_dtype,
                                P->at<uint32_t>(P->status_off), Root.nrows, c->num_sms, bound, W, rp, sorted_q);
     if (s) return fail(c, s, "tree plan: device tables");
+    // the tree pass compiled for the plan (row pass and node search specialised;
+    // the interpreted kernel stays when NVRTC is missing or the compile fails)
+    if (!(P->opts.flags & LMF_PLAN_NO_JIT) && Root.nrows > 0 && jit_available()) {
+      TreeJitSpec spec;
+      tree_jit_spec(P->tree.get(), &spec);
+      const std::string src = jit_tree_source(rp, spec);
+      if (c->dry) {
+        c->dry_sources.emplace_back(src, "lmf_tree_jit");
+      } else {
+        std::string log;
+        cudaKernel_t k = nullptr;
+        if (jit_kernel(src, "lmf_tree_jit", &k, &log))
+          tree_set_jit(P->tree.get(), k);
+        else
+          std::fprintf(stderr, "lmf: plan-time compile of the tree pass failed, interpreted kernel kept: %.400s\n",
+                       log.c_str());
+      }
+    }
   }
   if (use_tc) {
     gram_tc_finish(P->tc.get(), rp, P->arena.base);

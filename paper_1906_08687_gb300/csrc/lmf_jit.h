@@ -60,6 +60,33 @@ LeanShape lean_shape(const RootParams& rp, bool direct_z);
 // CUDA source of the key-level root scan of a plan (kernel lmf_root_lean_jit)
 std::string jit_lean_source(const RootParams& rp, const std::vector<DirectAgg>& direct, int min_ctas);
 
+// What the compiled tree pass needs from a tree plan (lmf_tree.cu): the z
+// width, and per group of mutually exclusive nodes the decision tree over the
+// nodes' predicates (entries: a split z <= thr to left / right, or a leaf
+// listing candidate nodes [left, left + right) of cand) and every node's
+// predicates (z, op 0: z <= thr, 1: z > thr).
+struct TreeJitSpec {
+  struct Entry {
+    int z, leaf;
+    float thr;
+    int left, right;
+  };
+  struct Pred {
+    int z, op;
+    float thr;
+  };
+  int mp = 16;
+  std::vector<int> droot;
+  std::vector<Entry> dt;
+  std::vector<int> cand;
+  std::vector<std::vector<Pred>> preds;
+};
+// CUDA source of the tree pass for a plan (kernel lmf_tree_jit): the row pass
+// (root columns and view records straight into the row's z) and the node
+// search (the decision tree as nested comparisons against constants)
+// generated, the rest the library's tree_body (lmf_tree_dev.cuh)
+std::string jit_tree_source(const RootParams& rp, const TreeJitSpec& t);
+
 // compiles src for sm_103a, or finds it in the process-wide cache of compiled
 // sources; on failure returns false with NVRTC's log in *log
 bool jit_kernel(const std::string& src, const char* name, cudaKernel_t* k, std::string* log);

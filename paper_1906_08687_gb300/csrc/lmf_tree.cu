@@ -30,7 +30,7 @@
 //                reduction.  Nothing per row leaves the SM.
 //   k_tree_out   every aggregate as a prefix / suffix sum over the buckets.
 #include "lmf_tree.h"
-#include "lmf_rowpass.cuh"
+#include "lmf_tree_dev.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -40,55 +40,10 @@
 
 namespace lmf {
 
-constexpr int kTreeMaxMom = 8;
-constexpr int kTreeResNodes = 256;  // nodes whose resident-key sums fit the shared table
-constexpr uint16_t kNoNode = 0xFFFF;
-
-struct TreePred {
-  int16_t z;
-  int16_t op;     // 0: x <= thr, 1: x > thr
-  float thr;
-};
-
 struct TreeOut {
   int32_t node, split, j, op, mom, is_count;
   int64_t dst;
   double inv_scale;
-};
-
-struct TreeDev {
-  int32_t n_nodes, n_groups, n_split, max_bins, n_mom;
-  int32_t mom_stride;          // words per histogram cell: 4 (one 32-byte sector) when n_mom <= 4
-  const int32_t* pred_off;     // [n_nodes + 1]
-  const TreePred* preds;
-  const int32_t* group_off;    // [n_groups + 1] into group_nodes
-  const int32_t* group_nodes;
-  const int16_t* split_z;      // [n_split]
-  const int32_t* thr_off;      // [n_split + 1]
-  const float* thr;
-  int16_t mom_a[kTreeMaxMom], mom_b[kTreeMaxMom];  // z indices, -1: absent
-  double mom_scale[kTreeMaxMom];                   // 0: the count moment (w itself)
-  // decision tree over the nodes' predicates, per group: internal entries
-  // send a row left when z[dz] <= dthr; a leaf lists candidate nodes
-  // [dleft, dleft + dright) of dcand, each checked on all of its predicates
-  const int32_t* droot;        // [n_groups]
-  const struct TreeDt* dt;
-  const int32_t* dcand;
-  // splits on an attribute of the resident key's dimension (the root's first
-  // sort key, Sec. 3.5): bit f of res_mask; their cells are summed per
-  // (node, key) in shared memory and added once per key (res_q: the probe group, -1: none)
-  int32_t res_q;
-  unsigned long long res_mask;
-  long long* H;                // [n_nodes][n_split][max_bins][mom_stride]
-  int64_t N;
-  uint32_t* status;
-};
-
-struct TreeDt {
-  int16_t z;
-  int16_t leaf;                // 1: left/right are the candidate range [left, left + right)
-  float thr;
-  int32_t left, right;
 };
 
 struct TreeShape {
@@ -124,6 +79,7 @@ struct TreePlanImpl {
   int num_sms = 0;
   TreeShape shape{2};
   bool tuned = false;
+  cudaKernel_t jit = nullptr;    // the pass compiled for the plan (null: k_tree_fused)
 };
 
 TreePlan::~TreePlan() { delete impl; }
@@ -150,8 +106,13 @@ bool disjoint(const std::vector<TreePred>& a, const std::vector<TreePred>& b) {
 // Decision tree over a set of mutually exclusive nodes: an internal entry
 // splits on one predicate (z, thr) of the nodes; a node that requires z <= thr
 // goes only left, one that requires z > thr only right, the others both ways.
-// The predicate that leaves the smaller side largest is taken; a set that no
-// predicate splits is a leaf (its nodes are checked in full).
+// The predicate whose larger side is smallest is taken (ties: the fewer nodes
+// on both sides together), so that the nodes of a tree level, which split
+// into halves on the predicate of their common ancestor, give a tree of the
+// level's depth; a set that no predicate splits, or a tree that reached
+// kMaxDt entries, ends in a leaf (its nodes are checked in full).
+constexpr size_t kMaxDt = size_t(1) << 16;
+
 int build_dt(const std::vector<std::vector<TreePred>>& nodes, const std::vector<int>& set, int depth,
              std::vector<TreeDt>* dt, std::vector<int32_t>* cand) {
   const int at = (int)dt->size();
@@ -161,22 +122,23 @@ int build_dt(const std::vector<std::vector<TreePred>>& nodes, const std::vector<
     cand->insert(cand->end(), set.begin(), set.end());
     return at;
   };
-  if (set.size() <= 1 || depth >= 24) return leaf();
+  if (set.size() <= 1 || depth >= 24 || dt->size() >= kMaxDt) return leaf();
   std::map<std::pair<int, float>, std::pair<int, int>> cnt;  // (z, thr) -> (nodes only left, only right)
   for (int n : set)
     for (const TreePred& p : nodes[n]) {
       auto& c = cnt[{p.z, p.thr}];
       (p.op == 0 ? c.first : c.second)++;
     }
-  int best_min = 0;
+  const int n = (int)set.size();
+  int best_max = n, best_sum = 2 * n;
   std::pair<int, float> best{-1, 0.f};
   for (auto& kv : cnt) {
-    const int n = (int)set.size();
     const int l = n - kv.second.second, r = n - kv.second.first;  // sizes of the two sides
     if (l >= n || r >= n) continue;
-    const int mn = std::min(l, r);
-    if (mn > best_min) {
-      best_min = mn;
+    const int mx = std::max(l, r), sum = l + r;
+    if (mx < best_max || (mx == best_max && sum < best_sum)) {
+      best_max = mx;
+      best_sum = sum;
       best = kv.first;
     }
   }
@@ -504,193 +466,10 @@ lmf_status tree_finish(TreePlan* tp, char* base, long long* res_i64, double* res
 // ---------------------------------------------------------------------------
 // kernels
 
-// exact sum over the lanes of `mask` of a 64-bit integer (two's complement,
-// mod 2^64): three 32-bit warp reductions of its 16 + 16 + 32-bit pieces,
-// none of which can overflow over 32 lanes; every lane of mask gets the sum
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned mask, unsigned long long v) {
-  const unsigned s0 = __reduce_add_sync(mask, static_cast<unsigned>(v & 0xffffu));
-  const unsigned s1 = __reduce_add_sync(mask, static_cast<unsigned>((v >> 16) & 0xffffu));
-  const unsigned s2 = __reduce_add_sync(mask, static_cast<unsigned>(v >> 32));
-  return (static_cast<unsigned long long>(s2) << 32) + (static_cast<unsigned long long>(s1) << 16) + s0;
-}
-
-__device__ __forceinline__ void red_add_u64(long long* dst, long long v) {
-  atomicAdd(reinterpret_cast<unsigned long long*>(dst), static_cast<unsigned long long>(v));
-}
-
-// the row's node in group g: descend the decision tree, then check the
-// candidates of the leaf on all of their predicates; kNoNode when none holds
-__device__ __forceinline__ int tree_node_of(const TreeDev& d, int g, const float* zrow) {
-  int i = d.droot[g];
-  TreeDt e = d.dt[i];
-  while (!e.leaf) {
-    i = zrow[e.z] <= e.thr ? e.left : e.right;
-    e = d.dt[i];
-  }
-  for (int c = e.left; c < e.left + e.right; ++c) {
-    const int n = d.dcand[c];
-    bool ok = true;
-    for (int k = d.pred_off[n]; k < d.pred_off[n + 1] && ok; ++k) {
-      const TreePred pr = d.preds[k];
-      const float x = zrow[pr.z];
-      ok = pr.op == 0 ? (x <= pr.thr) : (x > pr.thr);
-    }
-    if (ok) return n;
-  }
-  return kNoNode;
-}
-
-constexpr int kTreeThreads = 256;
-constexpr int kTreeThrSmem = 48 * 1024;   // thresholds staged in shared memory up to this size
-
 template <int MP>
 __global__ void __launch_bounds__(kTreeThreads, 2) k_tree_fused(const __grid_constant__ RootParams p,
                                                                 const __grid_constant__ TreeDev d) {
-  extern __shared__ __align__(16) uint32_t sm[];
-  const int nthr = d.thr_off[d.n_split];
-  const bool thr_smem = static_cast<size_t>(nthr) * 4 <= static_cast<size_t>(kTreeThrSmem);
-  float* thr_s = reinterpret_cast<float*>(sm);                  // all thresholds, split after split
-  float* Z = reinterpret_cast<float*>(sm + (thr_smem ? ((nthr + 3) & ~3) : 0));
-  int32_t* C = reinterpret_cast<int32_t*>(Z + kTreeThreads * (MP + 1));
-  const int ncat = p.n_rowcat > 0 ? p.n_rowcat : 1;
-  // the row's moments, one 32-byte record, the source of its bulk reductions
-  __shared__ __align__(16) unsigned long long stage[kTreeThreads][4];
-  const bool bulk = d.mom_stride == 4;
-  if (thr_smem)
-    for (int j = threadIdx.x; j < nthr; j += blockDim.x) thr_s[j] = d.thr[j];
-  const float* thr = thr_smem ? thr_s : d.thr;
-  float* zrow = Z + threadIdx.x * (MP + 1);  // odd stride: no bank conflicts
-  int32_t* crow = C + threadIdx.x * ncat;
-  const int lane = threadIdx.x & 31;
-  // the resident key's sums per node, added to the histogram once per key
-  __shared__ unsigned long long racc[kTreeResNodes][4];
-  const bool resident = d.res_q >= 0;
-  const GroupDesc& RG = p.grp[resident ? d.res_q : 0];
-  long long res_key = -1;
-  for (int i = threadIdx.x; i < kTreeResNodes * 4; i += blockDim.x) (&racc[0][0])[i] = 0ull;
-  // adds the resident key's sums to their cells (one per node and resident
-  // split) and clears them; every thread of the CTA calls this
-  auto res_flush = [&]() {
-    __syncthreads();
-    int nres = 0;
-    int fres[64];
-    for (int f = 0; f < d.n_split && f < 64; ++f)
-      if ((d.res_mask >> f) & 1ull) fres[nres++] = f;
-    if (res_key >= 0)
-      for (int e = threadIdx.x; e < d.n_nodes * nres; e += blockDim.x) {
-        const int n = e / nres, f = fres[e % nres];
-        if (racc[n][0] == 0ull && racc[n][1] == 0ull && racc[n][2] == 0ull && racc[n][3] == 0ull) continue;
-        const int zf = d.split_z[f];
-        const float x = __uint_as_float(RG.rec[res_key * RG.stride + RG.n_cnt + (zf - p.grp_zoff[d.res_q])]);
-        const int t0 = d.thr_off[f];
-        int l = 0, h = d.thr_off[f + 1] - t0;
-        while (l < h) {
-          const int mid = (l + h) >> 1;
-          if (thr[t0 + mid] < x) l = mid + 1;
-          else h = mid;
-        }
-        const int64_t cell = ((static_cast<int64_t>(n) * d.n_split + f) * d.max_bins + l) * d.mom_stride;
-        for (int m = 0; m < d.n_mom; ++m)
-          if (racc[n][m] != 0ull) red_add_u64(d.H + cell + m, static_cast<long long>(racc[n][m]));
-      }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kTreeResNodes * 4; i += blockDim.x) (&racc[0][0])[i] = 0ull;
-    __syncthreads();
-  };
-  __syncthreads();
-  // each CTA a contiguous range of rows (the resident key changes rarely
-  // inside it); every lane of a warp runs every iteration (warp reductions
-  // below), rows past the range are inactive
-  const int64_t r_begin = static_cast<int64_t>(blockIdx.x) * d.N / gridDim.x;
-  const int64_t r_end = (static_cast<int64_t>(blockIdx.x) + 1) * d.N / gridDim.x;
-  for (int64_t base = r_begin; base < r_end; base += blockDim.x) {
-    if (resident) {  // CTA-uniform: the key of the chunk's first row
-      const int32_t k0 = RG.fk[base];
-      const long long nk = (k0 >= 0 && k0 < RG.K) ? k0 : -1;
-      if (nk != res_key) {
-        res_flush();
-        res_key = nk;
-      }
-    }
-    const int64_t row = base + threadIdx.x;
-    long long w = 0;
-    if (row < r_end) w = root_row_z<MP>(p, row, zrow, crow);
-    // the row's cells of resident splits go to the shared sums
-    const bool row_res = resident && w != 0 && res_key >= 0 && static_cast<long long>(RG.fk[row]) == res_key;
-    long long mv[kTreeMaxMom];
-    bool have = false;
-    for (int g = 0; g < d.n_groups; ++g) {
-      const int n = w != 0 ? tree_node_of(d, g, zrow) : static_cast<int>(kNoNode);
-      const bool on_g = n != static_cast<int>(kNoNode);
-      const unsigned on_mask = __ballot_sync(0xffffffffu, on_g);
-      if (on_mask == 0u) continue;  // warp-uniform
-      if (on_g && !have) {  // the row's fixed-point moments, once
-#pragma unroll
-        for (int m = 0; m < kTreeMaxMom; ++m) {
-          if (m >= d.n_mom) break;
-          long long v = w;
-          if (d.mom_scale[m] > 0.0) {
-            double x = static_cast<double>(w);
-            if (d.mom_a[m] >= 0) x *= static_cast<double>(zrow[d.mom_a[m]]);
-            if (d.mom_b[m] >= 0) x *= static_cast<double>(zrow[d.mom_b[m]]);
-            v = llrint(x * d.mom_scale[m]);
-          }
-          mv[m] = v;
-        }
-        have = true;
-        if (bulk) {  // the previous row's reductions have read the record: refill it
-          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-#pragma unroll
-          for (int m = 0; m < 4; ++m) stage[threadIdx.x][m] = m < d.n_mom ? static_cast<unsigned long long>(mv[m]) : 0ull;
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        }
-      }
-      if (on_g && row_res)
-        for (int m = 0; m < d.n_mom && m < 4; ++m)
-          if (mv[m] != 0) atomicAdd(&racc[n][m], static_cast<unsigned long long>(mv[m]));
-      for (int f = 0; f < d.n_split; ++f) {
-        // a resident split of a row with the resident key is in the shared sums
-        const bool on = on_g && !(row_res && f < 64 && ((d.res_mask >> f) & 1ull));
-        int64_t cell = 0;
-        if (on) {
-          const float x = zrow[d.split_z[f]];
-          const int t0 = d.thr_off[f];
-          int l = 0, h = d.thr_off[f + 1] - t0;
-          while (l < h) {  // number of thresholds < x
-            const int mid = (l + h) >> 1;
-            if (thr[t0 + mid] < x) l = mid + 1;
-            else h = mid;
-          }
-          cell = ((static_cast<int64_t>(n) * d.n_split + f) * d.max_bins + l) * d.mom_stride;
-        }
-        const unsigned f_mask = __ballot_sync(0xffffffffu, on);
-        if (f_mask == 0u) continue;  // warp-uniform
-        const int f_lead = __ffs(f_mask) - 1;
-        const int64_t c0 = __shfl_sync(0xffffffffu, cell, f_lead);
-        if (__all_sync(0xffffffffu, !on || cell == c0)) {  // one cell for the whole warp
-#pragma unroll
-          for (int m = 0; m < kTreeMaxMom; ++m) {
-            if (m >= d.n_mom) break;
-            const unsigned long long sum = warp_sum_u64(0xffffffffu, on ? static_cast<unsigned long long>(mv[m]) : 0ull);
-            if (lane == f_lead && sum != 0ull) red_add_u64(d.H + c0 + m, static_cast<long long>(sum));
-          }
-        } else if (on && bulk) {  // the row's record added to its 32-byte cell in one reduction
-          asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], 32;" ::"l"(d.H + cell),
-                       "r"(static_cast<uint32_t>(__cvta_generic_to_shared(&stage[threadIdx.x][0])))
-                       : "memory");
-        } else if (on) {
-#pragma unroll
-          for (int m = 0; m < kTreeMaxMom; ++m) {
-            if (m >= d.n_mom) break;
-            if (mv[m] != 0) red_add_u64(d.H + cell + m, mv[m]);
-          }
-        }
-      }
-      if (bulk) asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-    }
-  }
-  if (resident) res_flush();
-  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  tree_body<InterpTreeRow<MP>, MP>(p, d);
 }
 
 __global__ void k_tree_out(const __grid_constant__ TreeDev d, const TreeOut* outs, int n, long long* res_i64,
@@ -721,6 +500,25 @@ size_t fused_smem(const TreePlanImpl& T, const RootParams& rp) {
   return thr + z + cat;
 }
 
+cudaError_t launch_fused_jit(const TreePlanImpl& T, const RootParams& rp, const TreeShape& sh, cudaStream_t s) {
+  const size_t sm = fused_smem(T, rp);
+  const void* fn = reinterpret_cast<const void*>(T.jit);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int fit = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, kTreeThreads, sm) != cudaSuccess) {
+    cudaGetLastError();  // the query is only advisory: the launch bounds guarantee two
+    fit = 2;
+  }
+  const int cps = std::max(1, std::min(sh.cps, std::max(1, fit)));
+  const int64_t need = (T.dev.N + kTreeThreads - 1) / kTreeThreads;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(T.num_sms) * cps));
+  void* args[] = {const_cast<RootParams*>(&rp), const_cast<TreeDev*>(&T.dev)};
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(kTreeThreads), args, sm, s);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 template <int MP>
 cudaError_t launch_fused_mp(const TreePlanImpl& T, const RootParams& rp, const TreeShape& sh, cudaStream_t s) {
   const size_t sm = fused_smem(T, rp);
@@ -737,6 +535,7 @@ cudaError_t launch_fused_mp(const TreePlanImpl& T, const RootParams& rp, const T
 }
 
 cudaError_t launch_fused(const TreePlanImpl& T, const RootParams& rp, const TreeShape& sh, cudaStream_t s) {
+  if (T.jit) return launch_fused_jit(T, rp, sh, s);
   switch (T.mp) {
     case 16: return launch_fused_mp<16>(T, rp, sh, s);
     case 32: return launch_fused_mp<32>(T, rp, sh, s);
@@ -757,6 +556,23 @@ cudaError_t tree_launch(TreePlan* tp, const RootParams& rp, cudaStream_t s, int*
   *nk += 2;
   return cudaGetLastError();
 }
+
+void tree_jit_spec(const TreePlan* tp, TreeJitSpec* out) {
+  const TreePlanImpl& T = *tp->impl;
+  out->mp = T.mp;
+  out->droot.assign(T.droot.begin(), T.droot.end());
+  out->dt.clear();
+  for (const TreeDt& e : T.dt) out->dt.push_back({e.z, e.leaf, e.thr, e.left, e.right});
+  out->cand.assign(T.dcand.begin(), T.dcand.end());
+  out->preds.clear();
+  for (const auto& v : T.nodes) {
+    std::vector<TreeJitSpec::Pred> ps;
+    for (const TreePred& pr : v) ps.push_back({pr.z, pr.op, pr.thr});
+    out->preds.push_back(ps);
+  }
+}
+
+void tree_set_jit(TreePlan* tp, cudaKernel_t k) { tp->impl->jit = k; }
 
 bool tree_needs_tuning(const TreePlan* tp) { return tp && tp->impl && !tp->impl->tuned; }
 

@@ -12,6 +12,7 @@
 
 #include "lmf.h"
 #include "lmf_internal.h"
+#include "lmf_jit.h"
 
 namespace lmf {
 
@@ -34,21 +35,25 @@ struct TreePlan {
 // sorted thresholds and moments (monomials of degree <= 2).
 lmf_status tree_plan(const std::vector<TreeAggIn>& in, const std::map<std::string, int>& zidx,
                      TreePlan* tp, std::string* msg);
-// Device buffers: histogram and work queues (reset every run) ...
+// Device buffers: the histogram (reset every run) ...
 void tree_alloc_zeroed(TreePlan* tp, int64_t N, const std::function<size_t(size_t)>& take);
-// ... per-row pass buffers and plan tables (written once or fully every run).
+// ... plan tables and outputs (written once).
 void tree_alloc(TreePlan* tp, int64_t N, const std::function<size_t(size_t)>& take);
 lmf_status tree_finish(TreePlan* tp, char* base, long long* res_i64, double* res_f64,
                        const std::vector<int64_t>& agg_off, const std::vector<int>& filt_idx,
                        const std::vector<int32_t>& agg_dtype, uint32_t* status, int64_t N,
                        int num_sms, const std::map<std::string, double>& bound, double W,
                        const RootParams& rp, int res_q);
+// What the plan-time compiler needs (jit_tree_source); the compiled pass, when
+// set, replaces the library's interpreted kernel
+void tree_jit_spec(const TreePlan* tp, TreeJitSpec* out);
+void tree_set_jit(TreePlan* tp, cudaKernel_t k);
 cudaError_t tree_launch(TreePlan* tp, const RootParams& rp, cudaStream_t s, int* n_kernels);
-// The autotuner times the histogram pass over its shape candidates once the
-// per-row buffers hold a run's data, and keeps the fastest.
+// The autotuner times the pass over its CTAs-per-SM candidates at the first
+// run and keeps the fastest.
 bool tree_needs_tuning(const TreePlan* tp);
 cudaError_t tree_autotune(TreePlan* tp, const RootParams& rp, cudaStream_t s);
-// chosen histogram shape, for reporting: slices, split attributes and nodes per slice, CTAs per SM, chunk rows
+// chosen shape, for reporting: slices (1), split attributes, nodes, CTAs per SM, chunk rows (0)
 void tree_shape(const TreePlan* tp, int* out5);
 void tree_counts(const TreePlan* tp, int32_t* nodes, int32_t* groups);
 

@@ -1,9 +1,11 @@
 // Host-only check of the plan-time code generator (no GPU needed): builds
 // plans of several shapes by hand, generates the plain and the tensor-core
-// root-scan sources for each, and compiles them for sm_103a with NVRTC.
+// root-scan sources for each (and a tree pass), and compiles them for sm_103a
+// with NVRTC.
 // Used by tests/test_jit_codegen.py.  Exit status 0 when every source
 // compiles; one line per compiled source on stdout.
 #include "lmf_jit.cu"
+#include "lmf_jit_tree.cu"
 
 #include <cstdio>
 #include <string>
@@ -235,6 +237,26 @@ int main() {
     dir.push_back(s);
     rp.n_direct = static_cast<int>(dir.size());
     bad += !compile(jit_lean_source(rp, dir, 2), "key-level random");
+  }
+  {  // the tree pass of a snowflake root: two groups of nodes, a decision tree over their predicates
+    RootParams rp = base(true);
+    rp.x[2].dtype = 2;
+    TreeJitSpec t;
+    t.mp = 32;
+    t.preds = {{}, {{3, 0, 0.5f}}, {{3, 1, 0.5f}}, {{3, 1, 0.5f}, {12, 0, -1.25e-3f}}, {{3, 1, 0.5f}, {12, 1, -1.25e-3f}}};
+    // group 0: the root node alone; group 1: z3 <= 0.5 -> node 1, else one of nodes 2..4
+    t.droot = {0, 1};
+    t.dt = {{0, 1, 0.f, 0, 1}, {3, 0, 0.5f, 2, 3}, {0, 1, 0.f, 1, 1}, {0, 1, 0.f, 2, 3}};
+    t.cand = {0, 1, 3, 4, 2};
+    bad += !compile(jit_tree_source(rp, t), "tree pass");
+    // a decision tree too large to spell out: the node search over the device tables
+    t.dt.resize(5000, TreeJitSpec::Entry{0, 1, 0.f, 0, 1});
+    const std::string big = jit_tree_source(rp, t);
+    if (big.find("tree_node_of(d, g, zrow)") == std::string::npos) {
+      std::printf("FAIL large tree not searched through the tables\n");
+      ++bad;
+    }
+    bad += !compile(big, "tree pass (table search)");
   }
   {  // a root without probe groups: features only
     RootParams rp{};

@@ -3,7 +3,9 @@ several shapes (sorted snowflake with resident key and category views,
 fanning-out joins, more tables than the kernel parameters hold, FP64 and root
 categories, wide z, a root without probe groups) compile for sm_103a with
 NVRTC, for the plain and the tensor-core scan, and the key-level scan with its
-bulk, runs and resident-key reverse views."""
+bulk, runs and resident-key reverse views, and the tree pass with its
+decision tree over the nodes' predicates (spelled out, or searched through
+the device tables when too large)."""
 import os
 import shutil
 import subprocess
@@ -28,4 +30,4 @@ def test_generated_sources_compile(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=500)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
     ok = [l for l in r.stdout.splitlines() if l.startswith('ok ')]
-    assert len(ok) == 9, r.stdout
+    assert len(ok) == 11, r.stdout
