@@ -2,9 +2,19 @@
 // batch of threshold-filtered aggregates into nodes, split attributes and the
 // decision tree that finds a row's node.  Used by tests/test_tree_plan.py.
 // Exit status 0 when every check holds; one line per check on stdout.
+//
+// With `--emit DIR` it instead writes, for plans of several shapes, the tree
+// pass source generated for the plan (case_K.cu) and a set of points with the
+// node each group's brute-force search gives them (case_K.txt: "G P NZ", then
+// per point NZ float bit patterns in hex and G node ids, 65535 for none), so
+// that the test can compile the generated node search on the host and
+// compare.
 #include "lmf_tree.cu"
+#include "lmf_jit_tree.cu"
 
+#include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -61,9 +71,120 @@ int dt_node(const TreePlanImpl& T, int g, const std::vector<float>& z) {
   return -1;
 }
 
+// random conjunctions of 1-3 predicates over four features, thresholds from
+// a small grid (so that nodes share predicates and overlap), each node with
+// three thresholds of a fifth attribute as its split
+std::vector<TreeAggIn> random_nodes(int n_nodes, uint64_t seed, std::map<std::string, int>* zidx) {
+  for (int i = 0; i < 5; ++i) (*zidx)["f" + std::to_string(i)] = 1 + i;
+  (*zidx)["y"] = 6;
+  uint64_t x = seed;
+  auto next = [&]() {
+    x = x * 6364136223846793005ull + 1442695040888963407ull;
+    return static_cast<int>(x >> 33);
+  };
+  const double grid[5] = {-1.0, -0.5, 0.0, 0.5, 1.0};
+  std::vector<TreeAggIn> in;
+  for (int k = 0; k < n_nodes; ++k) {
+    std::vector<TreeFactorIn> node;
+    const int np = 1 + next() % 3;
+    for (int j = 0; j < np; ++j)
+      node.push_back({"f" + std::to_string(next() % 4), next() % 2 ? LMF_LE : LMF_GT, 0, grid[next() % 5]});
+    for (int j = 0; j < 3; ++j) {
+      TreeAggIn a;
+      a.factors = node;
+      a.factors.push_back({"f4", LMF_LE, 0, 10.0 + j});
+      a.factors.push_back({"y", LMF_POW, 1, 0.0});
+      in.push_back(a);
+    }
+  }
+  return in;
+}
+
+bool emit_case(const std::string& dir, int k, const std::vector<TreeAggIn>& in, const std::map<std::string, int>& zidx) {
+  TreePlan tp;
+  std::string msg;
+  if (tree_plan(in, zidx, &tp, &msg) != LMF_OK) {
+    std::printf("FAIL plan of case %d: %s\n", k, msg.c_str());
+    return false;
+  }
+  const TreePlanImpl& T = *tp.impl;
+  TreeJitSpec spec;
+  tree_jit_spec(&tp, &spec);
+  RootParams rp{};
+  const std::string src = jit_tree_source(rp, spec);
+  FILE* f = std::fopen((dir + "/case_" + std::to_string(k) + ".cu").c_str(), "w");
+  if (!f) return false;
+  std::fwrite(src.data(), 1, src.size(), f);
+  std::fclose(f);
+  // points: thresholds, their neighbours and uniform values on every coordinate
+  std::vector<float> special;
+  for (const auto& v : T.nodes)
+    for (const TreePred& p : v) {
+      special.push_back(p.thr);
+      special.push_back(std::nextafter(p.thr, -INFINITY));
+      special.push_back(std::nextafter(p.thr, INFINITY));
+    }
+  const int nz = static_cast<int>(zidx.size()) + 1, G = static_cast<int>(T.groups.size()), P = 4000;
+  f = std::fopen((dir + "/case_" + std::to_string(k) + ".txt").c_str(), "w");
+  if (!f) return false;
+  std::fprintf(f, "%d %d %d\n", G, P, nz);
+  uint64_t x = 977 + k;
+  for (int t = 0; t < P; ++t) {
+    std::vector<float> z(nz);
+    for (auto& v : z) {
+      x = x * 6364136223846793005ull + 1442695040888963407ull;
+      const uint32_t r = static_cast<uint32_t>(x >> 32);
+      v = (r & 1) && !special.empty() ? special[(r >> 1) % special.size()]
+                                      : static_cast<float>((r >> 8) % 4096) / 1024.f - 2.f;
+      uint32_t u;
+      std::memcpy(&u, &v, 4);
+      std::fprintf(f, "%08x ", u);
+    }
+    for (int g = 0; g < G; ++g) {
+      int want = kNoNode, hits = 0;
+      for (int n : T.groups[g]) {
+        bool ok = true;
+        for (const TreePred& p : T.nodes[n]) ok = ok && (p.op == 0 ? z[p.z] <= p.thr : z[p.z] > p.thr);
+        if (ok) {
+          want = n;
+          ++hits;
+        }
+      }
+      if (hits > 1) {
+        std::printf("FAIL case %d: two nodes of group %d hold at one point\n", k, g);
+        return false;
+      }
+      std::fprintf(f, "%d ", want);
+    }
+    std::fprintf(f, "\n");
+  }
+  std::fclose(f);
+  std::printf("emitted case %d: %zu nodes, %d groups, %zu decision-tree entries\n", k, T.nodes.size(), G, T.dt.size());
+  return true;
+}
+
 }  // namespace
 
-int main() {
+int main(int argc, char** argv) {
+  if (argc == 3 && std::string(argv[1]) == "--emit") {
+    bool ok = true;
+    {  // one complete level of depth 6: one group
+      std::map<std::string, int> zidx;
+      ok = ok && emit_case(argv[2], 0, level(6, 20, &zidx), zidx);
+    }
+    {  // the leaves of depths 2 and 3 of one tree: nested nodes, several groups
+      std::map<std::string, int> zidx;
+      std::vector<TreeAggIn> in = level(2, 20, &zidx);
+      const std::vector<TreeAggIn> l3 = level(3, 20, &zidx);
+      in.insert(in.end(), l3.begin(), l3.end());
+      ok = ok && emit_case(argv[2], 1, in, zidx);
+    }
+    for (int k = 2; k < 6; ++k) {  // random overlapping conjunctions
+      std::map<std::string, int> zidx;
+      ok = ok && emit_case(argv[2], k, random_nodes(12 * k, 31 * k + 7, &zidx), zidx);
+    }
+    return ok ? 0 : 1;
+  }
   for (int depth : {3, 6}) {
     std::map<std::string, int> zidx;
     const std::vector<TreeAggIn> in = level(depth, 20, &zidx);
