@@ -92,7 +92,7 @@ def test_generated_node_search(check_exe, tmp_path):
     out.mkdir()
     r = subprocess.run([str(check_exe), '--emit', str(out)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
-    cases = sorted(p for p in os.listdir(out) if p.endswith('.cu'))
+    cases = sorted(p for p in os.listdir(out) if p.startswith('case_') and p.endswith('.cu'))
     assert len(cases) == 6, r.stdout
     groups = [int(m) for m in re.findall(r'(\d+) groups', r.stdout)]
     assert groups[0] == 1 and max(groups[1:]) > 1, r.stdout     # one group, and cases with several
@@ -110,4 +110,35 @@ def test_generated_node_search(check_exe, tmp_path):
         assert c.returncode == 0, c.stderr[-3000:]
         run = subprocess.run([str(exe), str(out / (name[:-3] + '.txt'))], capture_output=True, text=True,
                              timeout=120)
+        assert run.returncode == 0, (name, run.stdout, run.stderr)
+
+
+@pytest.mark.timeout(900)
+def test_generated_row_pass(check_exe, tmp_path):
+    from paper_1906_08687_gb300 import build
+    out = tmp_path / 'cases'
+    out.mkdir()
+    r = subprocess.run([str(check_exe), '--emit', str(out)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
+    rows = sorted(p for p in os.listdir(out) if p.startswith('row_case_'))
+    assert len(rows) == 3
+    csrc = os.path.join(ROOT, 'paper_1906_08687_gb300', 'csrc')
+    for name in rows:
+        k = int(name[len('row_case_'):-3])
+        src = open(out / name).read()
+        head = ('static __device__ __forceinline__ long long row(const RootParams& p, int64_t r, float* zrow, '
+                'int32_t* crow) {')
+        i = src.index(head)
+        j = src.index('  static __device__ __forceinline__ int node(', i)
+        fn = ('static long long gen_row(const lmf::RootParams& p, int64_t r, float* zrow, int32_t* crow) {'
+              + src[i + len(head):j])
+        hdr = tmp_path / ('row_%d.h' % k)
+        hdr.write_text(fn)
+        exe = tmp_path / ('row_%d' % k)
+        cmd = [build._nvcc(), '-std=c++17', '-O1', '-I', csrc, '-I', os.path.join(ROOT, 'include'),
+               '-I', os.path.join(ROOT, 'tests'), '-DTREE_ROW_CASE=%d' % k, '-DTREE_ROW_HEADER="%s"' % hdr,
+               os.path.join(ROOT, 'tests', 'tree_row_host.cu'), '-o', str(exe)]
+        c = subprocess.run(cmd, capture_output=True, text=True)
+        assert c.returncode == 0, c.stderr[-3000:]
+        run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
         assert run.returncode == 0, (name, run.stdout, run.stderr)

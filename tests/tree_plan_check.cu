@@ -8,9 +8,11 @@
 // node each group's brute-force search gives them (case_K.txt: "G P NZ", then
 // per point NZ float bit patterns in hex and G node ids, 65535 for none), so
 // that the test can compile the generated node search on the host and
-// compare.
+// compare; and the source generated for the root layouts of tree_row_cases.h
+// (row_case_K.cu), whose row pass tests/tree_row_host.cu checks.
 #include "lmf_tree.cu"
 #include "lmf_jit_tree.cu"
+#include "tree_row_cases.h"
 
 #include <cmath>
 #include <cstdio>
@@ -182,6 +184,20 @@ int main(int argc, char** argv) {
     for (int k = 2; k < 6; ++k) {  // random overlapping conjunctions
       std::map<std::string, int> zidx;
       ok = ok && emit_case(argv[2], k, random_nodes(12 * k, 31 * k + 7, &zidx), zidx);
+    }
+    for (int k = 0; k < kTreeRowCases; ++k) {  // the row pass for the layouts of tree_row_cases.h
+      const RootParams rp = tree_row_case(k);
+      TreeJitSpec t;
+      t.mp = (rp.m + 15) / 16 * 16;
+      t.droot = {0};
+      t.dt = {{0, 1, 0.f, 0, 0}};
+      const std::string src = jit_tree_source(rp, t);
+      FILE* f = std::fopen((std::string(argv[2]) + "/row_case_" + std::to_string(k) + ".cu").c_str(), "w");
+      ok = ok && f != nullptr;
+      if (f) {
+        std::fwrite(src.data(), 1, src.size(), f);
+        std::fclose(f);
+      }
     }
     return ok ? 0 : 1;
   }
