@@ -104,17 +104,42 @@ bool disjoint(const std::vector<TreePred>& a, const std::vector<TreePred>& b) {
 }
 
 // Decision tree over a set of mutually exclusive nodes: an internal entry
-// splits on one predicate (z, thr) of the nodes; a node that requires z <= thr
-// goes only left, one that requires z > thr only right, the others both ways.
-// The predicate whose larger side is smallest is taken (ties: the fewer nodes
-// on both sides together), so that the nodes of a tree level, which split
-// into halves on the predicate of their common ancestor, give a tree of the
-// level's depth; a set that no predicate splits, or a tree that reached
-// kMaxDt entries, ends in a leaf (its nodes are checked in full).
+// splits on one threshold (z, thr) taken from the nodes' predicates.  On z a
+// node allows the interval (lo, hi] that its predicates leave (lo the largest
+// threshold of a "z > t", hi the smallest of a "z <= t"); it goes left when
+// the interval reaches below thr (lo < thr), right when it reaches above
+// (hi > thr), both ways when it straddles thr, and nowhere when it is empty.
+// The split whose larger side is smallest is taken (ties: the fewer nodes on
+// both sides together), so that the nodes of a tree level, which split into
+// halves on the predicate of their common ancestor, give a tree of the level's
+// depth, and the cells of a grid of bins on a few attributes a tree of about
+// log2 of their number.  A set that no split divides, or a tree that reached
+// kMaxDt entries, kMaxCand candidates or kMaxWork predicate visits, ends in a
+// leaf (its nodes are checked in full).  Once a cap is reached only the
+// pending right subtrees of the current path (at most one per level) still
+// add leaves, so the tables stay within the caps plus 25 sets.
 constexpr size_t kMaxDt = size_t(1) << 16;
+constexpr size_t kMaxCand = size_t(1) << 20;
+constexpr size_t kMaxWork = size_t(1) << 26;
+
+// the interval (lo, hi] that node `preds` allows on z; (+inf, -inf] when empty
+void node_interval(const std::vector<TreePred>& preds, int z, float* lo, float* hi) {
+  float a = -INFINITY, b = INFINITY;
+  for (const TreePred& p : preds)
+    if (p.z == z) {
+      if (p.op == 0) b = std::min(b, p.thr);
+      else a = std::max(a, p.thr);
+    }
+  if (!(a < b)) {
+    a = INFINITY;
+    b = -INFINITY;
+  }
+  *lo = a;
+  *hi = b;
+}
 
 int build_dt(const std::vector<std::vector<TreePred>>& nodes, const std::vector<int>& set, int depth,
-             std::vector<TreeDt>* dt, std::vector<int32_t>* cand) {
+             std::vector<TreeDt>* dt, std::vector<int32_t>* cand, size_t* work) {
   const int at = (int)dt->size();
   dt->push_back(TreeDt{});
   auto leaf = [&]() {
@@ -122,37 +147,48 @@ int build_dt(const std::vector<std::vector<TreePred>>& nodes, const std::vector<
     cand->insert(cand->end(), set.begin(), set.end());
     return at;
   };
-  if (set.size() <= 1 || depth >= 24 || dt->size() >= kMaxDt) return leaf();
-  std::map<std::pair<int, float>, std::pair<int, int>> cnt;  // (z, thr) -> (nodes only left, only right)
-  for (int n : set)
-    for (const TreePred& p : nodes[n]) {
-      auto& c = cnt[{p.z, p.thr}];
-      (p.op == 0 ? c.first : c.second)++;
-    }
+  if (set.size() <= 1 || depth >= 24 || dt->size() >= kMaxDt || cand->size() >= kMaxCand || *work >= kMaxWork)
+    return leaf();
   const int n = (int)set.size();
+  // candidate thresholds per attribute
+  std::map<int, std::vector<float>> thrs;
+  for (int i : set)
+    for (const TreePred& p : nodes[i])
+      if (p.thr == p.thr) thrs[p.z].push_back(p.thr);  // (a NaN threshold orders nothing)
   int best_max = n, best_sum = 2 * n;
   std::pair<int, float> best{-1, 0.f};
-  for (auto& kv : cnt) {
-    const int l = n - kv.second.second, r = n - kv.second.first;  // sizes of the two sides
-    if (l >= n || r >= n) continue;
-    const int mx = std::max(l, r), sum = l + r;
-    if (mx < best_max || (mx == best_max && sum < best_sum)) {
-      best_max = mx;
-      best_sum = sum;
-      best = kv.first;
+  std::vector<float> lo(n), hi(n);
+  for (auto& kv : thrs) {
+    const int z = kv.first;
+    for (int k = 0; k < n; ++k) node_interval(nodes[set[k]], z, &lo[k], &hi[k]);
+    *work += static_cast<size_t>(n) * (nodes[set[0]].size() + 1);
+    std::sort(lo.begin(), lo.end());
+    std::sort(hi.begin(), hi.end());
+    std::vector<float>& ts = kv.second;
+    std::sort(ts.begin(), ts.end());
+    ts.erase(std::unique(ts.begin(), ts.end()), ts.end());
+    for (float t : ts) {
+      const int l = (int)(std::lower_bound(lo.begin(), lo.end(), t) - lo.begin());  // lo < t
+      const int r = (int)(hi.end() - std::upper_bound(hi.begin(), hi.end(), t));   // hi > t
+      if (l >= n || r >= n) continue;  // one side keeps every node: no progress
+      const int mx = std::max(l, r), sum = l + r;
+      if (mx < best_max || (mx == best_max && sum < best_sum)) {
+        best_max = mx;
+        best_sum = sum;
+        best = {z, t};
+      }
     }
   }
   if (best.first < 0) return leaf();
   std::vector<int> L, R;
-  for (int n : set) {
-    bool le = false, gt = false;
-    for (const TreePred& p : nodes[n])
-      if (p.z == best.first && p.thr == best.second) (p.op == 0 ? le : gt) = true;
-    if (!gt) L.push_back(n);
-    if (!le) R.push_back(n);
+  for (int i : set) {
+    float a, b;
+    node_interval(nodes[i], best.first, &a, &b);
+    if (a < best.second) L.push_back(i);
+    if (b > best.second) R.push_back(i);
   }
-  const int l = build_dt(nodes, L, depth + 1, dt, cand);
-  const int r = build_dt(nodes, R, depth + 1, dt, cand);
+  const int l = build_dt(nodes, L, depth + 1, dt, cand, work);
+  const int r = build_dt(nodes, R, depth + 1, dt, cand, work);
   (*dt)[at] = TreeDt{(int16_t)best.first, 0, best.second, l, r};
   return at;
 }
@@ -318,7 +354,8 @@ lmf_status tree_plan(const std::vector<TreeAggIn>& in, const std::map<std::strin
     }
     if (!placed) T.groups.push_back({n});
   }
-  for (auto& g : T.groups) T.droot.push_back(build_dt(T.nodes, g, 0, &T.dt, &T.dcand));
+  size_t dt_work = 0;
+  for (auto& g : T.groups) T.droot.push_back(build_dt(T.nodes, g, 0, &T.dt, &T.dcand, &dt_work));
   int mz = 0;
   for (auto& kv : zidx) mz = std::max(mz, kv.second + 1);
   T.mp = 16;

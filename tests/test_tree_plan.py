@@ -46,7 +46,7 @@ def test_tree_planner(check_exe):
     r = subprocess.run([str(check_exe)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
     ok = [l for l in r.stdout.splitlines() if l.startswith('ok ')]
-    assert len(ok) == 12, r.stdout
+    assert len(ok) == 17, r.stdout
 
 
 _HOST = r'''#include <cstdint>
@@ -93,7 +93,7 @@ def test_generated_node_search(check_exe, tmp_path):
     r = subprocess.run([str(check_exe), '--emit', str(out)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
     cases = sorted(p for p in os.listdir(out) if p.startswith('case_') and p.endswith('.cu'))
-    assert len(cases) == 6, r.stdout
+    assert len(cases) == 7, r.stdout
     groups = [int(m) for m in re.findall(r'(\d+) groups', r.stdout)]
     assert groups[0] == 1 and max(groups[1:]) > 1, r.stdout     # one group, and cases with several
     for name in cases:
