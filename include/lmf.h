@@ -31,8 +31,8 @@
  *   - LMF_LOG=1 in the environment prints every plan (root, probe groups,
  *     record sizes, root-scan form and launch shape) and the stage times of
  *     lmf_run_profiled to stderr.
- *   - LMF_JIT_DUMP=<directory> writes the CUDA source of every root scan the
- *     planner compiles there (<kernel>_<hash of the source>.cu).
+ *   - LMF_JIT_DUMP=<directory> writes the CUDA source of every root scan and
+ *     tree pass the planner compiles there (<kernel>_<hash of the source>.cu).
  */
 #ifndef LMF_H_
 #define LMF_H_
@@ -135,10 +135,12 @@ typedef struct {
   int32_t flags;          /* LMF_PLAN_* bits */
 } lmf_plan_opts;
 
-/* lmf_plan_opts.flags: the plain root scan is compiled at plan time with the
-   plan's layout as constants (the compilation step of Sec. 1.2 / App. C, done
-   with NVRTC) unless this bit is set or NVRTC cannot be loaded; the
-   interpreted kernel (same arithmetic, same results) runs otherwise. */
+/* lmf_plan_opts.flags: the plain root scan, and for a batch with filtered
+   aggregates the tree pass (its row pass and its search for a row's node over
+   the nodes' thresholds), are compiled at plan time with the plan's layout as
+   constants (the compilation step of Sec. 1.2 / App. C, done with NVRTC)
+   unless this bit is set or NVRTC cannot be loaded; the interpreted kernels
+   (same arithmetic, same results) run otherwise. */
 #define LMF_PLAN_NO_JIT 1
 /* lmf_plan_opts.flags: keep every Gram block of the plain-precision root scan at
    the row level (FP32 products of the whole z = [1, x_root, view means]).  By
@@ -364,10 +366,10 @@ lmf_status lmf_plan_candidates(lmf_ctx* ctx, int batch_id, const lmf_plan_opts* 
                                lmf_plan_opts* out, int max, int* n);
 
 /*
- * Compile, on up to `threads` host threads (0: 8), the plan-time root scans of
- * every candidate of lmf_plan_candidates(base) into the process-wide cache of
- * compiled sources, so that planning those candidates afterwards finds them
- * compiled.  The candidates are planned without compiling (the batch is left
+ * Compile, on up to `threads` host threads (0: 8), the plan-time root scans
+ * (and tree passes) of every candidate of lmf_plan_candidates(base) into the
+ * process-wide cache of compiled sources, so that planning those candidates
+ * afterwards finds them compiled.  The candidates are planned without compiling (the batch is left
  * without a plan: plan it again before running).  *n_compiled (may be NULL)
  * gets the number of sources compiled.  Errors: LMF_ERR_ARG, LMF_ERR_STATE
  * before lmf_declare_join.
