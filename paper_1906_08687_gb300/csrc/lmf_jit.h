@@ -1,4 +1,4 @@
-// lmf_jit.h -- plan-time compilation of the root scan.
+// lmf_jit.h -- plan-time compilation of the root scan and the tree pass.
 //
 // The paper's engine compiles each aggregate batch into code specialised to
 // it (Sec. 1.2, compilation layer; App. C).  Here the plain root scan's row
@@ -7,6 +7,8 @@
 // shared-memory offsets) and compiled for sm_103a by NVRTC; the tile loop and
 // the Gram phase are the same device code as the interpreted kernel
 // (lmf_root_plain.cuh), so both compute the same values in the same order.
+// The tree pass of filtered aggregates is compiled the same way (its row pass
+// and its node search generated, lmf_jit_tree.cu; its body lmf_tree_dev.cuh).
 #pragma once
 
 #include <string>
