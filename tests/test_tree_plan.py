@@ -46,7 +46,7 @@ def test_tree_planner(check_exe):
     r = subprocess.run([str(check_exe)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
     ok = [l for l in r.stdout.splitlines() if l.startswith('ok ')]
-    assert len(ok) == 17, r.stdout
+    assert len(ok) == 18, r.stdout
 
 
 _HOST = r'''#include <cstdint>

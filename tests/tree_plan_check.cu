@@ -359,6 +359,69 @@ int main(int argc, char** argv) {
       expect(all_points_find_their_node(T, 6, 20000), "every point finds its grid cell");
     }
   }
+  {  // random batches: every aggregate's node, split threshold and moment are its own factors
+    bool faithful = true;
+    for (int trial = 0; trial < 20 && faithful; ++trial) {
+      std::map<std::string, int> zidx;
+      for (int i = 0; i < 6; ++i) zidx["f" + std::to_string(i)] = 1 + i;
+      zidx["y"] = 7;
+      uint64_t x = 1000 + trial;
+      auto next = [&]() {
+        x = x * 6364136223846793005ull + 1442695040888963407ull;
+        return static_cast<uint32_t>(x >> 33);
+      };
+      const double grid_t[7] = {-1.5, -0.25, 0.0, 0.1, 0.75, 2.0, 1e-3};
+      std::vector<TreeAggIn> in(1500);
+      for (auto& a : in) {
+        const int nt = 1 + next() % 5;
+        for (int k = 0; k < nt; ++k) {
+          const double t = next() % 4 ? grid_t[next() % 7] : (static_cast<double>(next()) / 4294967296.0 - 0.25) * 3.0;
+          a.factors.push_back({"f" + std::to_string(next() % 6), next() % 2 ? LMF_LE : LMF_GT, 0, t});
+        }
+        switch (next() % 4) {
+          case 1: a.factors.push_back({"y", LMF_POW, 1, 0.0}); break;
+          case 2: a.factors.push_back({"y", LMF_POW, 2, 0.0}); break;
+          case 3:
+            a.factors.push_back({"f0", LMF_POW, 1, 0.0});
+            a.factors.push_back({"y", LMF_POW, 1, 0.0});
+            break;
+          default: break;
+        }
+        // factors in any order
+        for (size_t k = a.factors.size(); k > 1; --k) std::swap(a.factors[k - 1], a.factors[next() % k]);
+      }
+      TreePlan tp;
+      std::string msg;
+      if (tree_plan(in, zidx, &tp, &msg) != LMF_OK || tp.impl->outs.size() != in.size()) {
+        faithful = false;
+        break;
+      }
+      const TreePlanImpl& T = *tp.impl;
+      for (size_t i = 0; i < in.size() && faithful; ++i) {
+        const auto& o = T.outs[i];
+        std::set<std::tuple<int, int, float>> want, got;
+        std::vector<int> mono_want;
+        for (const auto& f : in[i].factors) {
+          if (f.kind == LMF_POW) {
+            for (int e = 0; e < f.power; ++e) mono_want.push_back(zidx.at(f.attr));
+          } else {
+            want.insert({zidx.at(f.attr), f.kind == LMF_LE ? 0 : 1, round_down_f32(f.thr)});
+          }
+        }
+        for (const TreePred& p : T.nodes[o.node]) got.insert({p.z, p.op, p.thr});
+        got.insert({T.split_z[o.split], o.op, T.thr[o.split][o.j]});
+        std::vector<int> mono_got;
+        if (T.mom_z[o.mom].first >= 0) mono_got.push_back(T.mom_z[o.mom].first);
+        if (T.mom_z[o.mom].second >= 0) mono_got.push_back(T.mom_z[o.mom].second);
+        std::sort(mono_want.begin(), mono_want.end());
+        std::sort(mono_got.begin(), mono_got.end());
+        faithful = want == got && mono_want == mono_got;
+        if (!faithful) std::printf("aggregate %zu of trial %d decomposed wrongly\n", i, trial);
+      }
+      faithful = faithful && all_points_find_their_node(T, 8, 2000);
+    }
+    expect(faithful, "random batches decompose into their own factors, every point finds its nodes");
+  }
   {  // random overlapping conjunctions: several groups, every point finds its node
     std::map<std::string, int> zidx;
     TreePlan tp;
