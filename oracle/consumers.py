@@ -1,7 +1,9 @@
 """FP64 reference of the applications that consume an aggregate batch (Sec. 2):
 ridge linear regression trained by batch gradient descent over the covar
 matrix, the mutual information of two categorical attributes from the four
-count queries of Eq. mi, and the Chow-Liu tree over those values.
+count queries of Eq. mi, the Chow-Liu tree over those values, and the split
+choice of a classification tree (CART) from the class counts of Eq.
+classification-tree.
 
 TEST INFRASTRUCTURE ONLY (imported by tests; the engine never imports it).
 
@@ -17,6 +19,13 @@ Readings where the paper leaves a choice:
   spanning tree of the complete graph weighted by mutual information (an edge
   that would close a cycle is skipped); ties go to the pair (i, j), i < j,
   that comes first in row-major order.
+* Classification trees (Sec. 2, decision trees): the cost of a split of the
+  fragment D_i into the rows with X_j <= t and the rest is the entropy or Gini
+  index of each side weighted by the side's share of D_i (the CART cost of a
+  split; the paper gives the index of one fragment); entropy with the natural
+  logarithm (the chosen split does not depend on the base); a split that
+  leaves a side empty is not a split; ties go to the first candidate in the
+  order given (features in batch order, thresholds ascending).
 """
 from __future__ import annotations
 
@@ -145,3 +154,83 @@ def chow_liu_tree(n: int, mi: Dict[Tuple[int, int], float]) -> List[Tuple[int, i
         if len(edges) == n - 1:
             break
     return edges
+
+
+# ----------------------------------------------------------------------------
+# classification trees
+# ----------------------------------------------------------------------------
+def impurity(counts: Sequence[float], criterion: str = 'gini') -> float:
+    """Entropy -sum_k pi_k log pi_k or Gini index 1 - sum_k pi_k^2 of a fragment
+    with the given class counts, pi_k = count_k / |D_i| (Sec. 2); 0 for an
+    empty fragment."""
+    c = np.asarray(counts, np.float64)
+    n = float(c.sum())
+    if n <= 0:
+        return 0.0
+    pi = c / n
+    if criterion == 'gini':
+        return 1.0 - math.fsum(float(p) * float(p) for p in pi)
+    if criterion == 'entropy':
+        return -math.fsum(float(p) * math.log(float(p)) for p in pi if p > 0)
+    raise ValueError(criterion)
+
+
+def split_cost(left: Sequence[float], total: Sequence[float], criterion: str = 'gini') -> float:
+    """Cost of splitting a fragment with class counts `total` into `left` (the
+    rows with X_j <= t) and total - left: each side's impurity weighted by its
+    share of the fragment."""
+    lft = np.asarray(left, np.float64)
+    tot = np.asarray(total, np.float64)
+    rgt = tot - lft
+    n = float(tot.sum())
+    return (float(lft.sum()) / n) * impurity(lft, criterion) + (float(rgt.sum()) / n) * impurity(rgt, criterion)
+
+
+def best_split(total: Sequence[float], left: Sequence[Tuple[object, Sequence[float]]],
+               criterion: str = 'gini'):
+    """The candidate of least cost among `left`, a sequence of (condition,
+    class counts of the rows that satisfy it) in candidate order; returns
+    (condition, cost), or None when no candidate leaves both sides non-empty."""
+    n = float(np.asarray(total, np.float64).sum())
+    best = None
+    for cond, counts in left:
+        nl = float(np.asarray(counts, np.float64).sum())
+        if nl <= 0 or nl >= n:
+            continue
+        cost = split_cost(counts, total, criterion)
+        if best is None or cost < best[1]:
+            best = (cond, cost)
+    return best
+
+
+def classification_level_splits(batch, values, nodes, features, thresholds, n_classes: int,
+                                criterion: str = 'gini'):
+    """The CART step for one tree level from the results of a classification
+    level batch (the layout of workloads.config3_classification): per node, the
+    class counts of the node, of every candidate f <= t, and the best split.
+    Returns, per node, (node class counts, best (f, t) or None, its cost)."""
+    out = []
+    a = 0
+    for node in nodes:
+        total = np.asarray(values[a], np.int64).reshape(n_classes)
+        assert int(values[a + 1][0]) == int(total.sum()) and batch[a].factors == tuple(node)
+        a += 2
+        cands = []
+        for f in features:
+            for t in thresholds[f]:
+                assert batch[a].factors == tuple(node) + ((f, 'le', float(t)),)
+                counts = np.asarray(values[a], np.int64).reshape(n_classes)
+                assert int(values[a + 1][0]) == int(counts.sum())
+                cands.append(((f, float(t)), counts))
+                a += 2
+        b = best_split(total, cands, criterion)
+        out.append((total, None if b is None else b[0], None if b is None else b[1]))
+    assert a == len(batch)
+    return out
+
+
+def cart_children(node, split) -> List[tuple]:
+    """The two children of a node split on (f, t): the node's conditions with
+    f <= t, and with f > t."""
+    f, t = split
+    return [tuple(node) + ((f, 'le', float(t)),), tuple(node) + ((f, 'gt', float(t)),)]

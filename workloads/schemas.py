@@ -303,22 +303,17 @@ def _joined_sample(sch: Schema, attr: str, rows: np.ndarray) -> np.ndarray:
     return sch.owner(attr).col(attr).data[idx]
 
 
-def config3(n_fact: int = 10_000_000, seed: Optional[int] = None, n_nodes_depth: int = 6,
-            n_thresholds: int = 32, sample_rows: int = 1_000_000,
-            fact_order: str = 'sorted') -> Tuple[Schema, List[Agg]]:
-    rng = _rng(SEED_BASE + 3 if seed is None else seed)
-    sch, feats, _ = _snowflake(
-        rng, n_fact, 6,
-        dim_feat={'D1': 4, 'Sub1': 2, 'Sub2': 1, 'D2': 3, 'D3': 2, 'D4': 2},
-        dim_cat={}, fk_s=0.8, cat_s=1.1, cat_lo=5, cat_hi=1000, label=True, fact_order=fact_order)
-    # per feature: thresholds at the empirical j/(T+1) quantiles of a sample
+def _tree_level(sch: Schema, feats: Sequence[str], rng: np.random.Generator, n_fact: int,
+                n_nodes_depth: int, n_thresholds: int, sample_rows: int):
+    """Thresholds per feature at the empirical j/(T+1) quantiles of a sample of
+    joined rows, and the leaves of a random complete tree of the given depth
+    (each internal node a (feature, one of its thresholds) condition)."""
     rows = rng.integers(0, n_fact, size=min(sample_rows, n_fact))
     thr = {}
     for f in feats:
         v = _joined_sample(sch, f, rows).astype(np.float64)
         q = np.quantile(v, np.arange(1, n_thresholds + 1) / (n_thresholds + 1))
         thr[f] = np.unique(q.astype(np.float32)).astype(np.float64)
-    # a random complete tree; internal node = (feature, one of its thresholds)
     leaves: List[Tuple[Tuple[str, str, float], ...]] = [()]
     for _ in range(n_nodes_depth):
         nxt = []
@@ -328,6 +323,18 @@ def config3(n_fact: int = 10_000_000, seed: Optional[int] = None, n_nodes_depth:
             nxt.append(path + ((f, 'le', t),))
             nxt.append(path + ((f, 'gt', t),))
         leaves = nxt
+    return thr, leaves
+
+
+def config3(n_fact: int = 10_000_000, seed: Optional[int] = None, n_nodes_depth: int = 6,
+            n_thresholds: int = 32, sample_rows: int = 1_000_000,
+            fact_order: str = 'sorted') -> Tuple[Schema, List[Agg]]:
+    rng = _rng(SEED_BASE + 3 if seed is None else seed)
+    sch, feats, _ = _snowflake(
+        rng, n_fact, 6,
+        dim_feat={'D1': 4, 'Sub1': 2, 'Sub2': 1, 'D2': 3, 'D3': 2, 'D4': 2},
+        dim_cat={}, fk_s=0.8, cat_s=1.1, cat_lo=5, cat_hi=1000, label=True, fact_order=fact_order)
+    thr, leaves = _tree_level(sch, feats, rng, n_fact, n_nodes_depth, n_thresholds, sample_rows)
     batch = []
     for node in leaves:
         for f in feats:
@@ -337,6 +344,49 @@ def config3(n_fact: int = 10_000_000, seed: Optional[int] = None, n_nodes_depth:
                     batch.append(Agg(factors=node + ((f, 'le', float(t)),) + lab))
     sch.meta.update(name=f'tree-level-{n_fact}', features=feats, thresholds=thr,
                     nodes=leaves, label='y')
+    return sch, batch
+
+
+def config3_classification(n_fact: int = 1_000_000, n_classes: int = 4, seed: Optional[int] = None,
+                           n_nodes_depth: int = 6, n_thresholds: int = 32, sample_rows: int = 1_000_000,
+                           fact_order: str = 'sorted') -> Tuple[Schema, List[Agg]]:
+    """A classification-tree level (Sec. 2, decision trees): config 3's
+    snowflake and tree with a categorical label `cls` on the fact relation
+    instead of the continuous y.  The class is a noisy quantile bin of
+    x0 + d1_x0 + 0.5 d2_x0, so splits on those features lower the impurity.
+
+    Per leaf node nu, feature f and threshold t the two queries of Eq.
+    classification-tree and its total: COUNT grouped by cls and COUNT, both
+    under alpha = nu and f <= t; per node the same two under nu alone (the
+    counts the other side of every split is the difference from).  Order:
+    for each node, [CT(cls; nu), CT(nu)], then for each f, t:
+    [CT(cls; nu, f <= t), CT(nu, f <= t)]."""
+    rng = _rng(SEED_BASE + 31 if seed is None else seed)
+    sch, feats, _ = _snowflake(
+        rng, n_fact, 6,
+        dim_feat={'D1': 4, 'Sub1': 2, 'Sub2': 1, 'D2': 3, 'D3': 2, 'D4': 2},
+        dim_cat={}, fk_s=0.8, cat_s=1.1, cat_lo=5, cat_hi=1000, label=False, fact_order=fact_order)
+    rows = np.arange(n_fact)
+    score = (_joined_sample(sch, 'x0', rows).astype(np.float64)
+             + _joined_sample(sch, 'd1_x0', rows).astype(np.float64)
+             + 0.5 * _joined_sample(sch, 'd2_x0', rows).astype(np.float64))
+    score = score + 0.5 * np.std(score) * rng.standard_normal(n_fact)
+    edges = np.quantile(score, np.arange(1, n_classes) / n_classes)
+    cls = np.searchsorted(edges, score, side='right').astype(np.int32)
+    fact = sch.rel('F')
+    fact.columns.append(Column('cls', 'cat', cls, n_classes))
+    thr, leaves = _tree_level(sch, feats, rng, n_fact, n_nodes_depth, n_thresholds, sample_rows)
+    batch = []
+    for node in leaves:
+        batch.append(Agg(group_by=('cls',), factors=node))
+        batch.append(Agg(factors=node))
+        for f in feats:
+            for t in thr[f]:
+                alpha = node + ((f, 'le', float(t)),)
+                batch.append(Agg(group_by=('cls',), factors=alpha))
+                batch.append(Agg(factors=alpha))
+    sch.meta.update(name=f'classification-tree-level-{n_fact}', features=feats, thresholds=thr,
+                    nodes=leaves, label='cls', n_classes=n_classes)
     return sch, batch
 
 
