@@ -4,7 +4,7 @@ paper's datasets (Sec. 4, App. A), at reduced row counts."""
 import numpy as np
 import pytest
 
-from workloads import (config1, config2, config3, config4, config5_schema,
+from workloads import (config1, config2, config3, config3_classification, config4, config5_schema,
                        sort_by_join_attributes, zipf_keys)
 from workloads.schemas import Column, Relation, _rng
 
@@ -128,6 +128,26 @@ def test_config3_recipe():
         assert np.array_equal(t.astype(np.float32).astype(np.float64), t)   # FP32-exact
     assert len(batch) == 64 * sum(len(thr[f]) for f in feats) * 3
     assert sch.rel('F').col('y').data.dtype == np.float32
+
+
+def test_config3_classification_recipe():
+    sch, batch = config3_classification(100_000, n_classes=4, sample_rows=100_000)
+    feats, thr, nodes = sch.meta['features'], sch.meta['thresholds'], sch.meta['nodes']
+    assert len(feats) == 20 and len(nodes) == 64 and sch.meta['n_classes'] == 4
+    cls = sch.rel('F').col('cls')
+    assert cls.role == 'cat' and cls.cat_domain == 4 and cls.data.dtype == np.int32
+    share = np.bincount(cls.data, minlength=4) / len(cls.data)
+    assert np.all(np.abs(share - 0.25) < 0.01)                          # quantile bins of the score
+    assert 'y' not in sch.rel('F').names()
+    for f in feats:
+        assert np.array_equal(thr[f].astype(np.float32).astype(np.float64), thr[f])
+    # per node: its two queries, then two per (feature, threshold)
+    assert len(batch) == 64 * (2 + 2 * sum(len(thr[f]) for f in feats))
+    assert batch[0].group_by == ('cls',) and batch[1].group_by == () and batch[0].factors == nodes[0]
+    assert batch[2].factors == nodes[0] + ((feats[0], 'le', float(thr[feats[0]][0])),)
+    # the seed repeats its data
+    sch2, batch2 = config3_classification(100_000, n_classes=4, sample_rows=100_000)
+    assert np.array_equal(sch2.rel('F').col('cls').data, cls.data) and batch2 == batch
 
 
 def test_config4_recipe():
