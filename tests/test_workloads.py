@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from workloads import (config1, config2, config3, config3_classification, config4, config5_schema,
-                       sort_by_join_attributes, zipf_keys)
+                       many_to_many, sort_by_join_attributes, zipf_keys)
 from workloads.schemas import Column, Relation, _rng
 
 
@@ -148,6 +148,27 @@ def test_config3_classification_recipe():
     # the seed repeats its data
     sch2, batch2 = config3_classification(100_000, n_classes=4, sample_rows=100_000)
     assert np.array_equal(sch2.rel('F').col('cls').data, cls.data) and batch2 == batch
+
+
+def test_many_to_many_recipe():
+    sch, batch = many_to_many(50_000, n_user=5_000, n_business=1_000, seed=2)
+    assert [r.name for r in sch.relations] == ['Review', 'User', 'Business', 'Category', 'Attribute']
+    R, C, A = sch.rel('Review'), sch.rel('Category'), sch.rel('Attribute')
+    assert R.nrows == 50_000 and sch.rel('User').nrows == 5_000 and sch.rel('Business').nrows == 1_000
+    nc = np.bincount(C.col('business_id').data, minlength=1_000)
+    na = np.bincount(A.col('business_id').data, minlength=1_000)
+    assert nc.min() >= 1 and nc.max() <= 8 and na.min() == 0 and na.max() <= 12
+    assert np.all(np.diff(C.col('business_id').data) >= 0) and C.col('cat').data.max() < 40
+    assert 0 <= R.col('user_id').data.min() and R.col('user_id').data.max() < 5_000
+    assert set(np.unique(R.col('stars').data)) <= {1.0, 2.0, 3.0, 4.0, 5.0}
+    assert len(batch) == 45 + 1 and batch[-1].group_by == ('cat',)
+    # sorted on the join attributes (fewest distinct values first: business, then user),
+    # and the random order holds the same rows
+    order = np.lexsort([R.col('user_id').data, R.col('business_id').data])
+    assert np.array_equal(order, np.arange(R.nrows))
+    rnd, _ = many_to_many(50_000, n_user=5_000, n_business=1_000, seed=2, fact_order='random')
+    for c in R.names():
+        assert np.array_equal(np.sort(R.col(c).data), np.sort(rnd.rel('Review').col(c).data))
 
 
 def test_config4_recipe():

@@ -8,7 +8,7 @@ from .schemas import (  # noqa: F401
     Column, Relation, Schema, Agg,
     zipf_keys, sort_by_join_attributes, covar_batch, grouped_batch, pair_count_batch, cube_batch,
     config1, config2, config3, config3_classification, config4, config5_schema, tiny_schema, chain_schema,
-    spread_keys,
+    spread_keys, many_to_many,
     SEED_BASE,
 )
 from .tensors import to_device, to_pinned  # noqa: F401

@@ -587,3 +587,55 @@ def chain_schema(n: int, size: int, dom: int, seed: int, group_copies: bool = Fa
         if k > 1:
             edges.append((f'S{k - 1}', f'S{k}', f'X{k}'))
     return Schema(rels, edges, 'S1', meta={'name': f'chain-{n}'})
+
+
+# ----------------------------------------------------------------------------
+# a many-to-many join much larger than its inputs (Sec. 4, the Yelp shape)
+# ----------------------------------------------------------------------------
+def many_to_many(n_review: int = 1_000_000, n_user: int = 50_000, n_business: int = 20_000,
+                 max_categories: int = 8, max_attributes: int = 12, seed: Optional[int] = None,
+                 fact_order: str = 'sorted') -> Tuple[Schema, List[Agg]]:
+    """Review(user_id, business_id, stars, useful) as the root; User(user_id;
+    fans, review_count) and Business(business_id; bstars, lat) with unique
+    keys; Category(business_id; cat, cat_w) and Attribute(business_id;
+    attr_val) with 1..max_categories and 0..max_attributes rows per business,
+    so that a review joins with |Category(b)| x |Attribute(b)| tuples and the
+    join is some tens of times larger than its inputs (the shape of the Yelp
+    dataset of Sec. 4, where a business has many categories and attributes);
+    a business without attributes drops its reviews from the join.  Foreign
+    keys Zipf 0.8; categories Zipf 1.0 over 40 values.
+
+    Batch: the covar batch over the eight features (COUNT, SUM(x_i),
+    SUM(x_i x_j): every product of two features of the fanning-out relations
+    sums over their cross product per business) and COUNT grouped by cat."""
+    _check_order(fact_order)
+    rng = _rng(SEED_BASE + 41 if seed is None else seed)
+    users = zipf_keys(rng, n_review, n_user, 0.8)
+    biz = zipf_keys(rng, n_review, n_business, 0.8)
+    review = Relation('Review', [Column('user_id', 'key', users), Column('business_id', 'key', biz),
+                                 Column('stars', 'cont', rng.integers(1, 6, n_review).astype(np.float32)),
+                                 Column('useful', 'cont', _feature(rng, n_review, 1, np.float32))])
+    if fact_order == 'sorted':
+        review = sort_by_join_attributes(review, ['user_id', 'business_id'])
+    user = Relation('User', [Column('user_id', 'key', np.arange(n_user, dtype=np.int32)),
+                             Column('fans', 'cont', _feature(rng, n_user, 1, np.float32)),
+                             Column('review_count', 'cont', _feature(rng, n_user, 3, np.float32))])
+    business = Relation('Business', [Column('business_id', 'key', np.arange(n_business, dtype=np.int32)),
+                                     Column('bstars', 'cont', _feature(rng, n_business, 0, np.float32)),
+                                     Column('lat', 'cont', _feature(rng, n_business, 2, np.float32))])
+    nc = rng.integers(1, max_categories + 1, n_business)
+    cb = np.repeat(np.arange(n_business, dtype=np.int32), nc)
+    category = Relation('Category', [Column('business_id', 'key', cb),
+                                     Column('cat', 'cat', zipf_keys(rng, len(cb), 40, 1.0), 40),
+                                     Column('cat_w', 'cont', _feature(rng, len(cb), 0, np.float32))])
+    na = rng.integers(0, max_attributes + 1, n_business)
+    ab = np.repeat(np.arange(n_business, dtype=np.int32), na)
+    attribute = Relation('Attribute', [Column('business_id', 'key', ab),
+                                       Column('attr_val', 'cont', _feature(rng, len(ab), 2, np.float32))])
+    sch = Schema([review, user, business, category, attribute],
+                 [('Review', 'User', 'user_id'), ('Review', 'Business', 'business_id'),
+                  ('Business', 'Category', 'business_id'), ('Business', 'Attribute', 'business_id')],
+                 'Review')
+    feats = ['stars', 'useful', 'fans', 'review_count', 'bstars', 'lat', 'cat_w', 'attr_val']
+    sch.meta.update(name=f'many-to-many-{n_review}', features=feats, cats=['cat'])
+    return sch, covar_batch(feats) + [Agg(group_by=('cat',))]
