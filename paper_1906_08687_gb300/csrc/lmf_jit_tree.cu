@@ -75,13 +75,15 @@ std::string jit_tree_source(const RootParams& rp, const TreeJitSpec& t) {
   for (const auto& e : t.dt)
     if (e.leaf)
       for (int c = e.left; c < e.left + e.right; ++c) checks += 1 + t.preds[t.cand[c]].size();
-  if (t.dt.size() > kJitTreeMaxEntries || checks > kJitTreeMaxChecks) {
-    o << "    return tree_node_of(d, g, zrow);\n  }\n};\n}  // namespace lmf\n"
+  // the end of node() and the kernel over the library's body of the pass
+  auto finish = [&](const char* last) {
+    o << "    " << last << "\n  }\n};\n}  // namespace lmf\n"
       << "extern \"C\" __global__ void __launch_bounds__(lmf::kTreeThreads, 2) lmf_tree_jit(\n"
       << "    const __grid_constant__ lmf::RootParams p, const __grid_constant__ lmf::TreeDev d) {\n"
       << "  lmf::tree_body<lmf::JitTreeRow, " << t.mp << ">(p, d);\n}\n";
     return o.str();
-  }
+  };
+  if (t.dt.size() > kJitTreeMaxEntries || checks > kJitTreeMaxChecks) return finish("return tree_node_of(d, g, zrow);");
   std::function<void(int, int)> gen = [&](int i, int ind) {
     const std::string sp(static_cast<size_t>(ind), ' ');
     const TreeJitSpec::Entry& e = t.dt[i];
@@ -107,11 +109,7 @@ std::string jit_tree_source(const RootParams& rp, const TreeJitSpec& t) {
     gen(t.droot[g], 6);
     o << "    }\n";
   }
-  o << "    return static_cast<int>(kNoNode);\n  }\n};\n}  // namespace lmf\n"
-    << "extern \"C\" __global__ void __launch_bounds__(lmf::kTreeThreads, 2) lmf_tree_jit(\n"
-    << "    const __grid_constant__ lmf::RootParams p, const __grid_constant__ lmf::TreeDev d) {\n"
-    << "  lmf::tree_body<lmf::JitTreeRow, " << t.mp << ">(p, d);\n}\n";
-  return o.str();
+  return finish("return static_cast<int>(kNoNode);");
 }
 
 }  // namespace lmf
