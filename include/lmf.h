@@ -243,8 +243,10 @@ lmf_status lmf_declare_join(lmf_ctx* ctx, int n_edges, const int* parent_rel,
  * factor is a power (COUNT, possibly filtered), otherwise a float64 sum per
  * group.  Groups are dense, row-major over the group-by attributes' values;
  * empty groups read 0.
- * Errors: LMF_ERR_ARG (unknown attribute, bad factor), LMF_ERR_DTYPE (group-by
- * on a non-categorical attribute), LMF_ERR_STATE (before lmf_declare_join).
+ * Errors: LMF_ERR_ARG (unknown attribute, bad factor: a power other than 1 or
+ * 2, an unknown kind, a NaN threshold), LMF_ERR_DTYPE (group-by on a
+ * non-categorical attribute, a factor on a non-continuous one), LMF_ERR_STATE
+ * (before lmf_declare_join).
  */
 lmf_status lmf_declare_batch(lmf_ctx* ctx, const lmf_agg_spec* aggs, int n, int* batch_id);
 

@@ -679,6 +679,8 @@ lmf_status lmf_declare_batch(lmf_ctx* c, const lmf_agg_spec* aggs, int n, int* b
         if (x.power != 1 && x.power != 2) return fail(c, LMF_ERR_ARG, "aggregate %d: power %d", a, x.power);
       } else if (x.kind != LMF_LE && x.kind != LMF_GT) {
         return fail(c, LMF_ERR_ARG, "aggregate %d: factor kind %d", a, x.kind);
+      } else if (std::isnan(x.threshold)) {  // 1[x <= NaN] orders nothing
+        return fail(c, LMF_ERR_ARG, "aggregate %d: NaN threshold on %s", a, x.attr);
       }
       h.f.push_back({x.attr, x.kind, x.power, x.threshold});
     }
