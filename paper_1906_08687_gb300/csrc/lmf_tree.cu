@@ -27,7 +27,11 @@
 //                dimension attribute over a root sorted on its join keys --
 //                the warp sums its moments first (three 32-bit warp
 //                reductions per 64-bit value) and one lane issues the
-//                reduction.  Nothing per row leaves the SM.
+//                reduction.  Nothing per row leaves the SM.  Its body is
+//                tree_body (lmf_tree_dev.cuh); lmf_tree_jit, compiled for the
+//                plan at plan time (lmf_jit_tree.cu), runs the same body with
+//                the row pass and the node search generated for the plan, and
+//                replaces k_tree_fused when it was compiled.
 //   k_tree_out   every aggregate as a prefix / suffix sum over the buckets.
 #include "lmf_tree.h"
 #include "lmf_tree_dev.cuh"
