@@ -21,13 +21,18 @@
 //                the nodes' predicates, computes the row's fixed-point moments
 //                and its bucket for every split attribute (binary search over
 //                the thresholds, held in shared memory), and adds the moments
-//                to the histogram in global memory with 64-bit integer
-//                reductions (exact, order-free).  When every active row of a
-//                warp falls into one cell -- the rule for a split on a
+//                to the histogram in global memory as exact integers
+//                (order-free): the row's record, staged once in shared memory,
+//                to each split's 32-byte cell by one bulk reduction
+//                (cp.reduce.async.bulk .add.u64), or by 64-bit reductions when
+//                a cell holds more than four moments.  When every active row
+//                of a warp falls into one cell -- the rule for a split on a
 //                dimension attribute over a root sorted on its join keys --
 //                the warp sums its moments first (three 32-bit warp
 //                reductions per 64-bit value) and one lane issues the
-//                reduction.  Nothing per row leaves the SM.  Its body is
+//                reduction; splits on the resident key's dimension are summed
+//                per (node, key) in shared memory and added once per key.
+//                Nothing per row leaves the SM.  Its body is
 //                tree_body (lmf_tree_dev.cuh); lmf_tree_jit, compiled for the
 //                plan at plan time (lmf_jit_tree.cu), runs the same body with
 //                the row pass and the node search generated for the plan, and
